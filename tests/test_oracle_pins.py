@@ -1,0 +1,424 @@
+"""Pins for the FP64 oracle against facts that do not come from the oracle itself.
+
+The paper prints no worked example (no per-pixel value, image or kernel output), so every pin
+here is a closed form, a library routine the method reduces to in a special case, an invariant,
+brute force, or a central finite difference of the oracle's own forward:
+
+  * real SH basis (Eq. app-sh) == the real combination of scipy's complex harmonics, and it is
+    orthonormal on the sphere (quadrature);
+  * quaternion -> rotation == scipy.spatial.transform.Rotation;
+  * single isotropic Gaussian on the optical axis: footprint in closed form (Eq. proj, Eq. alpha);
+  * off-axis Gaussian: Sigma^I == J R Sigma^W R^T J^T with J from finite differences of the pinhole
+    map (Eq. proj), Sigma^W from scipy's rotation;
+  * two and three Gaussians on one ray: compositing, depth order, and the transmittance stop;
+  * telescoping (white Gaussians, black background => colour == accumulated opacity);
+  * permutation of the input order, rigid translation and (SH degree 0) rigid rotation of the
+    world leave the image unchanged, and the gradient identities these symmetries imply;
+  * brute force (no candidate culling) == accelerated candidate lists;
+  * central finite differences of every gradient, including the twist of the left pose update
+    T <- exp(xi^) T (Eq. leftupdate), with exp from scipy.linalg.expm.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.special
+from scipy.spatial.transform import Rotation
+
+import oracle
+from paper_2601_00705_gb300 import synthetic
+
+Y00 = 0.5 / math.sqrt(math.pi)
+
+
+def _cam(W, H, f=50.0, R=None, t=None, fy=None, cx=None, cy=None):
+    return dict(width=W, height=H, fx=f, fy=f if fy is None else fy,
+                cx=(W - 1) / 2 if cx is None else cx, cy=(H - 1) / 2 if cy is None else cy,
+                R=np.eye(3) if R is None else R, t=np.zeros(3) if t is None else t)
+
+
+def _scene(means, log_scales, quats, logits, sh):
+    return dict(means=np.asarray(means, float), log_scales=np.asarray(log_scales, float),
+                quats=np.asarray(quats, float), opacity_logits=np.asarray(logits, float),
+                sh=np.asarray(sh, float))
+
+
+def _logit(o):
+    return math.log(o / (1 - o))
+
+
+# ----------------------------------------------------------------------------- SH and rotations
+
+def _real_sh_scipy(l, m, dirs):
+    theta = np.arccos(np.clip(dirs[:, 2], -1, 1))
+    phi = np.mod(np.arctan2(dirs[:, 1], dirs[:, 0]), 2 * np.pi)
+    Y = scipy.special.sph_harm_y(l, abs(m), theta, phi)
+    if m > 0:
+        return math.sqrt(2) * Y.real
+    if m < 0:
+        return math.sqrt(2) * Y.imag
+    return Y.real
+
+
+def test_sh_basis_matches_scipy_real_harmonics():
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal((200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    Y = oracle.sh_basis(3, d)
+    for l in range(4):
+        for m in range(-l, l + 1):
+            np.testing.assert_allclose(Y[:, l * l + l + m], _real_sh_scipy(l, m, d), atol=1e-12,
+                                       err_msg=f"l={l} m={m}")
+
+
+def test_sh_basis_orthonormal_and_degree_truncation():
+    # Gauss-Legendre in cos(theta) x uniform phi integrates degree <= 6 products exactly.
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    ct, ph = np.meshgrid(xg, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    d = np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=-1).reshape(-1, 3)
+    w = (np.repeat(wg, nphi) * (2 * np.pi / nphi))
+    Y = oracle.sh_basis(3, d)
+    gram = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
+    for deg in range(4):
+        Yd = oracle.sh_basis(deg, d)
+        K = (deg + 1) ** 2
+        np.testing.assert_array_equal(Yd[:, K:], 0.0)
+        np.testing.assert_allclose(Yd[:, :K], Y[:, :K], atol=0)
+
+
+def test_quat_to_rotmat_matches_scipy():
+    rng = np.random.default_rng(1)
+    q = rng.standard_normal((100, 4)) * rng.uniform(0.1, 3.0, size=(100, 1))  # not unit
+    R = oracle.quat_to_rotmat(q)
+    ref = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()  # scipy is scalar-last
+    np.testing.assert_allclose(R, ref, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("eps2d", [0.0, 0.3])
+@pytest.mark.parametrize("fy", [50.0, 65.0])
+def test_single_isotropic_gaussian_closed_form(eps2d, fy):
+    W, H, fx = 24, 20, 50.0
+    z, s, o = 3.0, 0.12, 0.7
+    rgb = np.array([0.2, 0.5, 0.9])
+    bg = (0.1, 0.2, 0.3)
+    qrand = Rotation.random(random_state=3).as_quat()[[3, 0, 1, 2]]  # isotropic: any rotation
+    g = _scene([[0, 0, z]], [[math.log(s)] * 3], [qrand], [_logit(o)], [((rgb - 0.5) / Y00)[None]])
+    cam = _cam(W, H, fx, fy=fy, cx=11.3, cy=8.6)
+    cfg = dict(eps2d=eps2d, bg=bg)
+    out = oracle.render(g, [cam], cfg)
+    # J = diag(f/z) at x = y = 0  =>  Sigma^I = diag((fx s/z)^2, (fy s/z)^2) + eps I.
+    sx2 = (fx * s / z) ** 2 + eps2d
+    sy2 = (fy * s / z) ** 2 + eps2d
+    ys, xs = np.mgrid[0:H, 0:W]
+    G = np.exp(-0.5 * ((xs - 11.3) ** 2 / sx2 + (ys - 8.6) ** 2 / sy2)).reshape(-1)
+    a = np.minimum(0.99, o * G)
+    a = np.where(a >= 1 / 255, a, 0.0)
+    np.testing.assert_allclose(out["alpha"], a, atol=1e-13)
+    np.testing.assert_allclose(out["depth"], z * a, atol=1e-13)
+    np.testing.assert_allclose(out["color"], a[:, None] * rgb + (1 - a[:, None]) * np.array(bg),
+                               atol=1e-13)
+    np.testing.assert_array_equal(out["n_contrib"], (a > 0).astype(np.int32))
+    proj = oracle.project(g, [cam], cfg)
+    np.testing.assert_allclose(proj["cov2d"][0, 0], [sx2, 0.0, sy2], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(proj["mean2d"][0, 0], [11.3, 8.6], atol=1e-13)
+
+
+def _pinhole(Y, fx, fy, cx, cy):
+    return np.array([fx * Y[0] / Y[2] + cx, fy * Y[1] / Y[2] + cy])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_off_axis_covariance_matches_numeric_jacobian(seed):
+    rng = np.random.default_rng(seed)
+    R = Rotation.random(random_state=seed).as_matrix()
+    mu_c = np.array([rng.uniform(-0.6, 0.6), rng.uniform(-0.5, 0.5), rng.uniform(2, 4)])
+    t = rng.standard_normal(3)
+    mu_w = R.T @ (mu_c - t)
+    ls = rng.normal(-2.0, 0.4, 3)
+    q = rng.standard_normal(4)
+    fx, fy, cx, cy = 80.0, 70.0, 31.5, 23.5
+    g = _scene([mu_w], [ls], [q], [0.0], np.zeros((1, 1, 3)))
+    cam = _cam(64, 48, fx, R=R, t=t, fy=fy, cx=cx, cy=cy)
+    proj = oracle.project(g, [cam], dict(eps2d=0.0, jac_clamp=0.0))
+    h = 1e-6
+    J = np.zeros((2, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        J[:, k] = (_pinhole(mu_c + e, fx, fy, cx, cy) - _pinhole(mu_c - e, fx, fy, cx, cy)) / (2 * h)
+    Rq = Rotation.from_quat(q[[1, 2, 3, 0]]).as_matrix()
+    Sw = Rq @ np.diag(np.exp(2 * ls)) @ Rq.T
+    S = J @ R @ Sw @ R.T @ J.T
+    np.testing.assert_allclose(proj["cov2d"][0, 0], [S[0, 0], S[0, 1], S[1, 1]], rtol=1e-7)
+    np.testing.assert_allclose(proj["mean2d"][0, 0], _pinhole(mu_c, fx, fy, cx, cy), rtol=1e-13)
+    np.testing.assert_allclose(proj["depth"][0, 0], mu_c[2], rtol=1e-13)
+
+
+def _on_axis(zs, opac, rgbs, s=0.3):
+    n = len(zs)
+    return _scene([[0, 0, z] for z in zs], [[math.log(s)] * 3] * n, [[1, 0, 0, 0]] * n,
+                  [_logit(o) for o in opac], [((np.array(c) - 0.5) / Y00)[None] for c in rgbs])
+
+
+def test_two_gaussians_composite_front_to_back_by_depth():
+    c1, c2 = [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]
+    cam = _cam(9, 9, 40.0)
+    p = 4 * 9 + 4  # the principal point pixel (4, 4)
+    for z1, z2 in [(2.0, 3.0), (3.0, 2.0)]:
+        out = oracle.render(_on_axis([z1, z2], [0.6, 0.5], [c1, c2]), [cam])
+        a_near, a_far = (0.6, 0.5) if z1 < z2 else (0.5, 0.6)
+        c_near, c_far = (c1, c2) if z1 < z2 else (c2, c1)
+        z_near, z_far = min(z1, z2), max(z1, z2)
+        exp_c = a_near * np.array(c_near) + a_far * (1 - a_near) * np.array(c_far)
+        np.testing.assert_allclose(out["color"][p], exp_c, atol=1e-14)
+        np.testing.assert_allclose(out["depth"][p], a_near * z_near + a_far * (1 - a_near) * z_far,
+                                   atol=1e-14)
+        np.testing.assert_allclose(out["t_final"][p], (1 - a_near) * (1 - a_far), atol=1e-14)
+
+
+def test_transmittance_stop_and_alpha_clamp():
+    # alpha_1 = min(0.99, 0.995) = 0.99, alpha_2 = 0.98 keeps T = 2e-4 >= 1e-4;
+    # alpha_3 = 0.9 would give T = 2e-5 < 1e-4, so the third Gaussian is left out.
+    cols = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    out = oracle.render(_on_axis([2.0, 2.5, 3.0], [0.995, 0.98, 0.9], cols), [_cam(9, 9, 40.0)])
+    p = 4 * 9 + 4
+    np.testing.assert_array_equal(out["n_contrib"][p], 2)
+    np.testing.assert_allclose(out["color"][p], [0.99, 0.01 * 0.98, 0.0], atol=1e-14)
+    np.testing.assert_allclose(out["t_final"][p], 0.01 * 0.02, rtol=1e-12)
+
+
+def test_coverage_threshold_drops_faint_gaussians():
+    # A single Gaussian of opacity below 1/255 never covers a pixel.
+    out = oracle.render(_on_axis([2.0], [0.003], [[1, 1, 1]]), [_cam(9, 9, 40.0)])
+    np.testing.assert_array_equal(out["n_contrib"], 0)
+    np.testing.assert_array_equal(out["alpha"], 0.0)
+
+
+# ----------------------------------------------------------------------------- invariants
+
+def _tiny_scene(seed, n=200, W=48, H=36):
+    wl = synthetic.tiny(seed=seed, n=n, width=W, height=H)
+    return wl.gaussians.as_dict(), wl.cameras
+
+
+def test_telescoping_white_gaussians():
+    g, cams = _tiny_scene(11)
+    g = dict(g)
+    g["sh"] = np.full_like(g["sh"], 0.5 / Y00)  # every colour exactly 1
+    out = oracle.render(g, cams, dict(bg=(0, 0, 0)))
+    for ch in range(3):
+        np.testing.assert_allclose(out["color"][:, ch], out["alpha"], atol=1e-12)
+    np.testing.assert_allclose(out["alpha"] + out["t_final"], 1.0, atol=1e-15)
+    assert out["n_contrib"].max() > 3
+
+
+def test_bruteforce_equals_candidate_lists():
+    wl = synthetic.tiny()
+    g = wl.gaussians.as_dict()
+    a = oracle.render(g, wl.cameras)
+    b = oracle.render(g, wl.cameras, brute_force=True)
+    for k in ("color", "depth", "alpha", "t_final", "n_contrib", "ambiguous"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_thread_count_changes_only_summation_order():
+    g, cams = _tiny_scene(5)
+    up = np.random.default_rng(0).standard_normal((48 * 36, 3))
+    a = oracle.render(g, cams, d_color=up, threads=1)
+    b = oracle.render(g, cams, d_color=up, threads=7)
+    c = oracle.render(g, cams, d_color=up, threads=7)
+    np.testing.assert_array_equal(a["color"], b["color"])
+    for k in ("g_means", "g_sh", "g_pose"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-11, atol=1e-13, err_msg=k)
+        np.testing.assert_array_equal(b[k], c[k], err_msg=k)
+
+
+def test_input_permutation_invariance():
+    g, cams = _tiny_scene(12)
+    n = g["means"].shape[0]
+    perm = np.random.default_rng(0).permutation(n)
+    gp = {k: v[perm] for k, v in g.items()}
+    up = np.random.default_rng(1).standard_normal((48 * 36, 3))
+    a = oracle.render(g, cams, d_color=up)
+    b = oracle.render(gp, cams, d_color=up)
+    for k in ("color", "depth", "alpha", "n_contrib"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    np.testing.assert_allclose(a["g_means"][perm], b["g_means"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a["g_pose"], b["g_pose"], rtol=1e-10, atol=1e-14)
+
+
+def _random_pose(seed):
+    R = Rotation.random(random_state=seed).as_matrix()
+    return R
+
+
+def _scene_in_front(seed, n, W, H, f, degree):
+    """Gaussians spread in front of a rotated, translated camera."""
+    rng = np.random.default_rng(seed)
+    R = Rotation.random(random_state=seed + 100).as_matrix()
+    t = rng.standard_normal(3)
+    mu_c = np.stack([rng.uniform(-0.5, 0.5, n) * W / f * 2.5, rng.uniform(-0.5, 0.5, n) * H / f * 2.5,
+                     rng.uniform(2.0, 3.5, n)], axis=1)
+    mu_w = (mu_c - t) @ R  # R^T (mu_c - t)
+    K = (degree + 1) ** 2
+    sh = rng.normal(0, 0.3, (n, K, 3))
+    sh[:, 0, :] = (rng.uniform(0.2, 0.8, (n, 3)) - 0.5) / Y00
+    g = _scene(mu_w, rng.normal(math.log(0.06), 0.3, (n, 3)), rng.standard_normal((n, 4)),
+               rng.normal(0.0, 0.8, n), sh)
+    cam = _cam(W, H, f, R=R, t=t)
+    return g, cam
+
+
+def test_rigid_translation_invariance_and_gradient_identity():
+    g, cam = _scene_in_front(21, 30, 40, 32, 45.0, 3)
+    delta = np.array([0.7, -1.3, 0.4])
+    g2 = dict(g)
+    g2["means"] = g["means"] + delta
+    cam2 = dict(cam)
+    cam2["t"] = cam["t"] - cam["R"] @ delta
+    up = np.random.default_rng(2).standard_normal((40 * 32, 3))
+    a = oracle.render(g, [cam], d_color=up, d_depth=up[:, 0])
+    b = oracle.render(g2, [cam2], d_color=up, d_depth=up[:, 0])
+    np.testing.assert_allclose(a["color"], b["color"], atol=1e-10)
+    np.testing.assert_allclose(a["depth"], b["depth"], atol=1e-10)
+    # d/d delta of L(mu + delta, t - R delta) = 0  =>  sum_i dL/dmu_i = R^T dL/drho.
+    np.testing.assert_allclose(a["g_means"].sum(0), cam["R"].T @ a["g_pose"][0, :3], rtol=1e-8,
+                               atol=1e-12)
+
+
+def _quat_mul(a, b):
+    w1, v1 = a[..., :1], a[..., 1:]
+    w2, v2 = b[..., :1], b[..., 1:]
+    return np.concatenate([w1 * w2 - (v1 * v2).sum(-1, keepdims=True),
+                           w1 * v2 + w2 * v1 + np.cross(v1, v2)], axis=-1)
+
+
+def test_world_rotation_invariance_degree0_and_omega_identity():
+    g, cam = _scene_in_front(31, 30, 40, 32, 45.0, 0)
+    Qr = Rotation.random(random_state=7)
+    Q = Qr.as_matrix()
+    qQ = Qr.as_quat()[[3, 0, 1, 2]]
+    g2 = dict(g)
+    g2["means"] = g["means"] @ Q.T
+    g2["quats"] = _quat_mul(np.broadcast_to(qQ, g["quats"].shape), g["quats"])
+    cam2 = dict(cam)
+    cam2["R"] = cam["R"] @ Q.T
+    up = np.random.default_rng(3).standard_normal((40 * 32, 3))
+    a = oracle.render(g, [cam], d_color=up, d_alpha=up[:, 1])
+    b = oracle.render(g2, [cam2], d_color=up, d_alpha=up[:, 1])
+    np.testing.assert_allclose(a["color"], b["color"], atol=1e-10)
+    # Infinitesimal world rotation phi: mu -> mu + phi x mu, q -> (1, phi/2) q, R -> R - R[phi]_x.
+    # Invariance gives sum_i mu_i x g_mu_i + 1/2 sum_i (w g_v - g_w v + v x g_v) = R^T (g_omega - t x g_rho).
+    mu, gm = g["means"], a["g_means"]
+    q, gq = g["quats"], a["g_quats"]
+    lhs = np.cross(mu, gm).sum(0)
+    lhs += 0.5 * (q[:, :1] * gq[:, 1:] - gq[:, :1] * q[:, 1:] + np.cross(q[:, 1:], gq[:, 1:])).sum(0)
+    rho, om = a["g_pose"][0, :3], a["g_pose"][0, 3:]
+    rhs = cam["R"].T @ (om - np.cross(cam["t"], rho))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-7, atol=1e-10)
+
+
+# ----------------------------------------------------------------------------- finite differences
+
+FD_MARGINS = dict(margin_alpha=1e-3, margin_t=1e-3, margin_z=1e-9, margin_g=1e-3, margin_effect=0.0)
+
+
+def _loss(out, up):
+    return ((out["color"] * up["c"]).sum() + (out["depth"] * up["d"]).sum()
+            + (out["alpha"] * up["a"]).sum())
+
+
+def _twist_matrix(xi):
+    rho, om = xi[:3], xi[3:]
+    M = np.zeros((4, 4))
+    M[:3, :3] = np.array([[0, -om[2], om[1]], [om[2], 0, -om[0]], [-om[1], om[0], 0]])
+    M[:3, 3] = rho
+    return M
+
+
+def _fd_case(seed, degree, bg):
+    W, H, f = 20, 16, 30.0
+    for attempt in range(50):
+        g, cam = _scene_in_front(seed * 100 + attempt, 7, W, H, f, degree)
+        out = oracle.render(g, [cam], dict(FD_MARGINS, bg=bg))
+        if out["ambiguous"].any() or out["n_contrib"].max() < 3:
+            continue
+        return g, cam
+    raise RuntimeError("no kink-free scene found")
+
+
+@pytest.mark.parametrize("seed,degree", [(1, 0), (2, 3), (3, 1), (4, 2)])
+def test_gradients_match_central_finite_differences(seed, degree):
+    bg = (0.3, 0.1, 0.6)
+    cfg = dict(bg=bg)
+    g, cam = _fd_case(seed, degree, bg)
+    P = cam["width"] * cam["height"]
+    rng = np.random.default_rng(seed)
+    up = dict(c=rng.standard_normal((P, 3)), d=rng.standard_normal(P), a=rng.standard_normal(P))
+    ana = oracle.render(g, [cam], cfg, d_color=up["c"], d_depth=up["d"], d_alpha=up["a"], threads=1)
+
+    def L(gg, cc):
+        return _loss(oracle.render(gg, [cc], cfg, threads=1), up)
+
+    names = [("means", "g_means"), ("log_scales", "g_log_scales"), ("quats", "g_quats"),
+             ("opacity_logits", "g_opacity_logits"), ("sh", "g_sh")]
+    for pname, gname in names:
+        x = g[pname]
+        num = np.zeros_like(x)
+        for idx in np.ndindex(x.shape):
+            h = 1e-6 * max(1.0, abs(x[idx]))
+            gp = dict(g)
+            gp[pname] = x.copy()
+            gp[pname][idx] += h
+            gm = dict(g)
+            gm[pname] = x.copy()
+            gm[pname][idx] -= h
+            num[idx] = (L(gp, cam) - L(gm, cam)) / (2 * h)
+        scale = np.abs(num).max()
+        assert scale > 0, pname
+        np.testing.assert_allclose(ana[gname], num, atol=2e-6 * scale, rtol=2e-5, err_msg=pname)
+    # Twist of the left update T <- exp(xi^) T.
+    T = np.eye(4)
+    T[:3, :3] = cam["R"]
+    T[:3, 3] = cam["t"]
+    num = np.zeros(6)
+    for k in range(6):
+        vals = []
+        for sgn in (1, -1):
+            xi = np.zeros(6)
+            xi[k] = sgn * 1e-6
+            Tn = scipy.linalg.expm(_twist_matrix(xi)) @ T
+            cc = dict(cam)
+            cc["R"], cc["t"] = Tn[:3, :3], Tn[:3, 3]
+            vals.append(L(g, cc))
+        num[k] = (vals[0] - vals[1]) / 2e-6
+    np.testing.assert_allclose(ana["g_pose"][0], num, rtol=2e-5, atol=2e-6 * np.abs(num).max())
+
+
+def test_jacobian_clamp_blocks_gradient_of_clamped_component():
+    # A Gaussian far outside the guard band: its mean2d still moves with x, but the clamped
+    # J component does not; finite differences of the forward agree with the analytic gradient.
+    W, H, f = 20, 16, 30.0
+    g = _scene([[1.9, 0.1, 2.0]], [[math.log(0.5)] * 3], [[1, 0.2, 0.1, 0]], [_logit(0.8)],
+               [((np.array([0.5, 0.6, 0.7]) - 0.5) / Y00)[None]])
+    cam = _cam(W, H, f)
+    proj = oracle.project(g, [cam])
+    assert proj["valid"][0, 0]
+    up = np.random.default_rng(0).standard_normal((W * H, 3))
+    ana = oracle.render(g, [cam], d_color=up)
+    assert abs(ana["g_means"][0, 0]) > 0
+    h = 1e-6
+    vals = []
+    for s in (1, -1):
+        gg = dict(g)
+        gg["means"] = g["means"].copy()
+        gg["means"][0, 0] += s * h
+        vals.append((oracle.render(gg, [cam])["color"] * up).sum())
+    np.testing.assert_allclose(ana["g_means"][0, 0], (vals[0] - vals[1]) / (2 * h), rtol=1e-5)
