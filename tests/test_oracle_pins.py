@@ -183,6 +183,19 @@ def test_two_gaussians_composite_front_to_back_by_depth():
         np.testing.assert_allclose(out["t_final"][p], (1 - a_near) * (1 - a_far), atol=1e-14)
 
 
+def test_equal_depths_composite_in_index_order():
+    # Equal depth keys: the Gaussian with the lower input index is in front.
+    c1, c2 = [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]
+    cam = _cam(9, 9, 40.0)
+    p = 4 * 9 + 4
+    out = oracle.render(_on_axis([2.5, 2.5], [0.6, 0.5], [c1, c2]), [cam])
+    np.testing.assert_allclose(out["color"][p], 0.6 * np.array(c1) + 0.5 * 0.4 * np.array(c2),
+                               atol=1e-14)
+    out = oracle.render(_on_axis([2.5, 2.5], [0.5, 0.6], [c2, c1]), [cam])
+    np.testing.assert_allclose(out["color"][p], 0.5 * np.array(c2) + 0.6 * 0.5 * np.array(c1),
+                               atol=1e-14)
+
+
 def test_transmittance_stop_and_alpha_clamp():
     # alpha_1 = min(0.99, 0.995) = 0.99, alpha_2 = 0.98 keeps T = 2e-4 >= 1e-4;
     # alpha_3 = 0.9 would give T = 2e-5 < 1e-4, so the third Gaussian is left out.
