@@ -1,0 +1,204 @@
+/*
+ * rgs.h -- C ABI of the GB300 (sm_103a) differentiable 3D Gaussian-splatting rasterizer.
+ *
+ * The library renders a set of anisotropic 3D Gaussians into one or more pinhole views and
+ * back-propagates image gradients to every Gaussian parameter and to each view's SE(3) pose.
+ *
+ *   Forward  (Section 3.1, Eq. proj and Eq. alpha; Appendix C.1, Eq. app-sh):
+ *     mu^C = R mu^W + t, mu^I = pi(mu^C), Sigma^I = J R Sigma^W R^T J^T + eps2d I,
+ *     Sigma^W = R_q diag(exp(2 log_scale)) R_q^T, colour from real spherical harmonics of the
+ *     viewing direction, opacity o = sigmoid(logit); per pixel the covering Gaussians are
+ *     composited front to back, C = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j).
+ *   Backward (Section 3.1, differentiability in colour, opacity, mean, covariance and pose;
+ *     Section 3.2.3, Eq. leftupdate, Eq. muCjac, Eq. muIjac, Eq. sigmaIjac): gradients of the
+ *     rendered colour, depth and accumulated opacity with respect to means, log-scales,
+ *     quaternions, opacity logits, SH coefficients, and the twist xi = (rho, omega) of the left
+ *     update T_WC <- exp(xi^) T_WC, evaluated at xi = 0.
+ *
+ * Conventions
+ *   - Every array is a DEVICE pointer on the context's device unless stated otherwise, FP32,
+ *     C-contiguous, and owned by the caller. Nothing is copied: a device array passed to
+ *     rgs_render_forward must stay alive and unchanged until the matching rgs_render_backward
+ *     (and rgs_release_state) has completed on the stream.
+ *   - Images of all views are concatenated: view v occupies pixels [offset_v, offset_v + W_v H_v)
+ *     with offset_v = sum_{u<v} W_u H_u, row-major inside a view; colour is [P,3] interleaved.
+ *   - Pixel (x, y) is sampled at image coordinates (x, y). A Gaussian covers a pixel iff
+ *     alpha = min(alpha_max, o G) >= alpha_min; compositing stops before the Gaussian whose
+ *     inclusion would drop the transmittance below t_min; near-to-far order is by camera-space
+ *     depth of the Gaussian centre (rounded to float32), ties by Gaussian index.
+ *   - Outputs: colour = sum w_i c_i + T_final bg, depth = sum w_i z_i, alpha = 1 - T_final.
+ *   - All calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream). Gradient buffers are overwritten, not accumulated.
+ *   - Errors are returned as rgs_status; rgs_last_error() gives a message. No call throws or aborts.
+ *   - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef RGS_H_
+#define RGS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RGS_MAX_VIEWS 64
+
+typedef enum {
+  RGS_OK = 0,
+  RGS_ERR_INVALID_ARG = 1, /* a null, misaligned or out-of-range argument */
+  RGS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in rgs_last_error) */
+  RGS_ERR_CAPACITY = 3,    /* the (view, tile) pair list outgrew its capacity during stream
+                              capture; results are incomplete. Re-run outside capture (which
+                              grows it) or call rgs_reserve first */
+  RGS_ERR_NOMEM = 4,       /* device allocation failed */
+  RGS_ERR_STATE = 5,       /* unknown or released state handle */
+} rgs_status;
+
+/* Opaque context: owns per-forward saved state (projected records, sorted pair lists, tile
+ * ranges, per-pixel final transmittance and last-contributor index) and sort scratch. */
+typedef struct rgs_ctx rgs_ctx;
+
+/* The Gaussian set (Section 3.1; Appendix C.1). Device pointers, FP32, caller-owned.
+ *   means [n,3] world frame; log_scales [n,3]; quats [n,4] as (w, x, y, z), normalised inside
+ *   (need not be unit); opacity_logits [n]; sh [n,K,3], K = (sh_degree+1)^2, basis order
+ *   l = 0..sh_degree, m = -l..l. Each pointer must be 16-byte aligned. */
+typedef struct {
+  int32_t n;
+  int32_t sh_degree; /* 0..3 */
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+} rgs_gaussians;
+
+/* One pinhole view (HOST struct). world_to_cam is the row-major 3x4 [R | t] of T_WC,
+ * mu^C = R mu^W + t; R must be a rotation. Camera axes: x right, y down, z forward. */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float world_to_cam[12];
+} rgs_camera;
+
+/* Renderer constants (HOST struct); rgs_config_default fills the defaults shown. */
+typedef struct {
+  float alpha_min;  /* 1/255: a Gaussian covers a pixel iff min(alpha_max, o G) >= alpha_min */
+  float alpha_max;  /* 0.99 */
+  float t_min;      /* 1e-4: transmittance stop */
+  float znear;      /* 0.2: Gaussians with camera depth <= znear are culled */
+  float eps2d;      /* 0.3 px^2: dilation added to Sigma^I before inversion */
+  float jac_clamp;  /* 1.3: J uses x/z, y/z clamped to +-jac_clamp*(W/2)/fx, (H/2)/fy; 0 = off */
+  float bg[3];      /* background colour, added as bg * T_final */
+  int32_t tile_w;   /* tile shape of the binning and blend: 16x16 (default), 8x8 or 32x8 */
+  int32_t tile_h;
+} rgs_config;
+
+/* Forward outputs (device, caller-owned, P = sum_v W_v H_v): color [P,3], depth [P], alpha [P]. */
+typedef struct {
+  float* color;
+  float* depth;
+  float* alpha;
+} rgs_images;
+
+/* Upstream gradients of a scalar loss with respect to the forward outputs (device, [P,3], [P],
+ * [P]); a NULL member means zero. */
+typedef struct {
+  const float* d_color;
+  const float* d_depth;
+  const float* d_alpha;
+} rgs_image_grads;
+
+/* Bits of grad_mask for rgs_render_backward. */
+#define RGS_GRAD_MEANS 1u
+#define RGS_GRAD_SCALES 2u
+#define RGS_GRAD_QUATS 4u
+#define RGS_GRAD_OPACITY 8u
+#define RGS_GRAD_SH 16u
+#define RGS_GRAD_POSE 32u
+#define RGS_GRAD_ALL 63u
+
+/* Counters of the last forward on a state (read back with a stream synchronisation). */
+typedef struct {
+  int64_t n_visible;       /* (view, Gaussian) pairs that touch at least one tile */
+  int64_t n_pairs;         /* duplicated (view, tile, Gaussian) entries */
+  int64_t n_eval;          /* (pixel, Gaussian) list positions visited by the forward blend */
+  int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs */
+  int64_t pair_capacity;   /* allocated pair-list capacity */
+  int64_t state_bytes;     /* device bytes held by the state */
+  uint32_t status;         /* device status bits: 1 = pair list overflowed its capacity */
+  uint32_t reserved;
+} rgs_stats;
+
+/* Creates a context on CUDA device `device`. Returns RGS_ERR_INVALID_ARG for a null out pointer
+ * or bad device, RGS_ERR_CUDA if the device cannot be used. */
+rgs_status rgs_create(rgs_ctx** ctx, int device);
+
+/* Frees every state and scratch buffer (synchronises the device). NULL is a no-op. */
+void rgs_destroy(rgs_ctx* ctx);
+
+/* Fills the defaults listed in rgs_config. */
+void rgs_config_default(rgs_config* cfg);
+
+/* Message of the last failed call on this context ("" if none). Valid until the next call. */
+const char* rgs_last_error(const rgs_ctx* ctx);
+
+/* Renders n_views (1..RGS_MAX_VIEWS) views of the Gaussian set in one batched launch sequence
+ * (Section 3.1, Eq. proj and Eq. alpha; the keyframe window of the mapping loss, Eq. map-loss).
+ *   g: Gaussian set (n may be 0: empty images, alpha 0, colour = bg).
+ *   cams: HOST array of n_views cameras; each W, H in 1..16384.
+ *   cfg: HOST config, or NULL for the defaults.
+ *   out: device output images.
+ *   state: in/out. If *state is 0 a new state is created and its handle written back; otherwise
+ *     the named state is reused (its previous contents are replaced). The state keeps the data
+ *     the backward needs.
+ * Outside stream capture the call synchronises the stream once (after binning) to size the
+ * pair list. Under stream capture it never synchronises; if the pair list would overflow, the
+ * kernels record it, output is incomplete and rgs_query_stats reports status bit 1. */
+rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                              int32_t n_views, const rgs_config* cfg, rgs_images* out,
+                              uint64_t* state, void* stream);
+
+/* Back-propagates upstream image gradients through the forward saved in `state`
+ * (Section 3.1; Section 3.2.3 Eq. muCjac, Eq. muIjac, Eq. sigmaIjac). The Gaussian arrays and
+ * cameras of that forward are used; they must be unchanged.
+ *   grads: HOST struct of device pointers (members may be NULL = zero).
+ *   grad_mask: RGS_GRAD_* bits; outputs whose bit is clear may be NULL and are not written.
+ *   d_means [n,3], d_log_scales [n,3], d_quats [n,4], d_opacity_logits [n], d_sh [n,K,3]:
+ *     summed over all views of the forward; overwritten.
+ *   d_pose [n_views,6]: (rho, omega) per view, the gradient with respect to the twist of the
+ *     left update at xi = 0; overwritten. */
+rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t state, const rgs_image_grads* grads,
+                               uint32_t grad_mask, float* d_means, float* d_log_scales,
+                               float* d_quats, float* d_opacity_logits, float* d_sh,
+                               float* d_pose, void* stream);
+
+/* Frees a state's device memory (after its queued work completes). */
+rgs_status rgs_release_state(rgs_ctx* ctx, uint64_t state);
+
+/* Grows a state's pair-list capacity to at least `pair_capacity` entries (0 = leave), so that a
+ * later forward under stream capture does not overflow. Creates the state if *state is 0. */
+rgs_status rgs_reserve(rgs_ctx* ctx, uint64_t* state, int64_t pair_capacity, void* stream);
+
+/* Reads the counters of the last forward on `state` (synchronises `stream`). */
+rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t state, rgs_stats* out, void* stream);
+
+/* ---- Primitives of the binning stage, exposed for testing (Section 3.1: the front-to-back
+ * ordered covering set is built by a key sort). Device pointers, caller-owned. ---- */
+
+/* Stable LSD radix sort of n (key, value) pairs by key bits [begin_bit, end_bit), in place.
+ * keys/vals: device u32 arrays of n entries (vals may be NULL for a keys-only sort). Uses the
+ * context's scratch memory. 0 <= begin_bit < end_bit <= 32. */
+rgs_status rgs_radix_sort_u32(rgs_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n,
+                              int32_t begin_bit, int32_t end_bit, void* stream);
+
+/* Exclusive prefix sum of n u32 values into out (device arrays; out may equal in), and the
+ * total into *total_out (device u32, may be NULL). */
+rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
+                                  uint32_t* total_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGS_H_ */

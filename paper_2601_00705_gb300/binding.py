@@ -1,0 +1,215 @@
+"""ctypes binding of ``librgs.so`` (the C ABI in ``include/rgs.h``). Argument marshalling only:
+every step of the render runs in the library's CUDA kernels.
+
+The library is loaded from ``paper_2601_00705_gb300/_build/librgs.so`` (built by
+``paper_2601_00705_gb300.build``). There is no fallback: if the library cannot be built or
+loaded, importing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+RGS_MAX_VIEWS = 64
+RGS_OK, RGS_ERR_INVALID_ARG, RGS_ERR_CUDA, RGS_ERR_CAPACITY, RGS_ERR_NOMEM, RGS_ERR_STATE = range(6)
+GRAD_MEANS, GRAD_SCALES, GRAD_QUATS, GRAD_OPACITY, GRAD_SH, GRAD_POSE = 1, 2, 4, 8, 16, 32
+GRAD_ALL = 63
+
+# Every function the header declares (checked by the ABI tests).
+EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
+            "rgs_render_forward", "rgs_render_backward", "rgs_release_state", "rgs_reserve",
+            "rgs_query_stats", "rgs_radix_sort_u32", "rgs_exclusive_scan_u32")
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("world_to_cam", ctypes.c_float * 12)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
+                ("t_min", ctypes.c_float), ("znear", ctypes.c_float), ("eps2d", ctypes.c_float),
+                ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32)]
+
+
+class Images(ctypes.Structure):
+    _fields_ = [("color", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("alpha", ctypes.c_void_p)]
+
+
+class ImageGrads(ctypes.Structure):
+    _fields_ = [("d_color", ctypes.c_void_p), ("d_depth", ctypes.c_void_p),
+                ("d_alpha", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_visible", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("n_eval", ctypes.c_int64), ("n_nonfinite", ctypes.c_int64),
+                ("pair_capacity", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
+                ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_needed: bool = True):
+    """Loads librgs.so (building it first if it is missing or stale and nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed:
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB_PATH)
+        P, I32, I64, U32, U64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                 ctypes.c_uint64)
+        S = ctypes.c_int
+        sig = {
+            "rgs_create": (S, [ctypes.POINTER(P), ctypes.c_int]),
+            "rgs_destroy": (None, [P]),
+            "rgs_config_default": (None, [ctypes.POINTER(Config)]),
+            "rgs_last_error": (ctypes.c_char_p, [P]),
+            "rgs_render_forward": (S, [P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), I32,
+                                       ctypes.POINTER(Config), ctypes.POINTER(Images),
+                                       ctypes.POINTER(U64), P]),
+            "rgs_render_backward": (S, [P, U64, ctypes.POINTER(ImageGrads), U32, P, P, P, P, P, P,
+                                        P]),
+            "rgs_release_state": (S, [P, U64]),
+            "rgs_reserve": (S, [P, ctypes.POINTER(U64), I64, P]),
+            "rgs_query_stats": (S, [P, U64, ctypes.POINTER(Stats), P]),
+            "rgs_radix_sort_u32": (S, [P, P, P, I64, I32, I32, P]),
+            "rgs_exclusive_scan_u32": (S, [P, P, P, I64, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return _lib
+
+
+class RGSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"rgs error {status}: {message}")
+        self.status = status
+
+
+def default_config(**overrides) -> Config:
+    cfg = Config()
+    load().rgs_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "bg":
+            cfg.bg = (ctypes.c_float * 3)(*[float(x) for x in v])
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def make_cameras(cameras) -> ctypes.Array:
+    """Camera dicts (width, height, fx, fy, cx, cy, R [3,3], t [3]) -> rgs_camera array."""
+    arr = (Camera * len(cameras))()
+    for k, c in enumerate(cameras):
+        arr[k].width = int(c["width"])
+        arr[k].height = int(c["height"])
+        arr[k].fx, arr[k].fy = float(c["fx"]), float(c["fy"])
+        arr[k].cx, arr[k].cy = float(c["cx"]), float(c["cy"])
+        R = np.asarray(c["R"], dtype=np.float32).reshape(3, 3)
+        t = np.asarray(c["t"], dtype=np.float32).reshape(3)
+        Rt = np.concatenate([R, t[:, None]], axis=1).reshape(12)
+        for j in range(12):
+            arr[k].world_to_cam[j] = float(Rt[j])
+    return arr
+
+
+class Context:
+    """Owns one rgs_ctx on a CUDA device. Methods take raw device pointers (ints)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.rgs_create(ctypes.byref(h), int(device))
+        if st != RGS_OK:
+            raise RGSError(st, f"rgs_create(device={device}) failed")
+        self.handle = h
+
+    def _check(self, st: int):
+        if st != RGS_OK:
+            msg = self.lib.rgs_last_error(self.handle)
+            raise RGSError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, g: Gaussians, cams, cfg: Config, images: Images, state: int,
+                stream: int) -> int:
+        h = ctypes.c_uint64(state)
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        self._check(self.lib.rgs_render_forward(self.handle, ctypes.byref(g), cam_arr,
+                                                len(cam_arr), ctypes.byref(cfg),
+                                                ctypes.byref(images), ctypes.byref(h),
+                                                ctypes.c_void_p(stream)))
+        return h.value
+
+    def backward(self, state: int, grads: ImageGrads, grad_mask: int, d_means: int,
+                 d_log_scales: int, d_quats: int, d_opacity_logits: int, d_sh: int, d_pose: int,
+                 stream: int):
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_render_backward(
+            self.handle, ctypes.c_uint64(state), ctypes.byref(grads), ctypes.c_uint32(grad_mask),
+            P(d_means or None), P(d_log_scales or None), P(d_quats or None),
+            P(d_opacity_logits or None), P(d_sh or None), P(d_pose or None), P(stream)))
+
+    def release(self, state: int):
+        if state:
+            self._check(self.lib.rgs_release_state(self.handle, ctypes.c_uint64(state)))
+
+    def reserve(self, state: int, pair_capacity: int, stream: int = 0) -> int:
+        h = ctypes.c_uint64(state)
+        self._check(self.lib.rgs_reserve(self.handle, ctypes.byref(h), int(pair_capacity),
+                                         ctypes.c_void_p(stream)))
+        return h.value
+
+    def stats(self, state: int, stream: int = 0) -> dict:
+        s = Stats()
+        self._check(self.lib.rgs_query_stats(self.handle, ctypes.c_uint64(state), ctypes.byref(s),
+                                             ctypes.c_void_p(stream)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def radix_sort_u32(self, keys: int, vals: int, n: int, begin_bit: int, end_bit: int,
+                       stream: int = 0):
+        self._check(self.lib.rgs_radix_sort_u32(self.handle, ctypes.c_void_p(keys),
+                                                ctypes.c_void_p(vals or None), int(n),
+                                                int(begin_bit), int(end_bit),
+                                                ctypes.c_void_p(stream)))
+
+    def exclusive_scan_u32(self, inp: int, out: int, n: int, total: int = 0, stream: int = 0):
+        self._check(self.lib.rgs_exclusive_scan_u32(self.handle, ctypes.c_void_p(inp),
+                                                    ctypes.c_void_p(out), int(n),
+                                                    ctypes.c_void_p(total or None),
+                                                    ctypes.c_void_p(stream)))

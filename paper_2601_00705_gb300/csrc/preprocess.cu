@@ -1,0 +1,645 @@
+// preprocess.cu -- per-Gaussian projection (forward) and its adjoint with the SE(3) pose
+// gradient (backward).
+//
+// Forward (Section 3.1, Eq. proj; Appendix C.1, Eq. app-sh): one thread per Gaussian reads the
+// parameters once and loops over all views of the batch, writing one projected record per
+// (view, Gaussian). Backward (Section 3.2.3, Eq. muCjac, Eq. muIjac, Eq. sigmaIjac): the same
+// thread recomputes each view's projection, chains that view's screen-space gradients to the
+// parameters, sums over views in registers (so every parameter gradient is written once, with no
+// atomics), and reduces the per-view twist gradient over the block.
+#include "rgs_internal.cuh"
+
+namespace rgs {
+namespace {
+
+constexpr int kPreThreads = 128;
+
+// Real spherical harmonics of a unit direction, degree <= DEG (basis index l*l + l + m).
+// Y_{l,m} = sqrt(2) Re / Im of the complex harmonic with the Condon-Shortley phase, as
+// polynomials; the constants are 1/(2 sqrt(pi)), sqrt(3/(4pi)), sqrt(15/pi)/2, sqrt(5/pi)/4,
+// sqrt(15/pi)/4, sqrt(35/(2pi))/4, sqrt(105/pi)/2, sqrt(21/(2pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float kSH0 = 0.28209479177387814f;
+constexpr float kSH1 = 0.4886025119029199f;
+constexpr float kSH2a = 1.0925484305920792f;
+constexpr float kSH2b = 0.31539156525252005f;
+constexpr float kSH2c = 0.5462742152960396f;
+constexpr float kSH30 = 0.5900435899266435f;
+constexpr float kSH31 = 2.890611442640554f;
+constexpr float kSH32 = 0.4570457994644658f;
+constexpr float kSH33 = 0.3731763325901154f;
+constexpr float kSH35 = 1.445305721320277f;
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+  Y[0] = kSH0;
+  if (DEG >= 1) {
+    Y[1] = -kSH1 * y;
+    Y[2] = kSH1 * z;
+    Y[3] = -kSH1 * x;
+  }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kSH2a * x * y;
+    Y[5] = -kSH2a * y * z;
+    Y[6] = kSH2b * (2.0f * zz - xx - yy);
+    Y[7] = -kSH2a * x * z;
+    Y[8] = kSH2c * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -kSH30 * y * (3.0f * xx - yy);
+      Y[10] = kSH31 * x * y * z;
+      Y[11] = -kSH32 * y * (4.0f * zz - xx - yy);
+      Y[12] = kSH33 * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+      Y[13] = -kSH32 * x * (4.0f * zz - xx - yy);
+      Y[14] = kSH35 * z * (xx - yy);
+      Y[15] = -kSH30 * x * (xx - 3.0f * yy);
+    }
+  }
+}
+
+// sum_k w[k] * grad Y_k(x, y, z) (gradient of the polynomials above).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float* w,
+                                             float& gx, float& gy, float& gz) {
+  gx = gy = gz = 0.0f;
+  if (DEG >= 1) {
+    gy += -kSH1 * w[1];
+    gz += kSH1 * w[2];
+    gx += -kSH1 * w[3];
+  }
+  if (DEG >= 2) {
+    gx += kSH2a * y * w[4];
+    gy += kSH2a * x * w[4];
+    gy += -kSH2a * z * w[5];
+    gz += -kSH2a * y * w[5];
+    gx += -2.0f * kSH2b * x * w[6];
+    gy += -2.0f * kSH2b * y * w[6];
+    gz += 4.0f * kSH2b * z * w[6];
+    gx += -kSH2a * z * w[7];
+    gz += -kSH2a * x * w[7];
+    gx += 2.0f * kSH2c * x * w[8];
+    gy += -2.0f * kSH2c * y * w[8];
+    if (DEG >= 3) {
+      const float xx = x * x, yy = y * y, zz = z * z;
+      gx += -kSH30 * 6.0f * x * y * w[9];
+      gy += -kSH30 * 3.0f * (xx - yy) * w[9];
+      gx += kSH31 * y * z * w[10];
+      gy += kSH31 * x * z * w[10];
+      gz += kSH31 * x * y * w[10];
+      gx += kSH32 * 2.0f * x * y * w[11];
+      gy += -kSH32 * (4.0f * zz - xx - 3.0f * yy) * w[11];
+      gz += -kSH32 * 8.0f * y * z * w[11];
+      gx += -kSH33 * 6.0f * x * z * w[12];
+      gy += -kSH33 * 6.0f * y * z * w[12];
+      gz += kSH33 * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12];
+      gx += -kSH32 * (4.0f * zz - 3.0f * xx - yy) * w[13];
+      gy += kSH32 * 2.0f * x * y * w[13];
+      gz += -kSH32 * 8.0f * x * z * w[13];
+      gx += kSH35 * 2.0f * x * z * w[14];
+      gy += -kSH35 * 2.0f * y * z * w[14];
+      gz += kSH35 * (xx - yy) * w[14];
+      gx += -kSH30 * 3.0f * (xx - yy) * w[15];
+      gy += kSH30 * 6.0f * x * y * w[15];
+    }
+  }
+}
+
+// Per-Gaussian, view-independent quantities.
+struct GaussianLocal {
+  float m[3];
+  float qn[4];       // unit quaternion (w, x, y, z)
+  float qnorm;       // |q| before normalisation
+  float Rq[9];       // rotation of the Gaussian, row-major
+  float s[3];        // scales exp(log_scale)
+  float M[9];        // Rq diag(s)
+  float Sw[6];       // Sigma^W = M M^T: xx, xy, xz, yy, yz, zz
+  float opacity;
+};
+
+__device__ __forceinline__ void gaussian_local(const float* m, const float* ls, const float* q,
+                                               float logit, GaussianLocal& g) {
+  g.m[0] = m[0];
+  g.m[1] = m[1];
+  g.m[2] = m[2];
+  g.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const float inv = 1.0f / g.qnorm;
+  const float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+  g.qn[0] = w;
+  g.qn[1] = x;
+  g.qn[2] = y;
+  g.qn[3] = z;
+  g.Rq[0] = 1.0f - 2.0f * (y * y + z * z);
+  g.Rq[1] = 2.0f * (x * y - w * z);
+  g.Rq[2] = 2.0f * (x * z + w * y);
+  g.Rq[3] = 2.0f * (x * y + w * z);
+  g.Rq[4] = 1.0f - 2.0f * (x * x + z * z);
+  g.Rq[5] = 2.0f * (y * z - w * x);
+  g.Rq[6] = 2.0f * (x * z - w * y);
+  g.Rq[7] = 2.0f * (y * z + w * x);
+  g.Rq[8] = 1.0f - 2.0f * (x * x + y * y);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g.s[k] = expf(ls[k]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) g.M[3 * a + b] = g.Rq[3 * a + b] * g.s[b];
+  const float* M = g.M;
+  g.Sw[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  g.Sw[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  g.Sw[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  g.Sw[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  g.Sw[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  g.Sw[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  g.opacity = 1.0f / (1.0f + expf(-logit));
+}
+
+// Projection of one Gaussian into one view (Eq. proj).
+struct ViewProj {
+  float mc[3];             // camera-space mean (each component the float32 rounding of exact)
+  float u, w;              // x/z, y/z
+  float uc, wc;            // clamped for J
+  bool u_cl, w_cl;
+  float J00, J02, J11, J12;
+  float T[6];              // J R, row-major 2x3
+  float TS[6];             // T Sigma^W
+  float cov[3];            // Sigma^I + eps: xx, xy, yy
+  float conic[3];          // a, b, c
+  float mean2d[2];
+};
+
+// Returns false if the Gaussian is culled in this view (behind znear or degenerate).
+__device__ __forceinline__ bool project_view(const GaussianLocal& g, const ViewParams& vp,
+                                             const Consts& c, ViewProj& p) {
+  const float* R = vp.R;
+  p.mc[0] = dot3_plus_accurate(R[0], R[1], R[2], g.m[0], g.m[1], g.m[2], vp.t[0]);
+  p.mc[1] = dot3_plus_accurate(R[3], R[4], R[5], g.m[0], g.m[1], g.m[2], vp.t[1]);
+  p.mc[2] = dot3_plus_accurate(R[6], R[7], R[8], g.m[0], g.m[1], g.m[2], vp.t[2]);
+  const float z = p.mc[2];
+  if (!(z > c.znear)) return false;
+  const float rz = 1.0f / z;
+  p.u = __fdiv_rn(p.mc[0], z);
+  p.w = __fdiv_rn(p.mc[1], z);
+  p.uc = p.u;
+  p.wc = p.w;
+  p.u_cl = p.w_cl = false;
+  if (vp.lim_u > 0.0f) {
+    if (p.u > vp.lim_u) { p.uc = vp.lim_u; p.u_cl = true; }
+    if (p.u < -vp.lim_u) { p.uc = -vp.lim_u; p.u_cl = true; }
+    if (p.w > vp.lim_w) { p.wc = vp.lim_w; p.w_cl = true; }
+    if (p.w < -vp.lim_w) { p.wc = -vp.lim_w; p.w_cl = true; }
+  }
+  p.J00 = vp.fx * rz;
+  p.J02 = -vp.fx * p.uc * rz;
+  p.J11 = vp.fy * rz;
+  p.J12 = -vp.fy * p.wc * rz;
+  // T = J R.
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    p.T[k] = p.J00 * R[k] + p.J02 * R[6 + k];
+    p.T[3 + k] = p.J11 * R[3 + k] + p.J12 * R[6 + k];
+  }
+  // TS = T Sigma^W, Sigma^I = TS T^T + eps I.
+  const float* S = g.Sw;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float t0 = p.T[3 * r], t1 = p.T[3 * r + 1], t2 = p.T[3 * r + 2];
+    p.TS[3 * r + 0] = t0 * S[0] + t1 * S[1] + t2 * S[2];
+    p.TS[3 * r + 1] = t0 * S[1] + t1 * S[3] + t2 * S[4];
+    p.TS[3 * r + 2] = t0 * S[2] + t1 * S[4] + t2 * S[5];
+  }
+  p.cov[0] = p.TS[0] * p.T[0] + p.TS[1] * p.T[1] + p.TS[2] * p.T[2] + c.eps2d;
+  p.cov[1] = p.TS[0] * p.T[3] + p.TS[1] * p.T[4] + p.TS[2] * p.T[5];
+  p.cov[2] = p.TS[3] * p.T[3] + p.TS[4] * p.T[4] + p.TS[5] * p.T[5] + c.eps2d;
+  const float det = p.cov[0] * p.cov[2] - p.cov[1] * p.cov[1];
+  if (!(det > 0.0f)) return false;
+  const float idet = 1.0f / det;
+  p.conic[0] = p.cov[2] * idet;
+  p.conic[1] = -p.cov[1] * idet;
+  p.conic[2] = p.cov[0] * idet;
+  p.mean2d[0] = __fmaf_rn(vp.fx, p.u, vp.cx);
+  p.mean2d[1] = __fmaf_rn(vp.fy, p.w, vp.cy);
+  return true;
+}
+
+template <int DEG>
+__device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, float* c) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const float* p = sh + (size_t)i * 3 * K;
+  if ((3 * K) % 4 == 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < 3 * K / 4; ++k) {
+      const float4 v = __ldg(p4 + k);
+      c[4 * k] = v.x;
+      c[4 * k + 1] = v.y;
+      c[4 * k + 2] = v.z;
+      c[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) c[k] = __ldg(p + k);
+  }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
+    const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
+    const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ logits, const float* __restrict__ sh, float4* __restrict__ rec0,
+    float4* __restrict__ rec1, float4* __restrict__ rec2, uint32_t* __restrict__ ntiles,
+    Counters* __restrict__ counters) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const int i = blockIdx.x * kPreThreads + threadIdx.x;
+  if (i >= n) return;
+  float m[3], ls[3], q[4], shc[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m[k] = __ldg(means + 3 * (size_t)i + k);
+    ls[k] = __ldg(log_scales + 3 * (size_t)i + k);
+  }
+  const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
+  q[0] = q4.x;
+  q[1] = q4.y;
+  q[2] = q4.z;
+  q[3] = q4.w;
+  const float logit = __ldg(logits + i);
+  load_sh<DEG>(sh, i, shc);
+  bool finite = isfinite(logit);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) finite = finite && isfinite(m[k]) && isfinite(ls[k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) finite = finite && isfinite(q[k]);
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) finite = finite && isfinite(shc[k]);
+  GaussianLocal g;
+  if (finite) gaussian_local(m, ls, q, logit, g);
+  finite = finite && g.qnorm > 0.0f && isfinite(g.qnorm);
+  if (!finite) atomicAdd(&counters->n_nonfinite, (uint32_t)views.n_views);
+  const float kappa = finite ? 2.0f * logf(g.opacity / c.alpha_min) : -1.0f;
+  for (int v = 0; v < views.n_views; ++v) {
+    const ViewParams& vp = views.v[v];
+    const size_t vi = (size_t)v * n + i;
+    ViewProj p;
+    uint32_t count = 0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    if (finite && kappa >= 0.0f && project_view(g, vp, c, p)) {
+      r0 = make_float4(p.mean2d[0], p.mean2d[1], g.opacity, p.mc[2]);
+      r1 = make_float4(p.conic[0], p.conic[1], p.conic[2], kappa);
+      // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
+      float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
+            d2 = g.m[2] - vp.cam_center[2];
+      const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      d0 *= rn;
+      d1 *= rn;
+      d2 *= rn;
+      float Y[16];
+      sh_basis<DEG>(d0, d1, d2, Y);
+      float rgb[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc += shc[3 * k + ch] * Y[k];
+        rgb[ch] = fmaxf(acc, 0.0f);
+      }
+      r2 = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+      Ellipse e;
+      if (make_ellipse(r0, r1, e))
+        for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
+                          [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
+    }
+    rec0[vi] = r0;
+    rec1[vi] = r1;
+    rec2[vi] = r2;
+    ntiles[vi] = count;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward.
+// ------------------------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
+    const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
+    const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ logits, const float* __restrict__ sh,
+    const uint32_t* __restrict__ ntiles, float* __restrict__ g2d, uint32_t grad_mask,
+    float* __restrict__ d_means, float* __restrict__ d_log_scales, float* __restrict__ d_quats,
+    float* __restrict__ d_logits, float* __restrict__ d_sh, float* __restrict__ pose_partial) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int kWarps = kPreThreads / 32;
+  __shared__ float red[kWarps][6];
+  const int i = blockIdx.x * kPreThreads + threadIdx.x;
+  const bool in_range = i < n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, shc[3 * K];
+  float logit = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) shc[k] = 0.0f;
+  if (in_range) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      m[k] = __ldg(means + 3 * (size_t)i + k);
+      ls[k] = __ldg(log_scales + 3 * (size_t)i + k);
+    }
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
+    q[0] = q4.x;
+    q[1] = q4.y;
+    q[2] = q4.z;
+    q[3] = q4.w;
+    logit = __ldg(logits + i);
+    load_sh<DEG>(sh, i, shc);
+  }
+  GaussianLocal g;
+  gaussian_local(m, ls, q, logit, g);
+
+  float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
+  float gsh[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0f;
+  bool any_visible = false;
+  // Gradient of Sigma^W summed over views (chained to scale / rotation once at the end).
+  float gSw[6] = {0, 0, 0, 0, 0, 0};  // xx, xy, xz, yy, yz, zz (symmetric, off-diagonals once)
+
+  for (int v = 0; v < views.n_views; ++v) {
+    const ViewParams& vp = views.v[v];
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    const size_t vi = (size_t)v * n + i;
+    if (in_range && ntiles[vi] > 0u) {
+      any_visible = true;
+      float* gp = g2d + vi * kG2Stride;
+      const float4 ga = *reinterpret_cast<const float4*>(gp);
+      const float4 gb = *reinterpret_cast<const float4*>(gp + 4);
+      const float2 gc = *reinterpret_cast<const float2*>(gp + 8);
+      // Consume: leave the accumulator zeroed for the next backward.
+      *reinterpret_cast<float4*>(gp) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(gp + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float2*>(gp + 8) = make_float2(0.f, 0.f);
+      const float g_mx = ga.x, g_my = ga.y, g_ca = ga.z, g_cb = ga.w;
+      const float g_cc = gb.x, g_op = gb.y, g_r = gb.z, g_g = gb.w;
+      const float g_b = gc.x, g_zo = gc.y;
+      ViewProj p;
+      project_view(g, vp, c, p);
+      const float* R = vp.R;
+      // Opacity.
+      glogit += g_op * g.opacity * (1.0f - g.opacity);
+      // Conic -> Sigma^I: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]].
+      const float a = p.conic[0], b = p.conic[1], cc = p.conic[2];
+      const float hb = 0.5f * g_cb;
+      const float P00 = a * g_ca + b * hb, P01 = a * hb + b * g_cc;
+      const float P10 = b * g_ca + cc * hb, P11 = b * hb + cc * g_cc;
+      const float GS00 = -(P00 * a + P01 * b);
+      const float GS01 = -(P00 * b + P01 * cc);
+      const float GS11 = -(P10 * b + P11 * cc);
+      // Sigma^I = T Sigma^W T^T: G_T = 2 G_S (T Sigma^W); G_SigmaW += T^T G_S T.
+      float GT[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        GT[k] = 2.0f * (GS00 * p.TS[k] + GS01 * p.TS[3 + k]);
+        GT[3 + k] = 2.0f * (GS01 * p.TS[k] + GS11 * p.TS[3 + k]);
+      }
+      {
+        // (T^T G_S T)_{ab} = sum_rs T_ra GS_rs T_sb.
+        float U[6];  // G_S T, row-major 2x3
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          U[k] = GS00 * p.T[k] + GS01 * p.T[3 + k];
+          U[3 + k] = GS01 * p.T[k] + GS11 * p.T[3 + k];
+        }
+        gSw[0] += p.T[0] * U[0] + p.T[3] * U[3];
+        gSw[1] += 2.0f * (p.T[0] * U[1] + p.T[3] * U[4]);
+        gSw[2] += 2.0f * (p.T[0] * U[2] + p.T[3] * U[5]);
+        gSw[3] += p.T[1] * U[1] + p.T[4] * U[4];
+        gSw[4] += 2.0f * (p.T[1] * U[2] + p.T[4] * U[5]);
+        gSw[5] += p.T[2] * U[2] + p.T[5] * U[5];
+      }
+      // T = J R: G_J = G_T R^T (all six entries, the structural zeros of J included).
+      float GJ[6];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          GJ[3 * r + k] = GT[3 * r] * R[3 * k] + GT[3 * r + 1] * R[3 * k + 1] +
+                          GT[3 * r + 2] * R[3 * k + 2];
+      // J(mu^C), with no gradient through a clamped x/z or y/z.
+      const float z = p.mc[2], rz = 1.0f / z, rz2 = rz * rz;
+      float g_z = -vp.fx * rz2 * GJ[0] - vp.fy * rz2 * GJ[4] + vp.fx * p.uc * rz2 * GJ[2] +
+                  vp.fy * p.wc * rz2 * GJ[5];
+      float g_u = p.u_cl ? 0.0f : -vp.fx * rz * GJ[2];
+      float g_w = p.w_cl ? 0.0f : -vp.fy * rz * GJ[5];
+      // mu^I = (fx u + cx, fy w + cy).
+      g_u += g_mx * vp.fx;
+      g_w += g_my * vp.fy;
+      // u = x/z, w = y/z; depth output z.
+      float gmc[3];
+      gmc[0] = g_u * rz;
+      gmc[1] = g_w * rz;
+      gmc[2] = g_z - (g_u * p.mc[0] + g_w * p.mc[1]) * rz2 + g_zo;
+      // mu^C = R mu^W + t.
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gm[k] += R[k] * gmc[0] + R[3 + k] * gmc[1] + R[6 + k] * gmc[2];
+      // Colour: rgb = max(sum_k sh_k Y_k(dir) + 0.5, 0), dir = normalize(mu^W - c_W).
+      float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
+            d2 = g.m[2] - vp.cam_center[2];
+      const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      d0 *= rn;
+      d1 *= rn;
+      d2 *= rn;
+      float Y[16];
+      sh_basis<DEG>(d0, d1, d2, Y);
+      float graw[3] = {g_r, g_g, g_b};
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc += shc[3 * k + ch] * Y[k];
+        if (!(acc > 0.0f)) graw[ch] = 0.0f;
+      }
+      float wk[16];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        gsh[3 * k + 0] += graw[0] * Y[k];
+        gsh[3 * k + 1] += graw[1] * Y[k];
+        gsh[3 * k + 2] += graw[2] * Y[k];
+        wk[k] = graw[0] * shc[3 * k] + graw[1] * shc[3 * k + 1] + graw[2] * shc[3 * k + 2];
+      }
+      float gd[3] = {0.0f, 0.0f, 0.0f};
+      if (DEG > 0) {
+        float gx, gy, gz;
+        sh_basis_vjp<DEG>(d0, d1, d2, wk, gx, gy, gz);
+        const float dd = gx * d0 + gy * d1 + gz * d2;
+        gd[0] = (gx - d0 * dd) * rn;
+        gd[1] = (gy - d1 * dd) * rn;
+        gd[2] = (gz - d2 * dd) * rn;
+        gm[0] += gd[0];
+        gm[1] += gd[1];
+        gm[2] += gd[2];
+      }
+      // Twist of the left update (Eq. leftupdate, Eq. muCjac, Eq. sigmaIjac):
+      //   rho   = dL/dmu^C + R dL/d(dir-vector)            (the camera centre moves with -R^T t)
+      //   omega = mu^C x dL/dmu^C + skew part of J^T G_J   (rotation of Sigma^I, dR = [w]_x R)
+      pose[0] = gmc[0] + R[0] * gd[0] + R[1] * gd[1] + R[2] * gd[2];
+      pose[1] = gmc[1] + R[3] * gd[0] + R[4] * gd[1] + R[5] * gd[2];
+      pose[2] = gmc[2] + R[6] * gd[0] + R[7] * gd[1] + R[8] * gd[2];
+      pose[3] = p.mc[1] * gmc[2] - p.mc[2] * gmc[1] + p.J02 * GJ[1] + p.J12 * GJ[4] - p.J11 * GJ[5];
+      pose[4] = p.mc[2] * gmc[0] - p.mc[0] * gmc[2] + p.J00 * GJ[2] - p.J02 * GJ[0] - p.J12 * GJ[3];
+      pose[5] = p.mc[0] * gmc[1] - p.mc[1] * gmc[0] + p.J11 * GJ[3] - p.J00 * GJ[1];
+    }
+    if (grad_mask & RGS_GRAD_POSE) {
+      // Block reduction of the view's twist gradient -> one partial per (block, view).
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float x = pose[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        pose[k] = x;
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[warp][k] = pose[k];
+      __syncthreads();
+      if (threadIdx.x < 6) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+        pose_partial[((size_t)blockIdx.x * views.n_views + v) * 6 + threadIdx.x] = s;
+      }
+      __syncthreads();
+    }
+  }
+  if (!in_range) return;
+  // A Gaussian culled in every view (behind the near plane, degenerate or non-finite) gets zero
+  // gradients; its local quantities may be non-finite and must not enter the chain below.
+  const bool need_cov = any_visible && (grad_mask & (RGS_GRAD_SCALES | RGS_GRAD_QUATS)) != 0;
+  if (need_cov) {
+    // Sigma^W = M M^T, M = Rq diag(s): G_M = 2 G_Sym M with G_Sym the symmetric matrix whose
+    // off-diagonal entries are half the accumulated off-diagonal gradients.
+    const float S00 = gSw[0], S01 = 0.5f * gSw[1], S02 = 0.5f * gSw[2];
+    const float S11 = gSw[3], S12 = 0.5f * gSw[4], S22 = gSw[5];
+    float GM[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      GM[k] = 2.0f * (S00 * g.M[k] + S01 * g.M[3 + k] + S02 * g.M[6 + k]);
+      GM[3 + k] = 2.0f * (S01 * g.M[k] + S11 * g.M[3 + k] + S12 * g.M[6 + k]);
+      GM[6 + k] = 2.0f * (S02 * g.M[k] + S12 * g.M[3 + k] + S22 * g.M[6 + k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      gls[k] = (GM[k] * g.Rq[k] + GM[3 + k] * g.Rq[3 + k] + GM[6 + k] * g.Rq[6 + k]) * g.s[k];
+    float G[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) G[3 * a + b] = GM[3 * a + b] * g.s[b];
+    const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+    const float gw = 2.0f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+    const float gx = 2.0f * (y * G[1] + z * G[2] + y * G[3] - 2.0f * x * G[4] - w * G[5] +
+                             z * G[6] + w * G[7] - 2.0f * x * G[8]);
+    const float gy = 2.0f * (-2.0f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] -
+                             w * G[6] + z * G[7] - 2.0f * y * G[8]);
+    const float gz = 2.0f * (-2.0f * z * G[0] - w * G[1] + x * G[2] + w * G[3] -
+                             2.0f * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+    // Normalisation q / |q|.
+    const float dot = gw * w + gx * x + gy * y + gz * z;
+    const float iq = 1.0f / g.qnorm;
+    gq[0] = (gw - w * dot) * iq;
+    gq[1] = (gx - x * dot) * iq;
+    gq[2] = (gy - y * dot) * iq;
+    gq[3] = (gz - z * dot) * iq;
+  }
+  if ((grad_mask & RGS_GRAD_MEANS) && d_means)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d_means[3 * (size_t)i + k] = gm[k];
+  if ((grad_mask & RGS_GRAD_SCALES) && d_log_scales)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d_log_scales[3 * (size_t)i + k] = gls[k];
+  if ((grad_mask & RGS_GRAD_QUATS) && d_quats)
+    reinterpret_cast<float4*>(d_quats)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+  if ((grad_mask & RGS_GRAD_OPACITY) && d_logits) d_logits[i] = glogit;
+  if ((grad_mask & RGS_GRAD_SH) && d_sh) {
+    float* p = d_sh + (size_t)i * 3 * K;
+    if ((3 * K) % 4 == 0) {
+#pragma unroll
+      for (int k = 0; k < 3 * K / 4; ++k)
+        reinterpret_cast<float4*>(p)[k] =
+            make_float4(gsh[4 * k], gsh[4 * k + 1], gsh[4 * k + 2], gsh[4 * k + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3 * K; ++k) p[k] = gsh[k];
+    }
+  }
+}
+
+// d_pose[v,k] = sum over blocks of the partials, in double precision.
+__global__ void pose_finalize_kernel(const float* __restrict__ partial, int n_blocks,
+                                     int n_views, float* __restrict__ d_pose) {
+  const int vk = blockIdx.x;  // v * 6 + k
+  double s = 0.0;
+  for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += (double)partial[(size_t)b * n_views * 6 + vk];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d_pose[vk] = (float)red[0];
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
+                                      const rgs_gaussians& g, float4* rec0, float4* rec1,
+                                      float4* rec2, uint32_t* ntiles, Counters* counters,
+                                      cudaStream_t stream) {
+  if (g.n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((g.n + kPreThreads - 1) / kPreThreads);
+#define RGS_PRE_FWD(D)                                                                     \
+  preprocess_forward_kernel<D><<<blocks, kPreThreads, 0, stream>>>(                        \
+      views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, rec0, rec1, rec2, \
+      ntiles, counters)
+  switch (g.sh_degree) {
+    case 0: RGS_PRE_FWD(0); break;
+    case 1: RGS_PRE_FWD(1); break;
+    case 2: RGS_PRE_FWD(2); break;
+    default: RGS_PRE_FWD(3); break;
+  }
+#undef RGS_PRE_FWD
+  return cudaGetLastError();
+}
+
+int preprocess_backward_blocks(int n) { return (n + kPreThreads - 1) / kPreThreads; }
+
+cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
+                                       const rgs_gaussians& g, const uint32_t* ntiles,
+                                       float* g2d, uint32_t grad_mask, float* d_means,
+                                       float* d_log_scales, float* d_quats, float* d_logits,
+                                       float* d_sh, float* pose_partial, float* d_pose,
+                                       cudaStream_t stream) {
+  const int blocks = preprocess_backward_blocks(g.n);
+  if (blocks > 0) {
+#define RGS_PRE_BWD(D)                                                                       \
+  preprocess_backward_kernel<D><<<blocks, kPreThreads, 0, stream>>>(                         \
+      views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, ntiles, g2d,   \
+      grad_mask, d_means, d_log_scales, d_quats, d_logits, d_sh, pose_partial)
+    switch (g.sh_degree) {
+      case 0: RGS_PRE_BWD(0); break;
+      case 1: RGS_PRE_BWD(1); break;
+      case 2: RGS_PRE_BWD(2); break;
+      default: RGS_PRE_BWD(3); break;
+    }
+#undef RGS_PRE_BWD
+  }
+  if ((grad_mask & RGS_GRAD_POSE) && d_pose) {
+    if (blocks > 0) {
+      pose_finalize_kernel<<<views.n_views * 6, 256, 0, stream>>>(pose_partial, blocks,
+                                                                  views.n_views, d_pose);
+    } else {
+      cudaError_t e = cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * views.n_views, stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rgs

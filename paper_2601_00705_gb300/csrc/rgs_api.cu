@@ -1,0 +1,663 @@
+// rgs_api.cu -- the C ABI (include/rgs.h): context, per-forward saved state, device memory,
+// and the launch sequence of the forward and backward passes.
+//
+// Forward launch sequence for a batch of V views (one launch per stage covers every view):
+//   1. preprocess      per Gaussian, all views: projected records + tile counts  (Eq. proj)
+//   2. compact         visible (view, Gaussian) entries with their depth keys
+//   3. depth sort      stable radix sort of the visible entries by float32 depth
+//   4. offsets         exclusive scan of tile counts in depth order
+//   5. duplicate       one (tile, vi) pair per touched tile, emitted in depth order
+//   6. tile sort       stable radix sort of the pairs by global tile id; stability keeps each
+//                      tile's run in (depth, index) order
+//   7. ranges          [first, last + 1) of each tile's run
+//   8. blend           front-to-back compositing per tile                          (Eq. alpha)
+// Backward: backward blend (screen-space gradients) then backward preprocess (parameter and
+// twist gradients, Eq. muCjac / muIjac / sigmaIjac) and the twist reduction.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "rgs_internal.cuh"
+
+namespace rgs {
+cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
+                                      const rgs_gaussians& g, float4* rec0, float4* rec1,
+                                      float4* rec2, uint32_t* ntiles, Counters* counters,
+                                      cudaStream_t stream);
+int preprocess_backward_blocks(int n);
+cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
+                                       const rgs_gaussians& g, const uint32_t* ntiles,
+                                       float* g2d, uint32_t grad_mask, float* d_means,
+                                       float* d_log_scales, float* d_quats, float* d_logits,
+                                       float* d_sh, float* pose_partial, float* d_pose,
+                                       cudaStream_t stream);
+cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
+                             const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
+                             const float4* rec1, int64_t visible_cap, uint32_t capacity,
+                             uint32_t* keys, uint32_t* vals, Counters* counters,
+                             cudaStream_t stream);
+cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
+                               int total_tiles, uint32_t capacity, cudaStream_t stream);
+cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, const uint2* ranges,
+                         const uint32_t* pair_vals, const float4* rec0, const float4* rec1,
+                         const float4* rec2, float* color, float* depth, float* alpha,
+                         float* t_final, int32_t* last_index, const float* d_color,
+                         const float* d_depth, const float* d_alpha, float* g2d,
+                         Counters* counters, cudaStream_t stream);
+}  // namespace rgs
+
+using namespace rgs;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// A device allocation carved into aligned sub-buffers.
+struct Region {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+struct State {
+  // Inputs of the last forward (the backward reuses them).
+  rgs_gaussians g{};
+  Views views{};
+  Consts consts{};
+  int64_t vn = 0;            // n_views * n
+  bool has_forward = false;
+
+  // Capacities and regions.
+  int64_t vn_cap = 0, pix_cap = 0, tile_cap = 0, pair_cap = 0, pose_cap = 0;
+  Region r_vn, r_pix, r_tile, r_pair, r_scratch, r_pose, r_counters;
+
+  // Per (view, Gaussian).
+  float4 *rec0 = nullptr, *rec1 = nullptr, *rec2 = nullptr;
+  uint32_t* ntiles = nullptr;
+  uint32_t *vis_keys[2] = {nullptr, nullptr}, *vis_vals[2] = {nullptr, nullptr};
+  uint32_t* offsets = nullptr;
+  float* g2d = nullptr;
+  const uint32_t* order = nullptr;  // depth-sorted visible entries (one of vis_vals)
+  // Per pixel / tile / pair.
+  float* t_final = nullptr;
+  int32_t* last_index = nullptr;
+  uint2* ranges = nullptr;
+  uint32_t *pair_keys[2] = {nullptr, nullptr}, *pair_vals[2] = {nullptr, nullptr};
+  const uint32_t* sorted_vals = nullptr;
+  // Scratch.
+  uint32_t* hist = nullptr;
+  uint32_t* block_sums = nullptr;
+  int64_t hist_cap = 0, sums_cap = 0;
+  float* pose_partial = nullptr;
+  Counters* counters = nullptr;
+};
+
+}  // namespace
+
+struct rgs_ctx {
+  int device = 0;
+  std::string last_error;
+  std::map<uint64_t, State*> states;
+  uint64_t next_id = 1;
+  Counters* host_counters = nullptr;  // pinned
+};
+
+namespace {
+
+rgs_status fail(rgs_ctx* ctx, rgs_status s, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return s;
+}
+
+rgs_status cuda_fail(rgs_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? RGS_ERR_NOMEM : RGS_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RGS_CUDA(call, where)                                \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+  } while (0)
+
+void free_region(Region& r) {
+  if (r.base) cudaFree(r.base);
+  r.base = nullptr;
+  r.bytes = 0;
+}
+
+cudaError_t alloc_region(Region& r, size_t bytes) {
+  free_region(r);
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&r.base, bytes);
+  if (e != cudaSuccess) {
+    r.base = nullptr;
+    return e;
+  }
+  r.bytes = bytes;
+  return cudaSuccess;
+}
+
+template <typename T>
+T* carve(char*& p, int64_t count) {
+  T* out = reinterpret_cast<T*>(p);
+  p += align_up(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+  return out;
+}
+
+bool is_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Scratch for the scans and sorts of up to `items` elements.
+rgs_status ensure_scratch(rgs_ctx* ctx, State& s, int64_t items, bool capturing) {
+  const int64_t hist = sort_hist_entries(std::max<int64_t>(items, 1));
+  const int64_t sums = std::max(scan_blocks(hist), scan_blocks(std::max<int64_t>(items, 1))) + 1;
+  if (hist <= s.hist_cap && sums <= s.sums_cap) return RGS_OK;
+  if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "scratch too small during stream capture");
+  RGS_CUDA(cudaDeviceSynchronize(), "sync before scratch growth");
+  const size_t bytes = align_up(sizeof(uint32_t) * hist) + align_up(sizeof(uint32_t) * sums);
+  RGS_CUDA(alloc_region(s.r_scratch, bytes), "allocate sort scratch");
+  char* p = static_cast<char*>(s.r_scratch.base);
+  s.hist = carve<uint32_t>(p, hist);
+  s.block_sums = carve<uint32_t>(p, sums);
+  s.hist_cap = hist;
+  s.sums_cap = sums;
+  return RGS_OK;
+}
+
+rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t pose_entries, bool capturing,
+                     cudaStream_t stream) {
+  if (vn > s.vn_cap) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "per-Gaussian buffers grow during capture");
+    RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
+    const int64_t cap = vn;
+    size_t bytes = 3 * align_up(sizeof(float4) * cap) + 6 * align_up(sizeof(uint32_t) * cap) +
+                   align_up(sizeof(float) * kG2Stride * cap);
+    RGS_CUDA(alloc_region(s.r_vn, bytes), "allocate per-Gaussian buffers");
+    char* p = static_cast<char*>(s.r_vn.base);
+    s.rec0 = carve<float4>(p, cap);
+    s.rec1 = carve<float4>(p, cap);
+    s.rec2 = carve<float4>(p, cap);
+    s.ntiles = carve<uint32_t>(p, cap);
+    s.vis_keys[0] = carve<uint32_t>(p, cap);
+    s.vis_keys[1] = carve<uint32_t>(p, cap);
+    s.vis_vals[0] = carve<uint32_t>(p, cap);
+    s.vis_vals[1] = carve<uint32_t>(p, cap);
+    s.offsets = carve<uint32_t>(p, cap);
+    s.g2d = carve<float>(p, kG2Stride * cap);
+    // The screen-space gradient accumulators start at zero; every backward leaves them zero.
+    RGS_CUDA(cudaMemsetAsync(s.g2d, 0, sizeof(float) * kG2Stride * cap, stream), "zero g2d");
+    s.vn_cap = cap;
+  }
+  if (pose_entries > s.pose_cap) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "pose buffers grow during capture");
+    RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
+    RGS_CUDA(alloc_region(s.r_pose, sizeof(float) * pose_entries), "allocate pose partials");
+    s.pose_partial = static_cast<float*>(s.r_pose.base);
+    s.pose_cap = pose_entries;
+  }
+  return RGS_OK;
+}
+
+rgs_status ensure_pix_tiles(rgs_ctx* ctx, State& s, int64_t pixels, int64_t tiles,
+                            bool capturing) {
+  if (pixels > s.pix_cap) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "pixel buffers grow during capture");
+    RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
+    RGS_CUDA(alloc_region(s.r_pix, align_up(sizeof(float) * pixels) +
+                                        align_up(sizeof(int32_t) * pixels)),
+             "allocate pixel state");
+    char* p = static_cast<char*>(s.r_pix.base);
+    s.t_final = carve<float>(p, pixels);
+    s.last_index = carve<int32_t>(p, pixels);
+    s.pix_cap = pixels;
+  }
+  if (tiles > s.tile_cap) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "tile buffers grow during capture");
+    RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
+    RGS_CUDA(alloc_region(s.r_tile, sizeof(uint2) * tiles), "allocate tile ranges");
+    s.ranges = static_cast<uint2*>(s.r_tile.base);
+    s.tile_cap = tiles;
+  }
+  return RGS_OK;
+}
+
+rgs_status ensure_pairs(rgs_ctx* ctx, State& s, int64_t pairs) {
+  if (pairs <= s.pair_cap) return RGS_OK;
+  RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
+  const int64_t cap = std::max<int64_t>(pairs + pairs / 4, 4096);
+  if (cap >= (int64_t)UINT32_MAX) return fail(ctx, RGS_ERR_INVALID_ARG, "pair list exceeds 2^32");
+  RGS_CUDA(alloc_region(s.r_pair, 4 * align_up(sizeof(uint32_t) * cap)), "allocate pair lists");
+  char* p = static_cast<char*>(s.r_pair.base);
+  s.pair_keys[0] = carve<uint32_t>(p, cap);
+  s.pair_keys[1] = carve<uint32_t>(p, cap);
+  s.pair_vals[0] = carve<uint32_t>(p, cap);
+  s.pair_vals[1] = carve<uint32_t>(p, cap);
+  s.pair_cap = cap;
+  return RGS_OK;
+}
+
+State* find_state(rgs_ctx* ctx, uint64_t id) {
+  auto it = ctx->states.find(id);
+  return it == ctx->states.end() ? nullptr : it->second;
+}
+
+rgs_status get_or_create_state(rgs_ctx* ctx, uint64_t* handle, State** out) {
+  if (!handle) return fail(ctx, RGS_ERR_INVALID_ARG, "state handle pointer is null");
+  if (*handle == 0) {
+    State* s = new State();
+    const uint64_t id = ctx->next_id++;
+    ctx->states[id] = s;
+    *handle = id;
+    *out = s;
+    return RGS_OK;
+  }
+  State* s = find_state(ctx, *handle);
+  if (!s) return fail(ctx, RGS_ERR_STATE, "unknown state handle");
+  *out = s;
+  return RGS_OK;
+}
+
+void destroy_state(State* s) {
+  free_region(s->r_vn);
+  free_region(s->r_pix);
+  free_region(s->r_tile);
+  free_region(s->r_pair);
+  free_region(s->r_scratch);
+  free_region(s->r_pose);
+  free_region(s->r_counters);
+  delete s;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const rgs_config& cfg,
+                       Views& views, Consts& consts) {
+  if (!cams) return fail(ctx, RGS_ERR_INVALID_ARG, "cams is null");
+  if (n_views < 1 || n_views > kMaxViews)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n_views must be in 1..RGS_MAX_VIEWS");
+  const int tw = cfg.tile_w, th = cfg.tile_h;
+  if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8)))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "tile shape must be 16x16, 8x8 or 32x8");
+  std::memset(&views, 0, sizeof(views));
+  views.n_views = n_views;
+  views.tile_w = tw;
+  views.tile_h = th;
+  long long pix = 0;
+  long long tiles = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const rgs_camera& c = cams[v];
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+      return fail(ctx, RGS_ERR_INVALID_ARG, "camera size out of range");
+    if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !std::isfinite(c.cx) || !std::isfinite(c.cy))
+      return fail(ctx, RGS_ERR_INVALID_ARG, "camera intrinsics invalid");
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(c.world_to_cam[k]))
+        return fail(ctx, RGS_ERR_INVALID_ARG, "camera pose is not finite");
+    ViewParams& vp = views.v[v];
+    vp.width = c.width;
+    vp.height = c.height;
+    vp.tiles_x = (c.width + tw - 1) / tw;
+    vp.tiles_y = (c.height + th - 1) / th;
+    vp.tile_base = (int)tiles;
+    vp.pixel_offset = pix;
+    vp.fx = c.fx;
+    vp.fy = c.fy;
+    vp.cx = c.cx;
+    vp.cy = c.cy;
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) vp.R[3 * a + b] = c.world_to_cam[4 * a + b];
+      vp.t[a] = c.world_to_cam[4 * a + 3];
+    }
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < 3; ++b) s -= (double)vp.R[3 * b + a] * (double)vp.t[b];
+      vp.cam_center[a] = (float)s;
+    }
+    if (cfg.jac_clamp > 0.0f) {
+      vp.lim_u = (float)((double)cfg.jac_clamp * 0.5 * c.width / c.fx);
+      vp.lim_w = (float)((double)cfg.jac_clamp * 0.5 * c.height / c.fy);
+    } else {
+      vp.lim_u = vp.lim_w = 0.0f;
+    }
+    tiles += (long long)vp.tiles_x * vp.tiles_y;
+    pix += (long long)c.width * c.height;
+  }
+  if (tiles >= (1ll << 31) || pix >= (1ll << 31))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "too many pixels or tiles in one batch");
+  views.total_tiles = (int)tiles;
+  views.total_pixels = pix;
+  consts.alpha_min = cfg.alpha_min;
+  consts.alpha_max = cfg.alpha_max;
+  consts.t_min = cfg.t_min;
+  consts.znear = cfg.znear;
+  consts.eps2d = cfg.eps2d;
+  for (int k = 0; k < 3; ++k) consts.bg[k] = cfg.bg[k];
+  if (!(cfg.alpha_min > 0.0f) || !(cfg.alpha_max > cfg.alpha_min) || !(cfg.alpha_max < 1.0f) ||
+      !(cfg.t_min > 0.0f) || !(cfg.eps2d >= 0.0f) || !(cfg.znear > 0.0f) ||
+      !std::isfinite(cfg.znear))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "config values out of range");
+  return RGS_OK;
+}
+
+int bits_for(uint32_t count) {  // bits needed to represent values in [0, count)
+  int b = 0;
+  while (b < 32 && (count - 1) >> b) ++b;
+  return std::max(b, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+void rgs_config_default(rgs_config* cfg) {
+  if (!cfg) return;
+  cfg->alpha_min = 1.0f / 255.0f;
+  cfg->alpha_max = 0.99f;
+  cfg->t_min = 1e-4f;
+  cfg->znear = 0.2f;
+  cfg->eps2d = 0.3f;
+  cfg->jac_clamp = 1.3f;
+  cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
+  cfg->tile_w = 16;
+  cfg->tile_h = 16;
+}
+
+rgs_status rgs_create(rgs_ctx** out, int device) {
+  if (!out) return RGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return RGS_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return RGS_ERR_CUDA;
+  rgs_ctx* ctx = new rgs_ctx();
+  ctx->device = device;
+  if (cudaMallocHost(&ctx->host_counters, sizeof(Counters)) != cudaSuccess) {
+    delete ctx;
+    return RGS_ERR_NOMEM;
+  }
+  *out = ctx;
+  return RGS_OK;
+}
+
+void rgs_destroy(rgs_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->states) destroy_state(kv.second);
+  ctx->states.clear();
+  if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
+  delete ctx;
+}
+
+const char* rgs_last_error(const rgs_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+rgs_status rgs_release_state(rgs_ctx* ctx, uint64_t handle) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  State* s = find_state(ctx, handle);
+  if (!s) return fail(ctx, RGS_ERR_STATE, "unknown state handle");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();  // queued work may still read the state's buffers
+  destroy_state(s);
+  ctx->states.erase(handle);
+  return RGS_OK;
+}
+
+rgs_status rgs_reserve(rgs_ctx* ctx, uint64_t* handle, int64_t pair_capacity, void* stream) {
+  (void)stream;
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  State* s = nullptr;
+  rgs_status st = get_or_create_state(ctx, handle, &s);
+  if (st != RGS_OK) return st;
+  cudaSetDevice(ctx->device);
+  if (pair_capacity > 0) {
+    st = ensure_pairs(ctx, *s, pair_capacity);
+    if (st != RGS_OK) return st;
+    st = ensure_scratch(ctx, *s, std::max<int64_t>(s->pair_cap, s->vn_cap), false);
+    if (st != RGS_OK) return st;
+  }
+  return RGS_OK;
+}
+
+rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                              int32_t n_views, const rgs_config* cfg_in, rgs_images* out,
+                              uint64_t* handle, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  if (!g || !out) return fail(ctx, RGS_ERR_INVALID_ARG, "null gaussians or output struct");
+  if (g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n must be >= 0 and sh_degree in 0..3");
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null Gaussian parameter pointer");
+  if (g->n > 0 && (!aligned16(g->means) || !aligned16(g->log_scales) || !aligned16(g->quats) ||
+                   !aligned16(g->opacity_logits) || !aligned16(g->sh)))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "Gaussian parameter pointers must be 16-byte aligned");
+  if (!out->color || !out->depth || !out->alpha)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null output image pointer");
+  rgs_config cfg;
+  if (cfg_in) cfg = *cfg_in; else rgs_config_default(&cfg);
+  Views views;
+  Consts consts;
+  rgs_status st = build_views(ctx, cams, n_views, cfg, views, consts);
+  if (st != RGS_OK) return st;
+  const int64_t vn = (int64_t)n_views * g->n;
+  if (vn >= (1ll << 31)) return fail(ctx, RGS_ERR_INVALID_ARG, "n_views * n must be < 2^31");
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  const bool capturing = is_capturing(stream);
+  State* s = nullptr;
+  st = get_or_create_state(ctx, handle, &s);
+  if (st != RGS_OK) return st;
+  s->has_forward = false;
+  const int64_t pose_entries = (int64_t)preprocess_backward_blocks(g->n) * n_views * 6;
+  st = ensure_vn(ctx, *s, vn, pose_entries, capturing, stream);
+  if (st != RGS_OK) return st;
+  st = ensure_pix_tiles(ctx, *s, views.total_pixels, views.total_tiles, capturing);
+  if (st != RGS_OK) return st;
+  st = ensure_scratch(ctx, *s, std::max<int64_t>(vn, s->pair_cap), capturing);
+  if (st != RGS_OK) return st;
+  if (!s->r_counters.base) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "state must be created outside capture");
+    RGS_CUDA(alloc_region(s->r_counters, sizeof(Counters)), "allocate counters");
+    s->counters = static_cast<Counters*>(s->r_counters.base);
+  }
+  s->g = *g;
+  s->views = views;
+  s->consts = consts;
+  s->vn = vn;
+  Counters* cnt = s->counters;
+  RGS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), stream), "reset counters");
+
+  // 1. Projection.
+  RGS_CUDA(launch_preprocess_forward(views, consts, *g, s->rec0, s->rec1, s->rec2, s->ntiles, cnt,
+                                     stream),
+           "preprocess");
+  // 2. Visible entries with depth keys, in (view, Gaussian) order.
+  RGS_CUDA(launch_compact_visible(s->ntiles, s->rec0, vn, s->vis_keys[0], s->vis_vals[0],
+                                  &cnt->n_visible, s->block_sums, stream),
+           "compact");
+  // 3. Stable sort by depth (positive float bits order like the values; the sign bit is 0).
+  bool alt = false;
+  RGS_CUDA(launch_radix_sort(s->vis_keys[0], s->vis_vals[0], s->vis_keys[1], s->vis_vals[1], vn,
+                             &cnt->n_visible, 0, 31, s->hist, s->block_sums, &alt, stream),
+           "depth sort");
+  s->order = s->vis_vals[alt ? 1 : 0];
+  // 4. Pair offsets in depth order.
+  RGS_CUDA(launch_gather_scan(s->ntiles, s->order, vn, &cnt->n_visible, s->offsets,
+                              &cnt->n_pairs, s->block_sums, stream),
+           "pair offsets");
+  // Size the pair list (outside capture: read the count back and grow if needed).
+  int64_t pair_bound = s->pair_cap;
+  if (!capturing) {
+    RGS_CUDA(cudaMemcpyAsync(ctx->host_counters, cnt, sizeof(Counters), cudaMemcpyDeviceToHost,
+                             stream),
+             "read counters");
+    RGS_CUDA(cudaStreamSynchronize(stream), "sync for pair count");
+    const int64_t pairs = ctx->host_counters->n_pairs;
+    st = ensure_pairs(ctx, *s, pairs);
+    if (st != RGS_OK) return st;
+    st = ensure_scratch(ctx, *s, std::max<int64_t>(vn, s->pair_cap), false);
+    if (st != RGS_OK) return st;
+    pair_bound = pairs;
+  } else if (s->pair_cap == 0) {
+    return fail(ctx, RGS_ERR_CAPACITY, "pair list has no capacity under capture: rgs_reserve");
+  }
+  const uint32_t capacity = (uint32_t)s->pair_cap;
+  // 5. Duplicate (tile, vi) pairs in depth order.
+  RGS_CUDA(launch_duplicate(views, g->n, s->order, s->offsets, s->ntiles, s->rec0, s->rec1, vn,
+                            capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
+           "duplicate");
+  // 6. Stable sort by global tile id.
+  alt = false;
+  // Keys are tile ids in [0, total_tiles]; total_tiles itself marks an unused slot.
+  const int tile_bits = bits_for((uint32_t)views.total_tiles + 1u);
+  RGS_CUDA(launch_radix_sort(s->pair_keys[0], s->pair_vals[0], s->pair_keys[1], s->pair_vals[1],
+                             std::min<int64_t>(pair_bound, s->pair_cap), &cnt->n_pairs_stored, 0,
+                             tile_bits, s->hist, s->block_sums, &alt, stream),
+           "tile sort");
+  const uint32_t* sorted_keys = s->pair_keys[alt ? 1 : 0];
+  s->sorted_vals = s->pair_vals[alt ? 1 : 0];
+  // 7. Tile ranges.
+  RGS_CUDA(launch_tile_ranges(sorted_keys, cnt, s->ranges, views.total_tiles,
+                              (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), stream),
+           "tile ranges");
+  // 8. Blend.
+  RGS_CUDA(launch_blend(true, views, consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
+                        s->rec2, out->color, out->depth, out->alpha, s->t_final, s->last_index,
+                        nullptr, nullptr, nullptr, nullptr, cnt, stream),
+           "blend forward");
+  s->has_forward = true;
+  return RGS_OK;
+}
+
+rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads* grads,
+                               uint32_t grad_mask, float* d_means, float* d_log_scales,
+                               float* d_quats, float* d_opacity_logits, float* d_sh,
+                               float* d_pose, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  State* s = find_state(ctx, handle);
+  if (!s) return fail(ctx, RGS_ERR_STATE, "unknown state handle");
+  if (!s->has_forward) return fail(ctx, RGS_ERR_STATE, "state holds no completed forward");
+  if (grad_mask & ~RGS_GRAD_ALL) return fail(ctx, RGS_ERR_INVALID_ARG, "unknown grad_mask bits");
+  const int n = s->g.n;
+  struct Need { uint32_t bit; const void* p; const char* name; bool vec4; };
+  const Need needs[] = {{RGS_GRAD_MEANS, d_means, "d_means", false},
+                        {RGS_GRAD_SCALES, d_log_scales, "d_log_scales", false},
+                        {RGS_GRAD_QUATS, d_quats, "d_quats", true},
+                        {RGS_GRAD_OPACITY, d_opacity_logits, "d_opacity_logits", false},
+                        {RGS_GRAD_SH, d_sh, "d_sh", true},
+                        {RGS_GRAD_POSE, d_pose, "d_pose", false}};
+  for (const Need& nd : needs) {
+    if (!(grad_mask & nd.bit)) continue;
+    if (!nd.p && (n > 0 || nd.bit == RGS_GRAD_POSE))
+      return fail(ctx, RGS_ERR_INVALID_ARG, std::string(nd.name) + " is null but requested");
+    if (nd.p && nd.vec4 && !aligned16(nd.p))
+      return fail(ctx, RGS_ERR_INVALID_ARG, std::string(nd.name) + " must be 16-byte aligned");
+  }
+  const float* dc = grads ? grads->d_color : nullptr;
+  const float* dd = grads ? grads->d_depth : nullptr;
+  const float* da = grads ? grads->d_alpha : nullptr;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_blend(false, s->views, s->consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
+                        s->rec2, nullptr, nullptr, nullptr, s->t_final, s->last_index, dc, dd, da,
+                        s->g2d, s->counters, stream),
+           "blend backward");
+  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->ntiles, s->g2d, grad_mask,
+                                      d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+                                      s->pose_partial, d_pose, stream),
+           "preprocess backward");
+  return RGS_OK;
+}
+
+rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t handle, rgs_stats* out, void* stream_ptr) {
+  if (!ctx || !out) return RGS_ERR_INVALID_ARG;
+  State* s = find_state(ctx, handle);
+  if (!s) return fail(ctx, RGS_ERR_STATE, "unknown state handle");
+  std::memset(out, 0, sizeof(*out));
+  out->pair_capacity = s->pair_cap;
+  out->state_bytes = (int64_t)(s->r_vn.bytes + s->r_pix.bytes + s->r_tile.bytes +
+                               s->r_pair.bytes + s->r_scratch.bytes + s->r_pose.bytes +
+                               s->r_counters.bytes);
+  if (!s->counters) return RGS_OK;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  cudaSetDevice(ctx->device);
+  RGS_CUDA(cudaMemcpyAsync(ctx->host_counters, s->counters, sizeof(Counters),
+                           cudaMemcpyDeviceToHost, stream),
+           "read counters");
+  RGS_CUDA(cudaStreamSynchronize(stream), "sync for stats");
+  const Counters& c = *ctx->host_counters;
+  out->n_visible = c.n_visible;
+  out->n_pairs = c.n_pairs;
+  out->n_eval = (int64_t)c.n_eval;
+  out->n_nonfinite = c.n_nonfinite;
+  out->status = c.status;
+  return RGS_OK;
+}
+
+rgs_status rgs_radix_sort_u32(rgs_ctx* ctx, uint32_t* keys, uint32_t* vals, int64_t n,
+                              int32_t begin_bit, int32_t end_bit, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n < 0 || n >= (1ll << 31) || (n > 0 && !keys) || begin_bit < 0 || end_bit > 32 ||
+      begin_bit >= end_bit)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "bad sort arguments");
+  if (n == 0) return RGS_OK;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  cudaSetDevice(ctx->device);
+  const int64_t hist = sort_hist_entries(n);
+  const int64_t sums = std::max(scan_blocks(hist), scan_blocks(n)) + 1;
+  char* base = nullptr;
+  const size_t bytes = 2 * align_up(sizeof(uint32_t) * n) + align_up(sizeof(uint32_t) * hist) +
+                       align_up(sizeof(uint32_t) * sums);
+  RGS_CUDA(cudaMalloc(&base, bytes), "allocate sort scratch");
+  char* p = base;
+  uint32_t* kalt = carve<uint32_t>(p, n);
+  uint32_t* valt = carve<uint32_t>(p, n);
+  uint32_t* h = carve<uint32_t>(p, hist);
+  uint32_t* bs = carve<uint32_t>(p, sums);
+  bool alt = false;
+  cudaError_t e = launch_radix_sort(keys, vals, kalt, vals ? valt : nullptr, n, nullptr,
+                                    begin_bit, end_bit, h, bs, &alt, stream);
+  if (e == cudaSuccess && alt) {
+    e = cudaMemcpyAsync(keys, kalt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && vals)
+      e = cudaMemcpyAsync(vals, valt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(stream);
+  cudaFree(base);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "radix sort");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "radix sort sync");
+  return RGS_OK;
+}
+
+rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
+                                  uint32_t* total_out, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n < 0 || n >= (1ll << 31) || (n > 0 && (!in || !out)))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "bad scan arguments");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  cudaSetDevice(ctx->device);
+  const int64_t sums = scan_blocks(n) + 1;
+  uint32_t* bs = nullptr;
+  RGS_CUDA(cudaMalloc(&bs, sizeof(uint32_t) * sums), "allocate scan scratch");
+  cudaError_t e = launch_exclusive_scan(in, out, n, nullptr, total_out, bs, stream);
+  cudaError_t e2 = cudaStreamSynchronize(stream);
+  cudaFree(bs);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "scan sync");
+  return RGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// rgs_internal.cuh -- shared declarations and device helpers of the sm_103a rasterizer.
+//
+// Layout in HBM (V views, N Gaussians, "vi" = v * N + i):
+//   rec0[vi] = (mean2d.x, mean2d.y, opacity, depth z)      float4
+//   rec1[vi] = (conic a, conic b, conic c, kappa)          float4, kappa = 2 ln(o / alpha_min)
+//   rec2[vi] = (r, g, b, 0)                                float4
+//   ntiles[vi]: tiles touched (0 = culled / invisible)
+//   g2d[vi * 12 + s]: screen-space gradient slots (mean2d x/y, conic a/b/c, opacity, rgb, z)
+//   pair list: key = global tile id, value = vi; sorted so that each tile's run is in
+//              (depth, index) order; ranges[gtile] = [first, last + 1) of the run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rgs.h"
+
+namespace rgs {
+
+constexpr int kMaxViews = RGS_MAX_VIEWS;
+constexpr int kG2Stride = 12;  // floats per (view, Gaussian) screen-space gradient record
+
+// Screen-space gradient slots.
+enum G2Slot { kGMx = 0, kGMy, kGCa, kGCb, kGCc, kGOp, kGR, kGG, kGB, kGZ };
+
+struct ViewParams {
+  int width, height;
+  int tiles_x, tiles_y;
+  int tile_base;            // first global tile id of this view
+  int pad0;
+  long long pixel_offset;   // first pixel of this view in the concatenated images
+  float fx, fy, cx, cy;
+  float R[9];               // world-to-camera rotation, row-major
+  float t[3];
+  float cam_center[3];      // -R^T t
+  float lim_u, lim_w;       // guard band of x/z and y/z used by the projection Jacobian
+};
+
+// Every kernel receives the views by value (a __grid_constant__ parameter block), so a captured
+// CUDA graph carries its own camera data and no host-to-device copy is needed per call.
+struct Views {
+  int n_views;
+  int total_tiles;
+  long long total_pixels;
+  int tile_w, tile_h;
+  ViewParams v[kMaxViews];
+};
+
+struct Consts {
+  float alpha_min, alpha_max, t_min, znear, eps2d;
+  float bg[3];
+};
+
+// Device status bits.
+enum StatusBits : uint32_t { kStatusPairOverflow = 1u };
+
+// Device counters of one forward.
+struct Counters {
+  uint32_t n_visible;       // compacted (view, Gaussian) entries
+  uint32_t n_pairs;         // duplicated pairs
+  uint32_t n_pairs_stored;  // min(n_pairs, capacity)
+  uint32_t status;
+  uint32_t n_nonfinite;
+  uint32_t pad[3];
+  unsigned long long n_eval;
+};
+
+// ------------------------------------------------------------------------------------------
+// Small device helpers.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int view_of_tile(const Views& views, int gtile) {
+  int lo = 0, hi = views.n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (views.v[mid].tile_base <= gtile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Error-free product and sum (Dekker / Knuth) used by the compensated dot product below.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// r . m + t with the compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci.
+// Comput. 26(6), 2005): as accurate as evaluation in twice the working precision, then rounded
+// once. The camera-space depth computed this way is the float32 rounding of the exact value, so
+// the near-to-far sort key does not depend on the order of the floating-point operations.
+__device__ __forceinline__ float dot3_plus_accurate(float r0, float r1, float r2, float m0,
+                                                    float m1, float m2, float t) {
+  float p, s, h, e, q;
+  two_prod(r0, m0, p, s);
+  two_prod(r1, m1, h, e);
+  two_sum(p, h, p, q);
+  s = __fadd_rn(s, __fadd_rn(q, e));
+  two_prod(r2, m2, h, e);
+  two_sum(p, h, p, q);
+  s = __fadd_rn(s, __fadd_rn(q, e));
+  two_sum(p, t, p, q);
+  s = __fadd_rn(s, q);
+  return __fadd_rn(p, s);
+}
+
+// Exponent of the 2D Gaussian at offset d = p - mu^I: -1/2 (a dx^2 + c dy^2) - b dx dy.
+// Every operation is explicitly rounded so that the forward and backward blends reproduce the
+// same alpha bit for bit (the backward must re-take the forward's coverage decisions).
+__device__ __forceinline__ float gauss_power(float dx, float dy, float a, float b, float c) {
+  float q = __fmul_rn(a, __fmul_rn(dx, dx));
+  q = __fmaf_rn(c, __fmul_rn(dy, dy), q);
+  q = __fmaf_rn(__fmul_rn(2.0f, b), __fmul_rn(dx, dy), q);
+  return __fmul_rn(-0.5f, q);
+}
+
+// o * exp(power), explicitly rounded (see gauss_power).
+__device__ __forceinline__ float gauss_alpha_raw(float o, float power) {
+  return __fmul_rn(o, __expf(power));
+}
+
+// ------------------------------------------------------------------------------------------
+// Tile coverage of a projected Gaussian: the tiles whose pixel centres may lie inside the
+// alpha >= alpha_min ellipse {d : d^T Q d <= kappa} (Q = conic), padded by kTilePad pixels so
+// that the per-pixel FP32 test in the blend can never find a covered pixel outside the listed
+// tiles. Visits tile rows ty0..ty1 and, per row, the column span [tx0, tx1] of the ellipse
+// restricted to the row's pixel band.
+// ------------------------------------------------------------------------------------------
+constexpr float kTilePad = 1.0f;
+
+struct Ellipse {
+  float mx, my;           // centre
+  float sxx, sxy, syy;    // covariance Q^-1
+  float kappa;
+};
+
+__device__ __forceinline__ bool make_ellipse(float4 r0, float4 r1, Ellipse& e) {
+  const float a = r1.x, b = r1.y, c = r1.z;
+  const float detq = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+  if (!(detq > 0.0f) || !(r1.w >= 0.0f)) return false;
+  e.mx = r0.x;
+  e.my = r0.y;
+  e.sxx = __fdiv_rn(c, detq);
+  e.sxy = __fdiv_rn(-b, detq);
+  e.syy = __fdiv_rn(a, detq);
+  e.kappa = r1.w;
+  return true;
+}
+
+// Every operation below is explicitly rounded (no contraction), so the counting pass in the
+// preprocess and the emitting pass in the duplication visit exactly the same tiles.
+template <typename RowFn>
+__device__ __forceinline__ void for_each_tile_row(const Ellipse& e, int tile_w, int tile_h,
+                                                  int tiles_x, int tiles_y, RowFn&& fn) {
+  const float kap = __fadd_rn(__fmul_rn(e.kappa, 1.0001f), 1e-6f);
+  const float rx = __fsqrt_rn(__fmul_rn(kap, e.sxx));
+  const float ry = __fsqrt_rn(__fmul_rn(kap, e.syy));
+  const float y_lo = __fsub_rn(__fsub_rn(e.my, ry), kTilePad);
+  const float y_hi = __fadd_rn(__fadd_rn(e.my, ry), kTilePad);
+  const float x_lo = __fsub_rn(__fsub_rn(e.mx, rx), kTilePad);
+  const float x_hi = __fadd_rn(__fadd_rn(e.mx, rx), kTilePad);
+  const float tw = (float)tile_w, th = (float)tile_h;
+  // Clamp before converting to int: the extents of near-degenerate Gaussians can be huge.
+  const float fty0 = floorf(fminf(fmaxf(__fdiv_rn(y_lo, th), -1.0f), (float)tiles_y));
+  const float fty1 = floorf(fminf(fmaxf(__fdiv_rn(y_hi, th), -1.0f), (float)tiles_y));
+  const float ftx0 = floorf(fminf(fmaxf(__fdiv_rn(x_lo, tw), -1.0f), (float)tiles_x));
+  const float ftx1 = floorf(fminf(fmaxf(__fdiv_rn(x_hi, tw), -1.0f), (float)tiles_x));
+  const int ty0 = max(0, (int)fty0), ty1 = min(tiles_y - 1, (int)fty1);
+  const int bx0 = max(0, (int)ftx0), bx1 = min(tiles_x - 1, (int)ftx1);
+  if (ty0 > ty1 || bx0 > bx1) return;
+  // x | y of the ellipse: centre mx + s dy, half-width h sqrt(kap - dy^2 / syy).
+  const float s = __fdiv_rn(e.sxy, e.syy);
+  const float h = __fsqrt_rn(fmaxf(__fsub_rn(e.sxx, __fmul_rn(e.sxy, s)), 0.0f));
+  const float dy_star = __fmul_rn(e.sxy, __fsqrt_rn(__fdiv_rn(kap, e.sxx)));  // rightmost point
+  for (int ty = ty0; ty <= ty1; ++ty) {
+    const float b0 = fmaxf(__fsub_rn(__fsub_rn((float)(ty * tile_h), kTilePad), e.my), -ry);
+    const float b1 =
+        fminf(__fsub_rn(__fadd_rn((float)(ty * tile_h + tile_h - 1), kTilePad), e.my), ry);
+    float xmax, xmin;
+    if (b0 > b1) {
+      // The band lies in the padding only: keep the whole padded width.
+      xmax = x_hi;
+      xmin = x_lo;
+    } else {
+      if (dy_star >= b0 && dy_star <= b1) {
+        xmax = __fadd_rn(e.mx, rx);
+      } else {
+        const float d = fminf(fmaxf(dy_star, b0), b1);
+        const float hw = __fmul_rn(
+            h, __fsqrt_rn(fmaxf(__fsub_rn(kap, __fdiv_rn(__fmul_rn(d, d), e.syy)), 0.0f)));
+        xmax = __fadd_rn(__fadd_rn(e.mx, __fmul_rn(s, d)), hw);
+      }
+      if (-dy_star >= b0 && -dy_star <= b1) {
+        xmin = __fsub_rn(e.mx, rx);
+      } else {
+        const float d = fminf(fmaxf(-dy_star, b0), b1);
+        const float hw = __fmul_rn(
+            h, __fsqrt_rn(fmaxf(__fsub_rn(kap, __fdiv_rn(__fmul_rn(d, d), e.syy)), 0.0f)));
+        xmin = __fsub_rn(__fadd_rn(e.mx, __fmul_rn(s, d)), hw);
+      }
+      xmax = __fadd_rn(xmax, kTilePad);
+      xmin = __fsub_rn(xmin, kTilePad);
+    }
+    const int tx0 =
+        max(bx0, (int)floorf(fminf(fmaxf(__fdiv_rn(xmin, tw), -1.0f), (float)tiles_x)));
+    const int tx1 =
+        min(bx1, (int)floorf(fminf(fmaxf(__fdiv_rn(xmax, tw), -1.0f), (float)tiles_x)));
+    if (tx0 <= tx1) fn(ty, tx0, tx1);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files). All take device pointers and a stream.
+// ------------------------------------------------------------------------------------------
+struct ScanScratch {
+  uint32_t* block_sums;  // >= scan_blocks(n) + 1 entries
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+// Exclusive scan of in[0..n) (n read from n_dev if non-null, capped at n_cap) into out, total
+// into *total (may be null).
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_cap,
+                                  const uint32_t* n_dev, uint32_t* total, uint32_t* block_sums,
+                                  cudaStream_t stream);
+
+// Compaction of visible entries: for vi in [0, n) with ntiles[vi] > 0, writes
+// keys[pos] = float bits of rec0[vi].w (depth), vals[pos] = vi, count into *n_out.
+cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec0, int64_t n,
+                                   uint32_t* keys, uint32_t* vals, uint32_t* n_out,
+                                   uint32_t* block_sums, cudaStream_t stream);
+
+// offs[k] = exclusive scan of ntiles[order[k]] for k < *n_dev; total into *total.
+cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, int64_t n_cap,
+                               const uint32_t* n_dev, uint32_t* offs, uint32_t* total,
+                               uint32_t* block_sums, cudaStream_t stream);
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadixBins = 256;
+
+inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+// Scratch for a sort of up to n_cap elements: histogram table and scan block sums (u32 counts).
+inline int64_t sort_hist_entries(int64_t n_cap) { return sort_blocks(n_cap) * kRadixBins; }
+
+// Stable LSD radix sort of (keys, vals) by bits [begin_bit, end_bit); ping-pongs between the
+// (keys, vals) and (keys_alt, vals_alt) buffers and returns in *result_in_alt whether the
+// sorted data ended in the alternate buffers. vals may be null (keys only).
+cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                              uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
+                              int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
+                              bool* result_in_alt, cudaStream_t stream);
+
+}  // namespace rgs

@@ -1,0 +1,308 @@
+// sort.cu -- prefix scans, visibility compaction and the stable LSD radix sort that build the
+// front-to-back ordered covering lists (Section 3.1: per pixel, the covering Gaussians near to
+// far). All scans are reduce-then-scan (three kernels, no inter-block waiting), so no kernel
+// here ever spins on another block.
+#include "rgs_internal.cuh"
+
+namespace rgs {
+namespace {
+
+__device__ __forceinline__ uint32_t read_count(const uint32_t* n_dev, int64_t n_cap) {
+  if (!n_dev) return (uint32_t)n_cap;
+  const uint32_t n = *n_dev;
+  return n < (uint64_t)n_cap ? n : (uint32_t)n_cap;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total in *total.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < THREADS / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < THREADS / 32) warp_sums[lane] = w;  // inclusive warp prefix
+  }
+  __syncthreads();
+  const uint32_t warp_prefix = warp > 0 ? warp_sums[warp - 1] : 0u;
+  if (total) *total = warp_sums[THREADS / 32 - 1];
+  const uint32_t r = warp_prefix + x - v;
+  __syncthreads();  // warp_sums may be reused by the caller's next scan
+  return r;
+}
+
+// Loaders: value of element k.
+struct PlainLoad {
+  const uint32_t* in;
+  __device__ uint32_t operator()(uint32_t k) const { return in[k]; }
+};
+struct FlagLoad {
+  const uint32_t* in;
+  __device__ uint32_t operator()(uint32_t k) const { return in[k] > 0u ? 1u : 0u; }
+};
+struct GatherLoad {
+  const uint32_t* in;
+  const uint32_t* order;
+  __device__ uint32_t operator()(uint32_t k) const { return in[order[k]]; }
+};
+
+// Pass 1: per-block sums.
+template <typename Load>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load load, int64_t n_cap,
+                                                                   const uint32_t* n_dev,
+                                                                   uint32_t* block_sums) {
+  const uint32_t n = read_count(n_dev, n_cap);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+  if (base < n) {
+#pragma unroll 4
+    for (int k = 0; k < kScanItems; ++k) {
+      const int64_t idx = base + (int64_t)k * kScanThreads + threadIdx.x;
+      if (idx < n) s += load((uint32_t)idx);
+    }
+  }
+  uint32_t total;
+  block_exclusive_scan<kScanThreads>(s, &total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Pass 2: one block scans the block sums in place (exclusive) and writes the grand total.
+__global__ void __launch_bounds__(1024) scan_block_sums_kernel(uint32_t* block_sums,
+                                                               int64_t n_blocks,
+                                                               uint32_t* total) {
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n_blocks; base += 1024 * 4) {
+    uint32_t v[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * 4 + k;
+      v[k] = idx < n_blocks ? block_sums[idx] : 0u;
+      s += v[k];
+    }
+    uint32_t chunk_total;
+    uint32_t pre = block_exclusive_scan<1024>(s, &chunk_total);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * 4 + k;
+      if (idx < n_blocks) block_sums[idx] = carry + pre;
+      pre += v[k];
+    }
+    carry += chunk_total;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Pass 3: per-block exclusive scan plus the block's offset; the Store functor writes results.
+struct PlainStore {
+  uint32_t* out;
+  __device__ void operator()(uint32_t k, uint32_t value, uint32_t prefix) const {
+    (void)value;
+    out[k] = prefix;
+  }
+};
+struct CompactStore {
+  const float4* rec0;
+  uint32_t* keys;
+  uint32_t* vals;
+  __device__ void operator()(uint32_t k, uint32_t value, uint32_t prefix) const {
+    if (value) {
+      keys[prefix] = __float_as_uint(rec0[k].w);
+      vals[prefix] = k;
+    }
+  }
+};
+
+template <typename Load, typename Store>
+__global__ void __launch_bounds__(kScanThreads) scan_downsweep_kernel(Load load, Store store,
+                                                                      int64_t n_cap,
+                                                                      const uint32_t* n_dev,
+                                                                      const uint32_t* block_sums) {
+  const uint32_t n = read_count(n_dev, n_cap);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (base >= n) return;
+  // Thread t owns the kScanItems consecutive elements base + t * kScanItems + k.
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + k;
+    v[k] = idx < n ? load((uint32_t)idx) : 0u;
+    s += v[k];
+  }
+  uint32_t pre = block_exclusive_scan<kScanThreads>(s, nullptr) + block_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + k;
+    if (idx < n) store((uint32_t)idx, v[k], pre);
+    pre += v[k];
+  }
+}
+
+template <typename Load, typename Store>
+cudaError_t run_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_dev,
+                     uint32_t* total, uint32_t* block_sums, cudaStream_t stream) {
+  const int64_t nb = scan_blocks(n_cap);
+  if (nb == 0) {
+    if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
+    return cudaSuccess;
+  }
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, n_cap, n_dev, block_sums);
+  scan_block_sums_kernel<<<1, 1024, 0, stream>>>(block_sums, nb, total);
+  scan_downsweep_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
+                                                                   block_sums);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Radix sort. Each block owns kSortTile consecutive keys; warp w of the block owns the
+// contiguous sub-range [w * 32 * kSortItems, (w + 1) * 32 * kSortItems) and walks it in rounds
+// of 32 keys (lane l takes element r * 32 + l), so warp order, round order and lane order
+// together follow the input order, which makes the ranks stable.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint32_t* keys,
+                                                                     int64_t n_cap,
+                                                                     const uint32_t* n_dev,
+                                                                     int shift, uint32_t mask,
+                                                                     uint32_t* hist,
+                                                                     int64_t n_blocks) {
+  __shared__ uint32_t counts[kRadixBins];
+  const uint32_t n = read_count(n_dev, n_cap);
+  for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) counts[d] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base < n) {
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; ++k) {
+      const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
+      if (idx < n) atomicAdd(&counts[(keys[idx] >> shift) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  // Digit-major table: an exclusive scan over it yields each (digit, block) scatter offset.
+  for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads)
+    hist[(int64_t)d * n_blocks + blockIdx.x] = counts[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
+    const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+    int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* offsets,
+    int64_t n_blocks) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ uint32_t warp_counts[kWarps][kRadixBins];
+  const uint32_t n = read_count(n_dev, n_cap);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (base >= n) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = lane; d < kRadixBins; d += 32) warp_counts[warp][d] = 0;
+  __syncwarp();
+  const int64_t wbase = base + (int64_t)warp * 32 * kSortItems;
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t idx = wbase + r * 32 + lane;
+    const bool valid = idx < n;
+    key[r] = valid ? keys_in[idx] : 0u;
+    val[r] = (valid && vals_in) ? vals_in[idx] : 0u;
+    const uint32_t digit = valid ? ((key[r] >> shift) & mask) : kRadixBins;  // kRadixBins = none
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t before = __popc(peers & lt_mask);
+    uint32_t prior = 0;
+    if (valid) prior = warp_counts[warp][digit];
+    __syncwarp();
+    if (valid && before == 0) warp_counts[warp][digit] = prior + __popc(peers);
+    __syncwarp();
+    rank[r] = valid ? prior + before : 0xffffffffu;
+  }
+  __syncthreads();
+  // Exclusive prefix over warps, per digit: keys of earlier warps come first.
+  for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = warp_counts[w][d];
+      warp_counts[w][d] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    if (rank[r] == 0xffffffffu) continue;
+    const uint32_t digit = (key[r] >> shift) & mask;
+    const uint32_t pos =
+        offsets[(int64_t)digit * n_blocks + blockIdx.x] + warp_counts[warp][digit] + rank[r];
+    keys_out[pos] = key[r];
+    if (vals_out) vals_out[pos] = val[r];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_cap,
+                                  const uint32_t* n_dev, uint32_t* total, uint32_t* block_sums,
+                                  cudaStream_t stream) {
+  return run_scan(PlainLoad{in}, PlainStore{out}, n_cap, n_dev, total, block_sums, stream);
+}
+
+cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec0, int64_t n,
+                                   uint32_t* keys, uint32_t* vals, uint32_t* n_out,
+                                   uint32_t* block_sums, cudaStream_t stream) {
+  return run_scan(FlagLoad{ntiles}, CompactStore{rec0, keys, vals}, n, nullptr, n_out,
+                  block_sums, stream);
+}
+
+cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, int64_t n_cap,
+                               const uint32_t* n_dev, uint32_t* offs, uint32_t* total,
+                               uint32_t* block_sums, cudaStream_t stream) {
+  return run_scan(GatherLoad{ntiles, order}, PlainStore{offs}, n_cap, n_dev, total, block_sums,
+                  stream);
+}
+
+cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                              uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
+                              int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
+                              bool* result_in_alt, cudaStream_t stream) {
+  *result_in_alt = false;
+  const int64_t nb = sort_blocks(n_cap);
+  if (nb == 0 || end_bit <= begin_bit) return cudaSuccess;
+  const int bits = end_bit - begin_bit;
+  const int passes = (bits + 7) / 8;
+  const int per_pass = (bits + passes - 1) / passes;
+  uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals ? vals_alt : nullptr;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = begin_bit + p * per_pass;
+    const int w = (shift + per_pass <= end_bit) ? per_pass : end_bit - shift;
+    const uint32_t mask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
+    radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(kin, n_cap, n_dev, shift,
+                                                                    mask, hist, nb);
+    cudaError_t err = launch_exclusive_scan(hist, hist, nb * kRadixBins, nullptr, nullptr,
+                                            block_sums, stream);
+    if (err != cudaSuccess) return err;
+    radix_downsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
+        kin, vin, kout, vout, n_cap, n_dev, shift, mask, hist, nb);
+    uint32_t* t = kin;
+    kin = kout;
+    kout = t;
+    t = vin;
+    vin = vout;
+    vout = t;
+    *result_in_alt = !*result_in_alt;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rgs

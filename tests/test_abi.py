@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/rgs.h
+declares; the ctypes mirrors of the header's structs have the C layout. No GPU needed."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2601_00705_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rgs.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rgs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(binding.EXPORTED) == _declared_functions()
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_ctypes_structs_match_c_layout(tmp_path):
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rgs.h"\n'
+                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\","
+                   "sizeof(rgs_gaussians), sizeof(rgs_camera), sizeof(rgs_config),"
+                   "sizeof(rgs_images), sizeof(rgs_image_grads), sizeof(rgs_stats),"
+                   "offsetof(rgs_config, tile_w));return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                            check=True).stdout.split()]
+    assert sizes == [ctypes.sizeof(binding.Gaussians), ctypes.sizeof(binding.Camera),
+                     ctypes.sizeof(binding.Config), ctypes.sizeof(binding.Images),
+                     ctypes.sizeof(binding.ImageGrads), ctypes.sizeof(binding.Stats),
+                     binding.Config.tile_w.offset]
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    assert lib.rgs_create(ctypes.byref(h), 0) == binding.RGS_ERR_INVALID_ARG
+    assert lib.rgs_create(None, 0) == binding.RGS_ERR_INVALID_ARG
