@@ -1,0 +1,480 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched differentiable Gaussian-splatting rasterizer on GB300.
+
+One step = one forward + backward of the whole hot path over one batch: preprocess, depth sort,
+pair duplication, tile sort, tile ranges, forward blend, backward blend, backward preprocess with
+the per-view SE(3) twist gradient, for every view of the batch in one launch sequence, replayed
+as one CUDA graph. Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed
+steps. The default workload is the TUM-shaped mapping window: 10 keyframes at 640x480 over
+150k Gaussians with SH degree 3, all parameter gradients and the per-view pose gradients.
+
+Under torchrun each rank renders its own replica of the workload on its own GPU (weak scaling,
+no collective on the data path); `value` is the pixels of all ranks over the slowest rank's time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd renders/sec (Mpix/s) at 1 GB300 + % roofline; batched vs per-view speedup"
+WORKLOAD_NAMES = {
+    "tiny": "tiny-1x160x120-2k-sh0",
+    "replica": "replica-1x1200x680-300k-sh0-pose",
+    "tum": "tum-window-10x640x480-150k-sh3",
+    "uneven": "uneven-24views-mixed-1M-sh3",
+    "large": "large-16x1920x1080-3M-sh3",
+}
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 work of the blend kernels (FLOP, a fused multiply-add counted as 2, exp as 1):
+#   forward, per visited (pixel, Gaussian) position: offset 2, exponent 9, exp 1, o*G 1,
+#     clamp 1, threshold 1 = 15; per composited pair: 1-a, T(1-a), stop test, a*T, three colour
+#     and one depth FMA = 12 more.
+#   backward, per visited position: the same 15; per composited pair: transmittance recovery 2,
+#     weight 1, colour / depth grads 4, dL/dalpha 20, suffix updates 8, opacity / mean /
+#     conic grads 16 = 51 more.
+FWD_FLOP_EVAL, FWD_FLOP_CONTRIB = 15, 12
+BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 15, 51
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", default="tum", choices=sorted(WORKLOAD_NAMES))
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    return p.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples the SM clock and the throttle reasons of one GPU while the timed region runs.
+
+    Reads NVML directly (ctypes on libnvidia-ml, every 5 ms from a thread) because the timed
+    region can be far shorter than nvidia-smi's sampling period; falls back to
+    `nvidia-smi -lms 200` when NVML cannot be loaded. Only reads settings, never changes them.
+    """
+    # nvmlClocksEventReasons bits
+    HW_SLOWDOWN, SW_THERMAL, HW_THERMAL, SW_POWER_CAP = 0x8, 0x20, 0x40, 0x4
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.gpu = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+        self.samples = []
+        self.max_mhz = None
+        self.nvml = None
+        self.thread = None
+        self.stop_flag = False
+        self.proc = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if self.gpu.isdigit():
+                rc = lib.nvmlDeviceGetHandleByIndex_v2(int(self.gpu), ctypes.byref(h))
+            else:
+                rc = lib.nvmlDeviceGetHandleByUUID(self.gpu.encode(), ctypes.byref(h))
+            if rc != 0:
+                raise OSError("no NVML handle")
+            self.nvml, self.handle = lib, h
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                self.max_mhz = float(mx.value)
+        except OSError:
+            self.nvml = None
+
+    def _loop(self):
+        import ctypes
+        clk = ctypes.c_uint()
+        reasons = ctypes.c_ulonglong()
+        get_reasons = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not self.stop_flag:
+            if self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(clk)) == 0:
+                r = reasons.value if get_reasons(self.handle, ctypes.byref(reasons)) == 0 else 0
+                self.samples.append((float(clk.value), int(r)))
+            time.sleep(0.005)
+
+    def start(self):
+        if self.nvml is not None:
+            import threading
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=clocks.sm,clocks.max.sm,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join()
+            if not self.samples:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"]}
+            bits = [self.HW_SLOWDOWN, self.HW_THERMAL, self.SW_THERMAL, self.SW_POWER_CAP]
+            seen = sorted({names[k] for _, r in self.samples for k in range(4) if r & bits[k]})
+            return {"sm_mhz": float(np.median([s for s, _ in self.samples])),
+                    "sm_max_mhz": self.max_mhz, "reasons": seen, "samples": len(self.samples),
+                    "source": "nvml"}
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 5]
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[2 + k].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median([float(r[0]) for r in rows])),
+                "sm_max_mhz": float(max(float(r[1]) for r in rows)), "reasons": reasons,
+                "samples": len(rows), "source": "nvidia-smi"}
+
+
+# ------------------------------------------------------------------------------ oracle (CPU)
+
+def oracle_sample(wl, views):
+    """Times the FP64 oracle (forward + backward) on the given views of the workload."""
+    import oracle
+    from paper_2601_00705_gb300 import synthetic
+    g = wl.gaussians.as_dict()
+    cams = [wl.cameras[v] for v in views]
+    sub = synthetic.Workload(wl.name, wl.gaussians, cams, wl.grad_mask, wl.depth_weight)
+    d_color, d_depth, _ = synthetic.upstream(sub)
+    threads = oracle.default_threads()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.render(g, cams, d_color=d_color, d_depth=d_depth if wl.depth_weight else None,
+                  threads=threads)
+    dt = time.perf_counter() - t0
+    pixels = sum(c["width"] * c["height"] for c in cams)
+    return pixels, dt, threads
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: the FP64 CPU oracle as it stands, one view of the workload per step."""
+    from paper_2601_00705_gb300 import synthetic
+    if rank != 0:
+        return
+    wl = synthetic.make(args.workload)
+    V = len(wl.cameras)
+    for w in range(args.warmup):
+        oracle_sample(wl, [w % V])
+    total_px, total_s, threads = 0, 0.0, 1
+    for k in range(args.steps):
+        px, dt, threads = oracle_sample(wl, [k % V])
+        total_px += px
+        total_s += dt
+    value = total_px / total_s / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
+                         "sample": f"one full view of the {V}-view window per step "
+                                   "(forward + backward), views in turn"},
+        "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2601_00705_gb300 import binding, synthetic
+    from paper_2601_00705_gb300.render import Renderer
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = synthetic.make(args.workload)
+    g = wl.gaussians.as_dict()
+    n, K, V = g["means"].shape[0], g["sh"].shape[1], len(wl.cameras)
+    pixels = wl.n_pixels
+    mask = binding.GRAD_POSE if wl.grad_mask == "pose" else binding.GRAD_ALL
+    host = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)) for k, v in g.items()}
+    up_host = [torch.from_numpy(u) for u in synthetic.upstream(wl)[:2]]
+    params = [host[k].to(dev) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    ups = [u.to(dev) for u in up_host]
+    if not wl.depth_weight:
+        ups[1] = None
+    cams = binding.make_cameras(wl.cameras)
+    r = Renderer(dev)
+    r.ctx.set_phase_timing(True)
+    images = (torch.empty((pixels, 3), device=dev), torch.empty(pixels, device=dev),
+              torch.empty(pixels, device=dev))
+    shapes = dict(means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity_logits=(n,),
+                  sh=(n, K, 3), pose=(V, 6))
+    grads = {k: torch.empty(s, device=dev) for k, s in shapes.items()}
+
+    def step_eager(state):
+        _, _, _, state = r.forward_raw(*params, cams, state=state, out=images)
+        r.backward_raw(state, n, K, V, ups[0], ups[1], None, mask, out=grads)
+        return state
+
+    # Size every buffer outside capture, then capture one fwd+bwd as a graph.
+    state = 0
+    for _ in range(2):
+        state = step_eager(state)
+    torch.cuda.synchronize()
+    stats = r.stats(state)
+    graph = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream(dev)
+    cap_stream.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph, stream=cap_stream):
+            step_eager(state)
+    torch.cuda.current_stream(dev).wait_stream(cap_stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    stats = r.stats(state)
+    assert stats["status"] == 0, f"pair list overflow under capture: {stats}"
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    phase_sum = {}
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in r.ctx.phase_times(state).items():
+            phase_sum[k] = phase_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * pixels * args.steps / (total_ms / 1e3) / 1e6
+    phases = {k: v / args.steps for k, v in phase_sum.items()}
+    stats = r.stats(state)
+
+    # Per-view loop: the same kernels, one view per forward / backward, in one graph.
+    loop_states = []
+    loop_imgs, loop_ups = [], []
+    off = 0
+    for v in range(V):
+        P = wl.cameras[v]["width"] * wl.cameras[v]["height"]
+        loop_imgs.append(tuple(t[off:off + P] for t in images))
+        loop_ups.append((ups[0][off:off + P].contiguous(),
+                         None if ups[1] is None else ups[1][off:off + P].contiguous()))
+        off += P
+    cam_list = [binding.make_cameras([c]) for c in wl.cameras]
+    loop_grads = [{k: torch.empty((1, 6) if k == "pose" else s, device=dev)
+                   for k, s in shapes.items()} for _ in range(V)]
+
+    def loop_eager(states):
+        out = []
+        for v in range(V):
+            _, _, _, st = r.forward_raw(*params, cam_list[v], state=states[v], out=loop_imgs[v])
+            r.backward_raw(st, n, K, 1, loop_ups[v][0], loop_ups[v][1], None, mask,
+                           out=loop_grads[v])
+            out.append(st)
+        return out
+
+    loop_states = loop_eager([0] * V)
+    loop_states = loop_eager(loop_states)
+    torch.cuda.synchronize()
+    loop_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(loop_graph, stream=cap_stream):
+            loop_eager(loop_states)
+    torch.cuda.current_stream(dev).wait_stream(cap_stream)
+    for _ in range(args.warmup):
+        loop_graph.replay()
+    loop_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        loop_graph.replay()
+        e1.record()
+        e1.synchronize()
+        loop_ms.append(e0.elapsed_time(e1))
+    loop_ms_per_step = float(np.sum(loop_ms)) / args.steps
+
+    # End to end through the public API: pinned host inputs -> device, fwd + bwd, results back.
+    pin = {k: v.pin_memory() for k, v in host.items()}
+    up_pin = [u.pin_memory() for u in up_host]
+    out_host = {k: torch.empty(s, pin_memory=True) for k, s in shapes.items()}
+    img_host = [torch.empty(t.shape, pin_memory=True) for t in images]
+    h2d = sum(t.numel() * 4 for t in pin.values()) + up_pin[0].numel() * 4
+    if wl.depth_weight:
+        h2d += up_pin[1].numel() * 4
+    d2h = sum(t.numel() * 4 for k, t in out_host.items() if mask & dict(
+        means=1, log_scales=2, quats=4, opacity_logits=8, sh=16, pose=32)[k])
+    d2h += sum(t.numel() * 4 for t in img_host)
+
+    def step_e2e(st):
+        p = [pin[k].to(dev, non_blocking=True)
+             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+        uc = up_pin[0].to(dev, non_blocking=True)
+        ud = up_pin[1].to(dev, non_blocking=True) if wl.depth_weight else None
+        c, d, a, st = r.forward_raw(*p, cams, state=st)
+        gr = r.backward_raw(st, n, K, V, uc, ud, None, mask)
+        for k, t in gr.items():
+            if t is not None:
+                out_host[k].copy_(t, non_blocking=True)
+        for hbuf, dbuf in zip(img_host, (c, d, a)):
+            hbuf.copy_(dbuf, non_blocking=True)
+        return st
+
+    e2e_state = step_e2e(0)
+    torch.cuda.synchronize()
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_state = step_e2e(e2e_state)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        e2e_state = step_e2e(e2e_state)
+        e1.record()
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = float(np.sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * pixels * args.steps / (e2e_total / 1e3) / 1e6
+
+    # Roofline of the dominant kernel (the blend phases are single launches per step).
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = 2.0 * 128 * props.multi_processor_count * sm_max * 1e6 / 1e12  # TFLOP/s
+    n_eval, n_contrib = stats["n_eval"], stats["n_contrib"]
+    work = {
+        "blend_forward": FWD_FLOP_EVAL * n_eval + FWD_FLOP_CONTRIB * n_contrib,
+        "blend_backward": BWD_FLOP_EVAL * n_eval + BWD_FLOP_CONTRIB * n_contrib,
+    }
+    dominant = max(phases, key=phases.get)
+    if dominant in work:
+        achieved = work[dominant] / (phases[dominant] / 1e3) / 1e12
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "peak_source": f"FP32 FMA pipe: 128 lanes x 2 FLOP x {props.multi_processor_count}"
+                                   f" SMs x {sm_max:.0f} MHz ({peak_src} max SM clock)"}
+    else:
+        roofline = {"kernel": dominant, "bound": "hbm", "achieved": None,
+                    "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "frac": None,
+                    "traffic": None}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "n_gaussians": n, "views": V,
+                   "pixels_per_step": pixels, "sh_degree": int(round(K ** 0.5)) - 1,
+                   "grad": wl.grad_mask, "cuda_graph": True,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "roofline": roofline,
+        "batched_vs_per_view": {"per_view_loop_ms": loop_ms_per_step,
+                                "batched_ms": ms_per_step,
+                                "speedup": loop_ms_per_step / ms_per_step},
+        "phases_ms": phases,
+        "counts": {"visible": stats["n_visible"], "pairs": stats["n_pairs"],
+                   "evaluated": n_eval, "composited": n_contrib},
+    }
+    if world == 1 and rank == 0:
+        px, dt, threads = oracle_sample(wl, list(range(V)))
+        line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"all {V} views of the workload once (forward + "
+                                          f"backward, {px} pixels, {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # Only rank 0 times the CPU oracle; other ranks exit at once without work.
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), 0)
+        return
+    world, rank, local = dist_setup(args)
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

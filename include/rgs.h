@@ -123,11 +123,12 @@ typedef struct {
   int64_t n_visible;       /* (view, Gaussian) pairs that touch at least one tile */
   int64_t n_pairs;         /* duplicated (view, tile, Gaussian) entries */
   int64_t n_eval;          /* (pixel, Gaussian) list positions visited by the forward blend */
+  int64_t n_contrib;       /* of those, the ones composited (covering, before the stop) */
   int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs */
   int64_t pair_capacity;   /* allocated pair-list capacity */
   int64_t state_bytes;     /* device bytes held by the state */
   uint32_t status;         /* device status bits: 1 = pair list overflowed its capacity */
-  uint32_t reserved;
+  uint32_t kernel_launches; /* kernels launched by the last forward plus the last backward */
 } rgs_stats;
 
 /* Creates a context on CUDA device `device`. Returns RGS_ERR_INVALID_ARG for a null out pointer
@@ -182,6 +183,30 @@ rgs_status rgs_reserve(rgs_ctx* ctx, uint64_t* state, int64_t pair_capacity, voi
 
 /* Reads the counters of the last forward on `state` (synchronises `stream`). */
 rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t state, rgs_stats* out, void* stream);
+
+/* Phases timed by rgs_phase_times, in this order. */
+#define RGS_PHASE_PREPROCESS 0     /* projection, SH colour, tile counts (Eq. proj, Eq. app-sh) */
+#define RGS_PHASE_COMPACT 1        /* visible (view, Gaussian) entries with depth keys */
+#define RGS_PHASE_DEPTH_SORT 2     /* radix sort of the visible entries by depth */
+#define RGS_PHASE_OFFSETS 3        /* pair offsets (scan of tile counts in depth order) */
+#define RGS_PHASE_DUPLICATE 4      /* (tile, Gaussian) pair emission */
+#define RGS_PHASE_TILE_SORT 5      /* radix sort of the pairs by tile */
+#define RGS_PHASE_RANGES 6         /* per-tile [first, last + 1) */
+#define RGS_PHASE_BLEND_FORWARD 7  /* front-to-back compositing (Eq. alpha) */
+#define RGS_PHASE_BLEND_BACKWARD 8 /* back-to-front screen-space gradients */
+#define RGS_PHASE_PREPROCESS_BACKWARD 9 /* parameter and twist gradients (Eq. muCjac..sigmaIjac) */
+#define RGS_PHASE_COUNT 10
+
+/* Enables (enable != 0) or disables CUDA-event timing of the phases above on every later forward
+ * and backward of this context (also inside stream capture, where the events become graph
+ * nodes). Costs one event record per phase. */
+rgs_status rgs_set_phase_timing(rgs_ctx* ctx, int32_t enable);
+
+/* Device milliseconds of each phase of the most recent forward and backward on `state`
+ * (ms[RGS_PHASE_COUNT]; a phase that did not run reads 0). Synchronises `stream`. Outside stream
+ * capture, the duplicate phase of a forward includes the one host synchronisation that sizes
+ * the pair list. */
+rgs_status rgs_phase_times(rgs_ctx* ctx, uint64_t state, float* ms, int32_t n, void* stream);
 
 /* ---- Primitives of the binning stage, exposed for testing (Section 3.1: the front-to-back
  * ordered covering set is built by a key sort). Device pointers, caller-owned. ---- */

@@ -22,7 +22,11 @@ GRAD_ALL = 63
 # Every function the header declares (checked by the ABI tests).
 EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_render_forward", "rgs_render_backward", "rgs_release_state", "rgs_reserve",
-            "rgs_query_stats", "rgs_radix_sort_u32", "rgs_exclusive_scan_u32")
+            "rgs_query_stats", "rgs_set_phase_timing", "rgs_phase_times", "rgs_radix_sort_u32",
+            "rgs_exclusive_scan_u32")
+
+PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
+          "blend_forward", "blend_backward", "preprocess_backward")
 
 
 class Gaussians(ctypes.Structure):
@@ -56,9 +60,10 @@ class ImageGrads(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("n_visible", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
-                ("n_eval", ctypes.c_int64), ("n_nonfinite", ctypes.c_int64),
+                ("n_eval", ctypes.c_int64), ("n_contrib", ctypes.c_int64),
+                ("n_nonfinite", ctypes.c_int64),
                 ("pair_capacity", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
-                ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("status", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32)]
 
 
 _lock = threading.Lock()
@@ -94,6 +99,8 @@ def load(build_if_needed: bool = True):
             "rgs_release_state": (S, [P, U64]),
             "rgs_reserve": (S, [P, ctypes.POINTER(U64), I64, P]),
             "rgs_query_stats": (S, [P, U64, ctypes.POINTER(Stats), P]),
+            "rgs_set_phase_timing": (S, [P, I32]),
+            "rgs_phase_times": (S, [P, U64, ctypes.POINTER(ctypes.c_float), I32, P]),
             "rgs_radix_sort_u32": (S, [P, P, P, I64, I32, I32, P]),
             "rgs_exclusive_scan_u32": (S, [P, P, P, I64, P, P]),
         }
@@ -200,6 +207,15 @@ class Context:
         self._check(self.lib.rgs_query_stats(self.handle, ctypes.c_uint64(state), ctypes.byref(s),
                                              ctypes.c_void_p(stream)))
         return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def set_phase_timing(self, enable: bool):
+        self._check(self.lib.rgs_set_phase_timing(self.handle, int(bool(enable))))
+
+    def phase_times(self, state: int, stream: int = 0) -> dict:
+        ms = (ctypes.c_float * len(PHASES))()
+        self._check(self.lib.rgs_phase_times(self.handle, ctypes.c_uint64(state), ms, len(PHASES),
+                                             ctypes.c_void_p(stream)))
+        return dict(zip(PHASES, [float(x) for x in ms]))
 
     def radix_sort_u32(self, keys: int, vals: int, n: int, begin_bit: int, end_bit: int,
                        stream: int = 0):

@@ -604,6 +604,7 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
     case 2: RGS_PRE_FWD(2); break;
     default: RGS_PRE_FWD(3); break;
   }
+  RGS_LAUNCHED();
 #undef RGS_PRE_FWD
   return cudaGetLastError();
 }
@@ -628,12 +629,14 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
       case 2: RGS_PRE_BWD(2); break;
       default: RGS_PRE_BWD(3); break;
     }
+    RGS_LAUNCHED();
 #undef RGS_PRE_BWD
   }
   if ((grad_mask & RGS_GRAD_POSE) && d_pose) {
     if (blocks > 0) {
       pose_finalize_kernel<<<views.n_views * 6, 256, 0, stream>>>(pose_partial, blocks,
                                                                   views.n_views, d_pose);
+      RGS_LAUNCHED();
     } else {
       cudaError_t e = cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * views.n_views, stream);
       if (e != cudaSuccess) return e;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
     int32_t* __restrict__ last_index, Counters* __restrict__ counters) {
   constexpr int kThreads = TW * TH;
   __shared__ float4 s0[kThreads], s1[kThreads], s2[kThreads];
-  __shared__ unsigned long long s_eval[kThreads / 32];
+  __shared__ unsigned long long s_eval[kThreads / 32], s_contrib[kThreads / 32];
   const int gtile = blockIdx.x;
   const int v = view_of_tile(views, gtile);
   const ViewParams& vp = views.v[v];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
 
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
   int32_t last = -1;
-  uint32_t evals = 0;
+  uint32_t evals = 0, contribs = 0;
   bool done = !inside;
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
     if (__syncthreads_count(done) == kThreads) break;
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
       C2 = fmaf(w, g2.z, C2);
       D = fmaf(w, g0.w, D);
       T = Tn;
+      ++contribs;
       last = (int32_t)(start + k);
     }
   }
@@ -140,16 +141,26 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
     last_index[pix] = last;
   }
   // Evaluated (pixel, Gaussian) positions, for the roofline accounting.
-  unsigned long long e = evals;
+  unsigned long long e = evals, n_c = contribs;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  if ((threadIdx.x & 31) == 0) s_eval[threadIdx.x >> 5] = e;
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    n_c += __shfl_xor_sync(0xffffffffu, n_c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_eval[threadIdx.x >> 5] = e;
+    s_contrib[threadIdx.x >> 5] = n_c;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long s = 0;
+    unsigned long long s = 0, sc = 0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) s += s_eval[w];
+    for (int w = 0; w < kThreads / 32; ++w) {
+      s += s_eval[w];
+      sc += s_contrib[w];
+    }
     atomicAdd(&counters->n_eval, s);
+    atomicAdd(&counters->n_contrib, sc);
   }
 }
 
@@ -292,14 +303,16 @@ cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
                             const float* d_color, const float* d_depth, const float* d_alpha,
                             float* g2d, Counters* counters, cudaStream_t stream) {
   if (views.total_tiles == 0) return cudaSuccess;
-  if (forward)
+  if (forward) {
     blend_forward_kernel<TW, TH><<<views.total_tiles, TW * TH, 0, stream>>>(
         views, c, ranges, pair_vals, rec0, rec1, rec2, color, depth, alpha, t_final,
         last_index, counters);
-  else
+  } else {
     blend_backward_kernel<TW, TH><<<views.total_tiles, TW * TH, 0, stream>>>(
         views, c, ranges, pair_vals, rec0, rec1, rec2, t_final, last_index, d_color, d_depth,
         d_alpha, g2d);
+  }
+  RGS_LAUNCHED();
   return cudaGetLastError();
 }
 
@@ -315,8 +328,10 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
     duplicate_kernel<<<blocks, kDupThreads, 0, stream>>>(views, n, order, offsets, ntiles, rec0,
                                                          rec1, counters, capacity, keys, vals,
                                                          counters);
+    RGS_LAUNCHED();
   }
   store_pair_count_kernel<<<1, 1, 0, stream>>>(counters, capacity);
+  RGS_LAUNCHED();
   return cudaGetLastError();
 }
 
@@ -327,6 +342,7 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, u
   if (capacity > 0)
     tile_ranges_kernel<<<(capacity + 255) / 256, 256, 0, stream>>>(keys, counters,
                                                                    (uint32_t)total_tiles, ranges);
+    RGS_LAUNCHED();
   return cudaGetLastError();
 }
 

@@ -54,6 +54,8 @@ using namespace rgs;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kEvBwd0 = 9;                    // first backward event
+constexpr int kNumEvents = kEvBwd0 + 3;       // 9 forward marks + 3 backward marks
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -94,12 +96,18 @@ struct State {
   int64_t hist_cap = 0, sums_cap = 0;
   float* pose_partial = nullptr;
   Counters* counters = nullptr;
+  // Phase timing: event k is recorded at the start (k = 0) / end of each forward phase, and
+  // kEvBwd0 .. at the start / end of each backward phase.
+  cudaEvent_t ev[kNumEvents] = {};
+  bool fwd_timed = false, bwd_timed = false;
+  uint32_t fwd_launches = 0, bwd_launches = 0;
 };
 
 }  // namespace
 
 struct rgs_ctx {
   int device = 0;
+  bool timing = false;
   std::string last_error;
   std::map<uint64_t, State*> states;
   uint64_t next_id = 1;
@@ -253,6 +261,13 @@ rgs_status get_or_create_state(rgs_ctx* ctx, uint64_t* handle, State** out) {
   if (!handle) return fail(ctx, RGS_ERR_INVALID_ARG, "state handle pointer is null");
   if (*handle == 0) {
     State* s = new State();
+    for (cudaEvent_t& e : s->ev) {
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+        delete s;
+        return fail(ctx, RGS_ERR_CUDA, "cudaEventCreate failed");
+      }
+    }
     const uint64_t id = ctx->next_id++;
     ctx->states[id] = s;
     *handle = id;
@@ -266,6 +281,8 @@ rgs_status get_or_create_state(rgs_ctx* ctx, uint64_t* handle, State** out) {
 }
 
 void destroy_state(State* s) {
+  for (cudaEvent_t& e : s->ev)
+    if (e) cudaEventDestroy(e);
   free_region(s->r_vn);
   free_region(s->r_pix);
   free_region(s->r_tile);
@@ -345,6 +362,13 @@ rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const 
       !std::isfinite(cfg.znear))
     return fail(ctx, RGS_ERR_INVALID_ARG, "config values out of range");
   return RGS_OK;
+}
+
+// Records phase event k of state s when timing is enabled (as a graph node under capture).
+cudaError_t mark(const rgs_ctx* ctx, State& s, int k, cudaStream_t stream, bool capturing) {
+  if (!ctx->timing) return cudaSuccess;
+  return cudaEventRecordWithFlags(s.ev[k], stream,
+                                  capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 int bits_for(uint32_t count) {  // bits needed to represent values in [0, count)
@@ -474,26 +498,33 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   s->consts = consts;
   s->vn = vn;
   Counters* cnt = s->counters;
+  const uint64_t launches0 = launch_counter();
+  s->fwd_timed = ctx->timing;
   RGS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), stream), "reset counters");
+  RGS_CUDA(mark(ctx, *s, 0, stream, capturing), "event");
 
   // 1. Projection.
   RGS_CUDA(launch_preprocess_forward(views, consts, *g, s->rec0, s->rec1, s->rec2, s->ntiles, cnt,
                                      stream),
            "preprocess");
+  RGS_CUDA(mark(ctx, *s, 1, stream, capturing), "event");
   // 2. Visible entries with depth keys, in (view, Gaussian) order.
   RGS_CUDA(launch_compact_visible(s->ntiles, s->rec0, vn, s->vis_keys[0], s->vis_vals[0],
                                   &cnt->n_visible, s->block_sums, stream),
            "compact");
+  RGS_CUDA(mark(ctx, *s, 2, stream, capturing), "event");
   // 3. Stable sort by depth (positive float bits order like the values; the sign bit is 0).
   bool alt = false;
   RGS_CUDA(launch_radix_sort(s->vis_keys[0], s->vis_vals[0], s->vis_keys[1], s->vis_vals[1], vn,
                              &cnt->n_visible, 0, 31, s->hist, s->block_sums, &alt, stream),
            "depth sort");
   s->order = s->vis_vals[alt ? 1 : 0];
+  RGS_CUDA(mark(ctx, *s, 3, stream, capturing), "event");
   // 4. Pair offsets in depth order.
   RGS_CUDA(launch_gather_scan(s->ntiles, s->order, vn, &cnt->n_visible, s->offsets,
                               &cnt->n_pairs, s->block_sums, stream),
            "pair offsets");
+  RGS_CUDA(mark(ctx, *s, 4, stream, capturing), "event");
   // Size the pair list (outside capture: read the count back and grow if needed).
   int64_t pair_bound = s->pair_cap;
   if (!capturing) {
@@ -515,6 +546,7 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   RGS_CUDA(launch_duplicate(views, g->n, s->order, s->offsets, s->ntiles, s->rec0, s->rec1, vn,
                             capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
            "duplicate");
+  RGS_CUDA(mark(ctx, *s, 5, stream, capturing), "event");
   // 6. Stable sort by global tile id.
   alt = false;
   // Keys are tile ids in [0, total_tiles]; total_tiles itself marks an unused slot.
@@ -525,15 +557,19 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
            "tile sort");
   const uint32_t* sorted_keys = s->pair_keys[alt ? 1 : 0];
   s->sorted_vals = s->pair_vals[alt ? 1 : 0];
+  RGS_CUDA(mark(ctx, *s, 6, stream, capturing), "event");
   // 7. Tile ranges.
   RGS_CUDA(launch_tile_ranges(sorted_keys, cnt, s->ranges, views.total_tiles,
                               (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), stream),
            "tile ranges");
+  RGS_CUDA(mark(ctx, *s, 7, stream, capturing), "event");
   // 8. Blend.
   RGS_CUDA(launch_blend(true, views, consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
                         s->rec2, out->color, out->depth, out->alpha, s->t_final, s->last_index,
                         nullptr, nullptr, nullptr, nullptr, cnt, stream),
            "blend forward");
+  RGS_CUDA(mark(ctx, *s, 8, stream, capturing), "event");
+  s->fwd_launches = (uint32_t)(launch_counter() - launches0);
   s->has_forward = true;
   return RGS_OK;
 }
@@ -569,14 +605,48 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_gr
   const float* da = grads ? grads->d_alpha : nullptr;
   if (cudaSetDevice(ctx->device) != cudaSuccess)
     return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  const bool capturing = is_capturing(stream);
+  const uint64_t launches0 = launch_counter();
+  s->bwd_timed = ctx->timing;
+  RGS_CUDA(mark(ctx, *s, kEvBwd0, stream, capturing), "event");
   RGS_CUDA(launch_blend(false, s->views, s->consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
                         s->rec2, nullptr, nullptr, nullptr, s->t_final, s->last_index, dc, dd, da,
                         s->g2d, s->counters, stream),
            "blend backward");
+  RGS_CUDA(mark(ctx, *s, kEvBwd0 + 1, stream, capturing), "event");
   RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->ntiles, s->g2d, grad_mask,
                                       d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
                                       s->pose_partial, d_pose, stream),
            "preprocess backward");
+  RGS_CUDA(mark(ctx, *s, kEvBwd0 + 2, stream, capturing), "event");
+  s->bwd_launches = (uint32_t)(launch_counter() - launches0);
+  return RGS_OK;
+}
+
+rgs_status rgs_set_phase_timing(rgs_ctx* ctx, int32_t enable) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return RGS_OK;
+}
+
+rgs_status rgs_phase_times(rgs_ctx* ctx, uint64_t handle, float* ms, int32_t n,
+                           void* stream_ptr) {
+  if (!ctx || !ms || n < 0) return RGS_ERR_INVALID_ARG;
+  State* s = find_state(ctx, handle);
+  if (!s) return fail(ctx, RGS_ERR_STATE, "unknown state handle");
+  for (int k = 0; k < n; ++k) ms[k] = 0.0f;
+  cudaSetDevice(ctx->device);
+  RGS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream_ptr)), "sync for timing");
+  // Forward phases k = 0..7 lie between events k and k + 1; backward phases 8, 9 between the
+  // backward events.
+  for (int k = 0; k < n && k < RGS_PHASE_COUNT; ++k) {
+    const bool fwd = k < RGS_PHASE_BLEND_BACKWARD;
+    if (fwd ? !s->fwd_timed : !s->bwd_timed) continue;
+    const int e0 = fwd ? k : kEvBwd0 + (k - RGS_PHASE_BLEND_BACKWARD);
+    float t = 0.0f;
+    RGS_CUDA(cudaEventElapsedTime(&t, s->ev[e0], s->ev[e0 + 1]), "event timing");
+    ms[k] = t;
+  }
   return RGS_OK;
 }
 
@@ -600,8 +670,10 @@ rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t handle, rgs_stats* out, void* 
   out->n_visible = c.n_visible;
   out->n_pairs = c.n_pairs;
   out->n_eval = (int64_t)c.n_eval;
+  out->n_contrib = (int64_t)c.n_contrib;
   out->n_nonfinite = c.n_nonfinite;
   out->status = c.status;
+  out->kernel_launches = s->fwd_launches + s->bwd_launches;
   return RGS_OK;
 }
 

@@ -62,8 +62,16 @@ struct Counters {
   uint32_t status;
   uint32_t n_nonfinite;
   uint32_t pad[3];
-  unsigned long long n_eval;
+  unsigned long long n_eval;     // (pixel, Gaussian) positions the forward blend visited
+  unsigned long long n_contrib;  // of which composited (covering, before the stop)
 };
+
+// Host-side count of kernels the library has launched on the calling thread.
+inline uint64_t& launch_counter() {
+  static thread_local uint64_t count = 0;
+  return count;
+}
+#define RGS_LAUNCHED() (++::rgs::launch_counter())
 
 // ------------------------------------------------------------------------------------------
 // Small device helpers.

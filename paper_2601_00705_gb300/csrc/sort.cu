@@ -160,9 +160,12 @@ cudaError_t run_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_de
     return cudaSuccess;
   }
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, n_cap, n_dev, block_sums);
+  RGS_LAUNCHED();
   scan_block_sums_kernel<<<1, 1024, 0, stream>>>(block_sums, nb, total);
+  RGS_LAUNCHED();
   scan_downsweep_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
                                                                    block_sums);
+  RGS_LAUNCHED();
   return cudaGetLastError();
 }
 
@@ -289,11 +292,13 @@ cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
     const uint32_t mask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
     radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(kin, n_cap, n_dev, shift,
                                                                     mask, hist, nb);
+    RGS_LAUNCHED();
     cudaError_t err = launch_exclusive_scan(hist, hist, nb * kRadixBins, nullptr, nullptr,
                                             block_sums, stream);
     if (err != cudaSuccess) return err;
     radix_downsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
         kin, vin, kout, vout, n_cap, n_dev, shift, mask, hist, nb);
+    RGS_LAUNCHED();
     uint32_t* t = kin;
     kin = kout;
     kout = t;

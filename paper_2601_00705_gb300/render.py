@@ -9,6 +9,7 @@ runs in the library.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import binding
@@ -73,8 +74,10 @@ class Renderer:
         return color, depth, alpha, state
 
     def backward_raw(self, state: int, n: int, K: int, n_views: int, d_color=None, d_depth=None,
-                     d_alpha=None, grad_mask: int = binding.GRAD_ALL):
-        """Runs the backward of `state`; returns a dict of gradient tensors (None if not asked)."""
+                     d_alpha=None, grad_mask: int = binding.GRAD_ALL, out: dict | None = None):
+        """Runs the backward of `state`; returns a dict of gradient tensors (None if not asked).
+        `out` may supply preallocated float32 tensors (keys means, log_scales, quats,
+        opacity_logits, sh, pose)."""
         dev = self.device
 
         def prep(t, shape):
@@ -86,12 +89,22 @@ class Renderer:
         d_color = prep(d_color, (-1, 3))
         d_depth = prep(d_depth, (-1,))
         d_alpha = prep(d_alpha, (-1,))
+        given = out or {}
         out = {}
         shapes = dict(means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity_logits=(n,),
                       sh=(n, K, 3), pose=(n_views, 6))
         for (name, shape), bit in zip(shapes.items(), _GRAD_BITS):
-            out[name] = (torch.empty(shape, dtype=torch.float32, device=dev)
-                         if grad_mask & bit else None)
+            if not grad_mask & bit:
+                out[name] = None
+            elif given.get(name) is not None:
+                t = given[name]
+                if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != int(
+                        np.prod(shape)) or t.data_ptr() % 16:
+                    raise ValueError(f"preallocated gradient '{name}' must be a contiguous, "
+                                     f"16-byte aligned float32 tensor of {shape}")
+                out[name] = t
+            else:
+                out[name] = torch.empty(shape, dtype=torch.float32, device=dev)
         grads = binding.ImageGrads(d_color.data_ptr() if d_color is not None else None,
                                    d_depth.data_ptr() if d_depth is not None else None,
                                    d_alpha.data_ptr() if d_alpha is not None else None)
