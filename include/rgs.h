@@ -53,6 +53,7 @@ typedef enum {
                               grows it) or call rgs_reserve first */
   RGS_ERR_NOMEM = 4,       /* device allocation failed */
   RGS_ERR_STATE = 5,       /* unknown or released state handle */
+  RGS_ERR_TOO_LARGE = 6,   /* more elements than a fixed-scratch entry point supports */
 } rgs_status;
 
 /* Opaque context: owns per-forward saved state (projected records, sorted pair lists, tile
@@ -221,6 +222,28 @@ rgs_status rgs_radix_sort_u32(rgs_ctx* ctx, uint32_t* keys, uint32_t* vals, int6
  * total into *total_out (device u32, may be NULL). */
 rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                                   uint32_t* total_out, void* stream);
+
+/* ---- Allocation-free variant (the paper has no counterpart: this serves library users). ----
+ *
+ * rgs_exclusive_scan_u32_static computes exactly what rgs_exclusive_scan_u32 computes, but
+ * allocates nothing: no cudaMalloc, no cudaFree, no context. It is for callers that cannot
+ * allocate device memory at call time, such as a real-time tracking loop that must not block on
+ * the driver's allocator in the middle of a frame, or a process whose device memory is already
+ * reserved in full by another framework's caching allocator.
+ *   in, out: device u32 arrays of n elements (out may equal in); total_out: device u32 or NULL.
+ *   n: 0 <= n <= RGS_STATIC_SCAN_MAX_N; larger n returns RGS_ERR_TOO_LARGE before any GPU work.
+ *   stream: cudaStream_t as void* (NULL = legacy default stream). Runs on the current device.
+ * Its scratch (one u32 per 4096 elements) is a fixed 64 KiB device array inside the library,
+ * held by every GPU that loads the library until the process exits. The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture. All calls on a device share the array and keep the
+ * last call's contents; nothing in it needs to start at zero. Calls whose executions overlap on
+ * the GPU (different streams, or different host threads, without ordering) race on the array:
+ * serialise them. Returns RGS_ERR_INVALID_ARG for null arrays with n > 0 and RGS_ERR_CUDA if a
+ * CUDA call fails. */
+#define RGS_STATIC_SCAN_MAX_N (1 << 26)
+rgs_status rgs_exclusive_scan_u32_static(const uint32_t* in, uint32_t* out, int64_t n,
+                                         uint32_t* total_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,9 @@ import numpy as np
 from . import build as _build
 
 RGS_MAX_VIEWS = 64
-RGS_OK, RGS_ERR_INVALID_ARG, RGS_ERR_CUDA, RGS_ERR_CAPACITY, RGS_ERR_NOMEM, RGS_ERR_STATE = range(6)
+(RGS_OK, RGS_ERR_INVALID_ARG, RGS_ERR_CUDA, RGS_ERR_CAPACITY, RGS_ERR_NOMEM, RGS_ERR_STATE,
+ RGS_ERR_TOO_LARGE) = range(7)
+RGS_STATIC_SCAN_MAX_N = 1 << 26
 GRAD_MEANS, GRAD_SCALES, GRAD_QUATS, GRAD_OPACITY, GRAD_SH, GRAD_POSE = 1, 2, 4, 8, 16, 32
 GRAD_ALL = 63
 
@@ -23,7 +25,7 @@ GRAD_ALL = 63
 EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_render_forward", "rgs_render_backward", "rgs_release_state", "rgs_reserve",
             "rgs_query_stats", "rgs_set_phase_timing", "rgs_phase_times", "rgs_radix_sort_u32",
-            "rgs_exclusive_scan_u32")
+            "rgs_exclusive_scan_u32", "rgs_exclusive_scan_u32_static")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -103,6 +105,7 @@ def load(build_if_needed: bool = True):
             "rgs_phase_times": (S, [P, U64, ctypes.POINTER(ctypes.c_float), I32, P]),
             "rgs_radix_sort_u32": (S, [P, P, P, I64, I32, I32, P]),
             "rgs_exclusive_scan_u32": (S, [P, P, P, I64, P, P]),
+            "rgs_exclusive_scan_u32_static": (S, [P, P, I64, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
