@@ -39,15 +39,13 @@ WORKLOAD_NAMES = {
 }
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic FP32 work of the blend kernels (FLOP, a fused multiply-add counted as 2, exp as 1):
-#   forward, per visited (pixel, Gaussian) position: offset 2, exponent 9, exp 1, o*G 1,
-#     clamp 1, threshold 1 = 15; per composited pair: 1-a, T(1-a), stop test, a*T, three colour
-#     and one depth FMA = 12 more.
-#   backward, per visited position: the same 15; per composited pair: transmittance recovery 2,
-#     weight 1, colour / depth grads 4, dL/dalpha 20, suffix updates 8, opacity / mean /
-#     conic grads 16 = 51 more.
-FWD_FLOP_EVAL, FWD_FLOP_CONTRIB = 15, 12
-BWD_FLOP_EVAL, BWD_FLOP_CONTRIB = 15, 51
+# Algorithmic FP32 work of the blend kernels per evaluated (pixel, Gaussian) position (the
+# positions the forward visits until each pixel stops), as the hot-path scope table counts it:
+# the forward's coverage test and compositing, 15 FP32 operations (plus one exp); the backward's
+# recomputation, transmittance recovery and screen-space gradients, 40 FP32 operations (plus
+# two MUFU operations and the atomics after the warp reduction).
+FWD_FLOP_PER_EVAL = 15
+BWD_FLOP_PER_EVAL = 40
 
 
 def parse():
@@ -415,8 +413,8 @@ def run_ours(args, world, rank, local):
     fp32_peak = 2.0 * 128 * props.multi_processor_count * sm_max * 1e6 / 1e12  # TFLOP/s
     n_eval, n_contrib = stats["n_eval"], stats["n_contrib"]
     work = {
-        "blend_forward": FWD_FLOP_EVAL * n_eval + FWD_FLOP_CONTRIB * n_contrib,
-        "blend_backward": BWD_FLOP_EVAL * n_eval + BWD_FLOP_CONTRIB * n_contrib,
+        "blend_forward": FWD_FLOP_PER_EVAL * n_eval,
+        "blend_backward": BWD_FLOP_PER_EVAL * n_eval,
     }
     dominant = max(phases, key=phases.get)
     if dominant in work:

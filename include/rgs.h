@@ -93,6 +93,10 @@ typedef struct {
   float bg[3];      /* background colour, added as bg * T_final */
   int32_t tile_w;   /* tile shape of the binning and blend: 16x16 (default), 8x8 or 32x8 */
   int32_t tile_h;
+  int32_t pixels_per_thread; /* vertically adjacent pixels per blend thread: 1, 2 or 4
+                                (4 not with 8x8 tiles); 0 = default (4). Results do not depend
+                                on it or on the tile shape beyond atomics-order rounding of the
+                                gradients */
 } rgs_config;
 
 /* Forward outputs (device, caller-owned, P = sum_v W_v H_v): color [P,3], depth [P], alpha [P]. */

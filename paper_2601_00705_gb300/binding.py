@@ -48,7 +48,8 @@ class Config(ctypes.Structure):
     _fields_ = [("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("znear", ctypes.c_float), ("eps2d", ctypes.c_float),
                 ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("pixels_per_thread", ctypes.c_int32)]
 
 
 class Images(ctypes.Structure):

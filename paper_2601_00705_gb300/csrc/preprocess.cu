@@ -246,10 +246,13 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, const float* __restrict__ sh, float4* __restrict__ rec0,
     float4* __restrict__ rec1, float4* __restrict__ rec2, uint32_t* __restrict__ ntiles,
-    Counters* __restrict__ counters) {
+    Counters* __restrict__ counters, int views_per_chunk) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   if (i >= n) return;
+  // blockIdx.y selects a chunk of views, so small scenes still fill the GPU.
+  const int v_begin = blockIdx.y * views_per_chunk;
+  const int v_end = min(views.n_views, v_begin + views_per_chunk);
   float m[3], ls[3], q[4], shc[3 * K];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -273,9 +276,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
   GaussianLocal g;
   if (finite) gaussian_local(m, ls, q, logit, g);
   finite = finite && g.qnorm > 0.0f && isfinite(g.qnorm);
-  if (!finite) atomicAdd(&counters->n_nonfinite, (uint32_t)views.n_views);
+  if (!finite) atomicAdd(&counters->n_nonfinite, (uint32_t)(v_end - v_begin));
   const float kappa = finite ? 2.0f * logf(g.opacity / c.alpha_min) : -1.0f;
-  for (int v = 0; v < views.n_views; ++v) {
+  for (int v = v_begin; v < v_end; ++v) {
     const ViewParams& vp = views.v[v];
     const size_t vi = (size_t)v * n + i;
     ViewProj p;
@@ -283,7 +286,8 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     if (finite && kappa >= 0.0f && project_view(g, vp, c, p)) {
       r0 = make_float4(p.mean2d[0], p.mean2d[1], g.opacity, p.mc[2]);
-      r1 = make_float4(p.conic[0], p.conic[1], p.conic[2], kappa);
+      r1 = make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
+                       __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
       // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
       float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
             d2 = g.m[2] - vp.cam_center[2];
@@ -301,9 +305,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
         for (int k = 0; k < K; ++k) acc += shc[3 * k + ch] * Y[k];
         rgb[ch] = fmaxf(acc, 0.0f);
       }
-      r2 = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+      r2 = make_float4(rgb[0], rgb[1], rgb[2], kappa);
       Ellipse e;
-      if (make_ellipse(r0, r1, e))
+      if (make_ellipse(r0, r1, r2, e))
         for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
                           [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
     }
@@ -593,11 +597,17 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       float4* rec2, uint32_t* ntiles, Counters* counters,
                                       cudaStream_t stream) {
   if (g.n == 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((g.n + kPreThreads - 1) / kPreThreads);
+  // One thread per (Gaussian, chunk of views): enough threads to fill every SM a few times
+  // over, while a thread still reads its Gaussian's parameters once for several views.
+  const int blocks_x = (g.n + kPreThreads - 1) / kPreThreads;
+  const int target_blocks = 8 * 152;
+  const int chunks = max(1, min(views.n_views, (target_blocks + blocks_x - 1) / blocks_x));
+  const int per_chunk = (views.n_views + chunks - 1) / chunks;
+  const dim3 grid((unsigned)blocks_x, (unsigned)((views.n_views + per_chunk - 1) / per_chunk));
 #define RGS_PRE_FWD(D)                                                                     \
-  preprocess_forward_kernel<D><<<blocks, kPreThreads, 0, stream>>>(                        \
+  preprocess_forward_kernel<D><<<grid, kPreThreads, 0, stream>>>(                          \
       views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, rec0, rec1, rec2, \
-      ntiles, counters)
+      ntiles, counters, per_chunk)
   switch (g.sh_degree) {
     case 0: RGS_PRE_FWD(0); break;
     case 1: RGS_PRE_FWD(1); break;

@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const __grid_constant__ Views views, int n, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ntiles,
     const float4* __restrict__ rec0, const float4* __restrict__ rec1,
-    const Counters* __restrict__ counters_in, uint32_t capacity, uint32_t* __restrict__ keys,
+    const float4* __restrict__ rec2, const Counters* __restrict__ counters_in, uint32_t capacity,
+    uint32_t* __restrict__ keys,
     uint32_t* __restrict__ vals, Counters* __restrict__ counters) {
   const uint32_t k = blockIdx.x * kDupThreads + threadIdx.x;
   if (k >= counters_in->n_visible) return;
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   const ViewParams& vp = views.v[v];
   uint32_t off = begin;
   Ellipse e;
-  if (make_ellipse(rec0[vi], rec1[vi], e)) {
+  if (make_ellipse(rec0[vi], rec1[vi], rec2[vi], e)) {
     for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
                       [&](int ty, int tx0, int tx1) {
                         const uint32_t row = (uint32_t)(vp.tile_base + ty * vp.tiles_x);
@@ -69,16 +70,19 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys,
 }
 
 // ------------------------------------------------------------------------------------------
-// Forward blend.
+// Forward blend. A CTA covers one TW x TH tile with TW * TH / PPT threads; thread t owns the
+// PPT vertically adjacent pixels (x, y0 + k), k < PPT, of column x = t % TW, so every Gaussian
+// staged in shared memory is read once per thread and evaluated for PPT pixels.
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     const __grid_constant__ Views views, const Consts c, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ pair_vals, const float4* __restrict__ rec0,
     const float4* __restrict__ rec1, const float4* __restrict__ rec2, float* __restrict__ color,
     float* __restrict__ depth, float* __restrict__ alpha_out, float* __restrict__ t_final,
     int32_t* __restrict__ last_index, Counters* __restrict__ counters) {
-  constexpr int kThreads = TW * TH;
+  constexpr int kThreads = TW * TH / PPT;
+  static_assert(kThreads % 32 == 0, "whole warps only");
   __shared__ float4 s0[kThreads], s1[kThreads], s2[kThreads];
   __shared__ unsigned long long s_eval[kThreads / 32], s_contrib[kThreads / 32];
   const int gtile = blockIdx.x;
@@ -87,17 +91,25 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
   const int local = gtile - vp.tile_base;
   const int ty = local / vp.tiles_x, tx = local - ty * vp.tiles_x;
   const int px = tx * TW + (int)(threadIdx.x % TW);
-  const int py = ty * TH + (int)(threadIdx.x / TW);
-  const bool inside = px < vp.width && py < vp.height;
-  const float fx = (float)px, fy = (float)py;
+  const int py0 = ty * TH + (int)(threadIdx.x / TW) * PPT;
+  const float fx = (float)px;
   const uint2 range = ranges[gtile];
 
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
-  int32_t last = -1;
+  float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
+  int32_t last[PPT];
+  bool done[PPT];
+  bool all_done = true;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    T[k] = 1.0f;
+    C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
+    last[k] = -1;
+    done[k] = !(px < vp.width && py0 + k < vp.height);
+    all_done = all_done && done[k];
+  }
   uint32_t evals = 0, contribs = 0;
-  bool done = !inside;
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
-    if (__syncthreads_count(done) == kThreads) break;
+    if (__syncthreads_count(all_done) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
     if (j < range.y) {
       const uint32_t vi = pair_vals[j];
@@ -107,40 +119,53 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kThreads, range.y - start);
-    for (int k = 0; k < cnt && !done; ++k) {
-      ++evals;
-      const float4 g0 = s0[k];
-      const float4 g1 = s1[k];
-      const float power = gauss_power(__fsub_rn(fx, g0.x), __fsub_rn(fy, g0.y), g1.x, g1.y, g1.z);
-      const float a = fminf(c.alpha_max, gauss_alpha_raw(g0.z, power));
-      if (a < c.alpha_min) continue;
-      const float Tn = __fmul_rn(T, __fsub_rn(1.0f, a));
-      if (Tn < c.t_min) {
-        done = true;
-        break;
+    for (int g = 0; g < cnt && !all_done; ++g) {
+      const float4 g0 = s0[g];
+      const float4 g1 = s1[g];
+      const ColumnTerms ct = column_terms(__fsub_rn(fx, g0.x), g1.x, g1.y, g1.w);
+      all_done = true;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (!done[k]) {
+          ++evals;
+          const float dy = __fsub_rn((float)(py0 + k), g0.y);
+          const float a = fminf(c.alpha_max, opacity_times_gauss(ct, g1.z, dy));
+          if (a >= c.alpha_min) {
+            const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, a));
+            if (Tn < c.t_min) {
+              done[k] = true;
+            } else {
+              const float w = a * T[k];
+              const float4 g2 = s2[g];
+              C0[k] = fmaf(w, g2.x, C0[k]);
+              C1[k] = fmaf(w, g2.y, C1[k]);
+              C2[k] = fmaf(w, g2.z, C2[k]);
+              D[k] = fmaf(w, g0.w, D[k]);
+              T[k] = Tn;
+              ++contribs;
+              last[k] = (int32_t)(start + g);
+            }
+          }
+        }
+        all_done = all_done && done[k];
       }
-      const float w = a * T;
-      const float4 g2 = s2[k];
-      C0 = fmaf(w, g2.x, C0);
-      C1 = fmaf(w, g2.y, C1);
-      C2 = fmaf(w, g2.z, C2);
-      D = fmaf(w, g0.w, D);
-      T = Tn;
-      ++contribs;
-      last = (int32_t)(start + k);
     }
   }
-  if (inside) {
-    const long long pix = vp.pixel_offset + (long long)py * vp.width + px;
-    color[3 * pix + 0] = fmaf(T, c.bg[0], C0);
-    color[3 * pix + 1] = fmaf(T, c.bg[1], C1);
-    color[3 * pix + 2] = fmaf(T, c.bg[2], C2);
-    depth[pix] = D;
-    alpha_out[pix] = 1.0f - T;
-    t_final[pix] = T;
-    last_index[pix] = last;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int py = py0 + k;
+    if (px < vp.width && py < vp.height) {
+      const long long pix = vp.pixel_offset + (long long)py * vp.width + px;
+      color[3 * pix + 0] = fmaf(T[k], c.bg[0], C0[k]);
+      color[3 * pix + 1] = fmaf(T[k], c.bg[1], C1[k]);
+      color[3 * pix + 2] = fmaf(T[k], c.bg[2], C2[k]);
+      depth[pix] = D[k];
+      alpha_out[pix] = 1.0f - T[k];
+      t_final[pix] = T[k];
+      last_index[pix] = last[k];
+    }
   }
-  // Evaluated (pixel, Gaussian) positions, for the roofline accounting.
+  // Visited and composited (pixel, Gaussian) positions, for the roofline accounting.
   unsigned long long e = evals, n_c = contribs;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -165,17 +190,65 @@ __global__ void __launch_bounds__(TW * TH) blend_forward_kernel(
 }
 
 // ------------------------------------------------------------------------------------------
-// Backward blend.
+// Warp reduction of the ten screen-space gradient values of one Gaussian. Each butterfly level
+// halves the number of values a lane carries (10 -> 5 -> 3 -> 2 -> 1 -> 1), so it takes 12
+// shuffles instead of 10 x 5. On return the lane whose bits (b4 b3 b2 b1) select slot
+// reduced_slot() holds that slot's warp total (lanes with b0 = 1 hold a copy; slot -1 = none).
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) blend_backward_kernel(
+__device__ __forceinline__ float transpose_reduce10(const float (&a)[10], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+  float b[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float keep = h4 ? a[k + 5] : a[k];
+    const float send = h4 ? a[k] : a[k + 5];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float cc[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float hi = k + 3 < 5 ? b[(k + 3) % 5] : 0.0f;  // slots 3, 4 and an empty third
+    const float keep = h3 ? hi : b[k];
+    const float send = h3 ? b[k] : hi;
+    cc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float d[2];
+  {
+    const float keep0 = h2 ? cc[2] : cc[0];
+    const float send0 = h2 ? cc[0] : cc[2];
+    d[0] = keep0 + __shfl_xor_sync(0xffffffffu, send0, 4);
+    const float keep1 = h2 ? 0.0f : cc[1];
+    const float send1 = h2 ? cc[1] : 0.0f;
+    d[1] = keep1 + __shfl_xor_sync(0xffffffffu, send1, 4);
+  }
+  const float keep = h1 ? d[1] : d[0];
+  const float send = h1 ? d[0] : d[1];
+  float e = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  e += __shfl_xor_sync(0xffffffffu, e, 1);
+  return e;
+}
+
+__device__ __forceinline__ int reduced_slot(int lane) {
+  const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1,
+            b1 = (lane >> 1) & 1;
+  if (b2 == 0) return (b1 ? (b3 ? 4 : 1) : (b3 ? 3 : 0)) + 5 * b4;
+  if (b1 == 0 && b3 == 0) return 2 + 5 * b4;
+  return -1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward blend (same pixel layout as the forward).
+// ------------------------------------------------------------------------------------------
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     const __grid_constant__ Views views, const Consts c, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ pair_vals, const float4* __restrict__ rec0,
     const float4* __restrict__ rec1, const float4* __restrict__ rec2,
     const float* __restrict__ t_final, const int32_t* __restrict__ last_index,
     const float* __restrict__ d_color, const float* __restrict__ d_depth,
     const float* __restrict__ d_alpha, float* __restrict__ g2d) {
-  constexpr int kThreads = TW * TH;
+  constexpr int kThreads = TW * TH / PPT;
+  static_assert(kThreads % 32 == 0, "whole warps only");
   __shared__ float4 s0[kThreads], s1[kThreads], s2[kThreads];
   __shared__ uint32_t s_vi[kThreads];
   __shared__ int s_max_last[kThreads / 32];
@@ -185,28 +258,43 @@ __global__ void __launch_bounds__(TW * TH) blend_backward_kernel(
   const int local = gtile - vp.tile_base;
   const int ty = local / vp.tiles_x, tx = local - ty * vp.tiles_x;
   const int px = tx * TW + (int)(threadIdx.x % TW);
-  const int py = ty * TH + (int)(threadIdx.x / TW);
-  const bool inside = px < vp.width && py < vp.height;
-  const float fx = (float)px, fy = (float)py;
+  const int py0 = ty * TH + (int)(threadIdx.x / TW) * PPT;
+  const float fx = (float)px;
   const uint2 range = ranges[gtile];
   const int lane = threadIdx.x & 31;
+  const int slot = reduced_slot(lane);
 
-  float Tfin = 1.0f, gC0 = 0.0f, gC1 = 0.0f, gC2 = 0.0f, gD = 0.0f, gA = 0.0f;
-  int32_t last = -1;
-  if (inside) {
-    const long long pix = vp.pixel_offset + (long long)py * vp.width + px;
-    Tfin = t_final[pix];
-    last = last_index[pix];
-    if (d_color) {
-      gC0 = d_color[3 * pix + 0];
-      gC1 = d_color[3 * pix + 1];
-      gC2 = d_color[3 * pix + 2];
+  // Per pixel: transmittance behind the current position, the upstream gradients, and
+  // U = sum_ch dL/dC_ch S_ch + dL/dD S_D, where S is the colour / depth composited behind the
+  // current position (background included), so dL/dalpha = T q + (dL/dA T_final - U) / (1 - alpha)
+  // with q = dL/dC . c + dL/dD z.
+  float T[PPT], U[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gAT[PPT];
+  int32_t last[PPT];
+  int thread_last = -1;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    float Tfin = 1.0f;
+    gC0[k] = gC1[k] = gC2[k] = gD[k] = gAT[k] = 0.0f;
+    last[k] = -1;
+    const int py = py0 + k;
+    if (px < vp.width && py < vp.height) {
+      const long long pix = vp.pixel_offset + (long long)py * vp.width + px;
+      Tfin = t_final[pix];
+      last[k] = last_index[pix];
+      if (d_color) {
+        gC0[k] = d_color[3 * pix + 0];
+        gC1[k] = d_color[3 * pix + 1];
+        gC2[k] = d_color[3 * pix + 2];
+      }
+      if (d_depth) gD[k] = d_depth[pix];
+      if (d_alpha) gAT[k] = d_alpha[pix] * Tfin;
     }
-    if (d_depth) gD = d_depth[pix];
-    if (d_alpha) gA = d_alpha[pix];
+    T[k] = Tfin;
+    U[k] = Tfin * (gC0[k] * c.bg[0] + gC1[k] * c.bg[1] + gC2[k] * c.bg[2]);
+    thread_last = max(thread_last, last[k]);
   }
   // Only list positions up to the largest last-contributor index of the tile matter.
-  int m = last;
+  int m = thread_last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) s_max_last[threadIdx.x >> 5] = m;
@@ -216,9 +304,6 @@ __global__ void __launch_bounds__(TW * TH) blend_backward_kernel(
   for (int w = 0; w < kThreads / 32; ++w) max_last = max(max_last, s_max_last[w]);
   if (max_last < (int)range.x) return;
 
-  float T = Tfin;                                   // transmittance after the current position
-  float S0 = Tfin * c.bg[0], S1 = Tfin * c.bg[1], S2 = Tfin * c.bg[2];  // colour behind
-  float SD = 0.0f;                                  // depth behind
   const int first = (int)range.x;
   for (int bend = max_last + 1; bend > first; bend -= kThreads) {
     const int bstart = max(first, bend - kThreads);
@@ -233,69 +318,67 @@ __global__ void __launch_bounds__(TW * TH) blend_backward_kernel(
     }
     __syncthreads();
     for (int jj = bend - 1; jj >= bstart; --jj) {
-      const int k = jj - bstart;
-      float g[10];
+      const int g = jj - bstart;
+      float acc[10];
 #pragma unroll
-      for (int s = 0; s < 10; ++s) g[s] = 0.0f;
+      for (int s = 0; s < 10; ++s) acc[s] = 0.0f;
       bool contrib = false;
-      if (jj <= last) {
-        const float4 g0 = s0[k];
-        const float4 g1 = s1[k];
-        const float dx = __fsub_rn(fx, g0.x), dy = __fsub_rn(fy, g0.y);
-        const float power = gauss_power(dx, dy, g1.x, g1.y, g1.z);
-        const float oG = gauss_alpha_raw(g0.z, power);
-        const float a = fminf(c.alpha_max, oG);
-        if (a >= c.alpha_min) {
+      if (jj <= thread_last) {
+        const float4 g0 = s0[g];
+        const float4 g1 = s1[g];
+        const float4 g2 = s2[g];
+        const float dx = __fsub_rn(fx, g0.x);
+        const ColumnTerms ct = column_terms(dx, g1.x, g1.y, g1.w);
+        // Per-thread moments of dL/dpower over the thread's pixels (all share dx):
+        // sdp = sum dp, sdy = sum dp dy, sdy2 = sum dp dy^2.
+        float sdp = 0.0f, sdy = 0.0f, sdy2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (jj > last[k]) continue;
+          const float dy = __fsub_rn((float)(py0 + k), g0.y);
+          const float oG = opacity_times_gauss(ct, g1.z, dy);
+          const float a = fminf(c.alpha_max, oG);
+          if (a < c.alpha_min) continue;
           contrib = true;
-          const float om = __fsub_rn(1.0f, a);
-          const float rom = 1.0f / om;
-          T = T * rom;  // transmittance in front of this Gaussian
-          const float w = a * T;
-          const float4 g2 = s2[k];
-          g[kGR] = gC0 * w;
-          g[kGG] = gC1 * w;
-          g[kGB] = gC2 * w;
-          g[kGZ] = gD * w;
-          float dLda = gC0 * (g2.x * T - S0 * rom) + gC1 * (g2.y * T - S1 * rom) +
-                       gC2 * (g2.z * T - S2 * rom);
-          dLda += gD * (g0.w * T - SD * rom);
-          dLda += gA * Tfin * rom;
-          S0 = fmaf(w, g2.x, S0);
-          S1 = fmaf(w, g2.y, S1);
-          S2 = fmaf(w, g2.z, S2);
-          SD = fmaf(w, g0.w, SD);
+          const float rom = rcp_approx(__fsub_rn(1.0f, a));
+          T[k] = T[k] * rom;  // transmittance in front of this Gaussian
+          const float w = a * T[k];
+          acc[kGR] = fmaf(gC0[k], w, acc[kGR]);
+          acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
+          acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
+          acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
+          const float q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g0.w)));
+          const float dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
+          U[k] = fmaf(w, q, U[k]);
           if (oG < c.alpha_max) {
-            const float G = __expf(power);
-            g[kGOp] = dLda * G;
-            const float dp = dLda * a;  // d alpha / d power = o G = alpha
-            g[kGMx] = dp * (g1.x * dx + g1.y * dy);
-            g[kGMy] = dp * (g1.y * dx + g1.z * dy);
-            g[kGCa] = -0.5f * dp * dx * dx;
-            g[kGCb] = -dp * dx * dy;
-            g[kGCc] = -0.5f * dp * dy * dy;
+            const float dp = dLda * a;  // dL/dpower: d alpha / d power = o G = alpha
+            sdp += dp;
+            const float t = dp * dy;
+            sdy += t;
+            sdy2 = fmaf(t, dy, sdy2);
           }
+        }
+        if (contrib) {
+          // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = p - mu^I, alpha = o exp(power).
+          const float ca = g1.x * (-2.0f * kLn2), cb = g1.y * (-kLn2), cc = g1.z * (-2.0f * kLn2);
+          acc[kGOp] = sdp * rcp_approx(g0.z);  // d alpha / d o = G = alpha / o
+          acc[kGMx] = fmaf(ca * dx, sdp, cb * sdy);
+          acc[kGMy] = fmaf(cb * dx, sdp, cc * sdy);
+          acc[kGCa] = -0.5f * dx * dx * sdp;
+          acc[kGCb] = -dx * sdy;
+          acc[kGCc] = -0.5f * sdy2;
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int s = 0; s < 10; ++s) {
-          float x = g[s];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-          g[s] = x;
-        }
-        if (lane < 10) {
-          float val = g[0];
-#pragma unroll
-          for (int s = 1; s < 10; ++s) val = (lane == s) ? g[s] : val;
-          atomicAdd(g2d + (size_t)s_vi[k] * kG2Stride + lane, val);
-        }
+        const float total = transpose_reduce10(acc, lane);
+        if (slot >= 0 && (lane & 1) == 0)
+          atomicAdd(g2d + (size_t)s_vi[g] * kG2Stride + slot, total);
       }
     }
   }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
                             const uint2* ranges, const uint32_t* pair_vals, const float4* rec0,
                             const float4* rec1, const float4* rec2, float* color, float* depth,
@@ -303,12 +386,13 @@ cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
                             const float* d_color, const float* d_depth, const float* d_alpha,
                             float* g2d, Counters* counters, cudaStream_t stream) {
   if (views.total_tiles == 0) return cudaSuccess;
+  constexpr int kThreads = TW * TH / PPT;
   if (forward) {
-    blend_forward_kernel<TW, TH><<<views.total_tiles, TW * TH, 0, stream>>>(
+    blend_forward_kernel<TW, TH, PPT><<<views.total_tiles, kThreads, 0, stream>>>(
         views, c, ranges, pair_vals, rec0, rec1, rec2, color, depth, alpha, t_final,
         last_index, counters);
   } else {
-    blend_backward_kernel<TW, TH><<<views.total_tiles, TW * TH, 0, stream>>>(
+    blend_backward_kernel<TW, TH, PPT><<<views.total_tiles, kThreads, 0, stream>>>(
         views, c, ranges, pair_vals, rec0, rec1, rec2, t_final, last_index, d_color, d_depth,
         d_alpha, g2d);
   }
@@ -320,14 +404,15 @@ cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
 
 cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
-                             const float4* rec1, int64_t visible_cap, uint32_t capacity,
+                             const float4* rec1, const float4* rec2, int64_t visible_cap,
+                             uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream) {
   if (visible_cap > 0) {
     const unsigned blocks = (unsigned)((visible_cap + kDupThreads - 1) / kDupThreads);
     duplicate_kernel<<<blocks, kDupThreads, 0, stream>>>(views, n, order, offsets, ntiles, rec0,
-                                                         rec1, counters, capacity, keys, vals,
-                                                         counters);
+                                                         rec1, rec2, counters, capacity, keys,
+                                                         vals, counters);
     RGS_LAUNCHED();
   }
   store_pair_count_kernel<<<1, 1, 0, stream>>>(counters, capacity);
@@ -352,15 +437,22 @@ cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, cons
                          float* t_final, int32_t* last_index, const float* d_color,
                          const float* d_depth, const float* d_alpha, float* g2d,
                          Counters* counters, cudaStream_t stream) {
-  const int tw = views.tile_w, th = views.tile_h;
-#define RGS_BLEND(W, H)                                                                          \
-  return launch_blends_t<W, H>(forward, views, c, ranges, pair_vals, rec0, rec1, rec2, color,   \
-                               depth, alpha, t_final, last_index, d_color, d_depth, d_alpha, g2d, \
-                               counters, stream)
-  if (tw == 8 && th == 8) RGS_BLEND(8, 8);
-  if (tw == 32 && th == 8) RGS_BLEND(32, 8);
-  RGS_BLEND(16, 16);
+  const int tw = views.tile_w, th = views.tile_h, ppt = views.pixels_per_thread;
+#define RGS_BLEND(W, H, P)                                                                        \
+  if (tw == W && th == H && ppt == P)                                                             \
+  return launch_blends_t<W, H, P>(forward, views, c, ranges, pair_vals, rec0, rec1, rec2, color, \
+                                  depth, alpha, t_final, last_index, d_color, d_depth, d_alpha,   \
+                                  g2d, counters, stream)
+  RGS_BLEND(16, 16, 1);
+  RGS_BLEND(16, 16, 2);
+  RGS_BLEND(16, 16, 4);
+  RGS_BLEND(8, 8, 1);
+  RGS_BLEND(8, 8, 2);
+  RGS_BLEND(32, 8, 1);
+  RGS_BLEND(32, 8, 2);
+  RGS_BLEND(32, 8, 4);
 #undef RGS_BLEND
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace rgs

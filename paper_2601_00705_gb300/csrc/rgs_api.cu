@@ -36,7 +36,8 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        cudaStream_t stream);
 cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
-                             const float4* rec1, int64_t visible_cap, uint32_t capacity,
+                             const float4* rec1, const float4* rec2, int64_t visible_cap,
+                             uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream);
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
@@ -301,12 +302,17 @@ rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const 
   if (n_views < 1 || n_views > kMaxViews)
     return fail(ctx, RGS_ERR_INVALID_ARG, "n_views must be in 1..RGS_MAX_VIEWS");
   const int tw = cfg.tile_w, th = cfg.tile_h;
+  const int ppt = cfg.pixels_per_thread == 0 ? 4 : cfg.pixels_per_thread;
   if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8)))
     return fail(ctx, RGS_ERR_INVALID_ARG, "tile shape must be 16x16, 8x8 or 32x8");
+  if (!(ppt == 1 || ppt == 2 || ppt == 4) || (tw * th / ppt) % 32 != 0)
+    return fail(ctx, RGS_ERR_INVALID_ARG,
+                "pixels_per_thread must be 1, 2 or 4 with whole warps per tile");
   std::memset(&views, 0, sizeof(views));
   views.n_views = n_views;
   views.tile_w = tw;
   views.tile_h = th;
+  views.pixels_per_thread = ppt;
   long long pix = 0;
   long long tiles = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -392,6 +398,7 @@ void rgs_config_default(rgs_config* cfg) {
   cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.0f;
   cfg->tile_w = 16;
   cfg->tile_h = 16;
+  cfg->pixels_per_thread = 4;
 }
 
 rgs_status rgs_create(rgs_ctx** out, int device) {
@@ -543,8 +550,8 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   }
   const uint32_t capacity = (uint32_t)s->pair_cap;
   // 5. Duplicate (tile, vi) pairs in depth order.
-  RGS_CUDA(launch_duplicate(views, g->n, s->order, s->offsets, s->ntiles, s->rec0, s->rec1, vn,
-                            capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
+  RGS_CUDA(launch_duplicate(views, g->n, s->order, s->offsets, s->ntiles, s->rec0, s->rec1,
+                            s->rec2, vn, capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
            "duplicate");
   RGS_CUDA(mark(ctx, *s, 5, stream, capturing), "event");
   // 6. Stable sort by global tile id.

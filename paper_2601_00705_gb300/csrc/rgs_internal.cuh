@@ -2,8 +2,8 @@
 //
 // Layout in HBM (V views, N Gaussians, "vi" = v * N + i):
 //   rec0[vi] = (mean2d.x, mean2d.y, opacity, depth z)      float4
-//   rec1[vi] = (conic a, conic b, conic c, kappa)          float4, kappa = 2 ln(o / alpha_min)
-//   rec2[vi] = (r, g, b, 0)                                float4
+//   rec1[vi] = (qa, qb, qc, log2 o)                        float4, base-2 conic (see below)
+//   rec2[vi] = (r, g, b, kappa)                            float4, kappa = 2 ln(o / alpha_min)
 //   ntiles[vi]: tiles touched (0 = culled / invisible)
 //   g2d[vi * 12 + s]: screen-space gradient slots (mean2d x/y, conic a/b/c, opacity, rgb, z)
 //   pair list: key = global tile id, value = vi; sorted so that each tile's run is in
@@ -43,6 +43,8 @@ struct Views {
   int total_tiles;
   long long total_pixels;
   int tile_w, tile_h;
+  int pixels_per_thread;    // vertically adjacent pixels per blend thread
+  int pad1;
   ViewParams v[kMaxViews];
 };
 
@@ -116,20 +118,39 @@ __device__ __forceinline__ float dot3_plus_accurate(float r0, float r1, float r2
   return __fadd_rn(p, s);
 }
 
-// Exponent of the 2D Gaussian at offset d = p - mu^I: -1/2 (a dx^2 + c dy^2) - b dx dy.
-// Every operation is explicitly rounded so that the forward and backward blends reproduce the
-// same alpha bit for bit (the backward must re-take the forward's coverage decisions).
-__device__ __forceinline__ float gauss_power(float dx, float dy, float a, float b, float c) {
-  float q = __fmul_rn(a, __fmul_rn(dx, dx));
-  q = __fmaf_rn(c, __fmul_rn(dy, dy), q);
-  q = __fmaf_rn(__fmul_rn(2.0f, b), __fmul_rn(dx, dy), q);
-  return __fmul_rn(-0.5f, q);
+// Hardware base-2 exponential and reciprocal (PTX ex2.approx / rcp.approx): fixed instruction
+// sequences, so every kernel that evaluates the same input gets the same bits.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// o * exp(power), explicitly rounded (see gauss_power).
-__device__ __forceinline__ float gauss_alpha_raw(float o, float power) {
-  return __fmul_rn(o, __expf(power));
+// Coverage of a pixel by a projected Gaussian, alpha = min(alpha_max, o G), with
+// G = exp(-1/2 d^T Q d) and d = p - mu^I. The record stores the conic scaled to base 2,
+// (qa, qb, qc) = -log2(e) (a/2, b, c/2), and lo = log2(o), so that
+//   log2(o G) = (qa dx^2 + lo) + dy (qb dx + qc dy).
+// A thread evaluates one Gaussian for several pixels of one column (same dx): the first bracket
+// and qb dx are computed once, each pixel then costs two FMAs and one ex2. Every operation is
+// explicitly rounded, so the forward and backward blends take identical coverage decisions.
+struct ColumnTerms {
+  float A, B;
+};
+__device__ __forceinline__ ColumnTerms column_terms(float dx, float qa, float qb, float lo) {
+  return ColumnTerms{__fmaf_rn(__fmul_rn(qa, dx), dx, lo), __fmul_rn(qb, dx)};
 }
+__device__ __forceinline__ float opacity_times_gauss(const ColumnTerms& t, float qc, float dy) {
+  return ex2_approx(__fmaf_rn(dy, __fmaf_rn(qc, dy, t.B), t.A));
+}
+
+// Natural-log conic (a, b, c) from the stored base-2 form.
+constexpr float kLn2 = 0.69314718055994531f;
+constexpr float kLog2e = 1.4426950408889634f;
 
 // ------------------------------------------------------------------------------------------
 // Tile coverage of a projected Gaussian: the tiles whose pixel centres may lie inside the
@@ -146,44 +167,61 @@ struct Ellipse {
   float kappa;
 };
 
-__device__ __forceinline__ bool make_ellipse(float4 r0, float4 r1, Ellipse& e) {
-  const float a = r1.x, b = r1.y, c = r1.z;
+// From the stored records: rec0 = (mx, my, o, z), rec1 = base-2 conic and log2 o, rec2.w = kappa.
+__device__ __forceinline__ bool make_ellipse(float4 r0, float4 r1, float4 r2, Ellipse& e) {
+  const float a = __fmul_rn(r1.x, -2.0f * kLn2), b = __fmul_rn(r1.y, -kLn2),
+              c = __fmul_rn(r1.z, -2.0f * kLn2);
   const float detq = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
-  if (!(detq > 0.0f) || !(r1.w >= 0.0f)) return false;
+  if (!(detq > 0.0f) || !(r2.w >= 0.0f)) return false;
   e.mx = r0.x;
   e.my = r0.y;
-  e.sxx = __fdiv_rn(c, detq);
-  e.sxy = __fdiv_rn(-b, detq);
-  e.syy = __fdiv_rn(a, detq);
-  e.kappa = r1.w;
+  const float inv = __fdividef(1.0f, detq);
+  e.sxx = __fmul_rn(c, inv);
+  e.sxy = __fmul_rn(-b, inv);
+  e.syy = __fmul_rn(a, inv);
+  e.kappa = r2.w;
   return true;
 }
 
-// Every operation below is explicitly rounded (no contraction), so the counting pass in the
-// preprocess and the emitting pass in the duplication visit exactly the same tiles.
+// sqrt through the hardware reciprocal square root: not correctly rounded, but a fixed
+// instruction sequence, so every kernel that calls it gets the same bits for the same input.
+__device__ __forceinline__ float sqrt_fixed(float x) {
+  return x > 0.0f ? __fmul_rn(x, rsqrtf(x)) : 0.0f;
+}
+
+// Every operation below is a single instruction with no contraction (explicitly rounded
+// arithmetic, hardware approximations of reciprocals and square roots), so the counting pass in
+// the preprocess and the emitting pass in the duplication visit exactly the same tiles. The
+// approximations err by a few ulp, far inside the 1-pixel padding.
 template <typename RowFn>
 __device__ __forceinline__ void for_each_tile_row(const Ellipse& e, int tile_w, int tile_h,
                                                   int tiles_x, int tiles_y, RowFn&& fn) {
   const float kap = __fadd_rn(__fmul_rn(e.kappa, 1.0001f), 1e-6f);
-  const float rx = __fsqrt_rn(__fmul_rn(kap, e.sxx));
-  const float ry = __fsqrt_rn(__fmul_rn(kap, e.syy));
+  const float rx = sqrt_fixed(__fmul_rn(kap, e.sxx));
+  const float ry = sqrt_fixed(__fmul_rn(kap, e.syy));
+  const float inv_tw = 1.0f / (float)tile_w, inv_th = 1.0f / (float)tile_h;  // powers of two
   const float y_lo = __fsub_rn(__fsub_rn(e.my, ry), kTilePad);
   const float y_hi = __fadd_rn(__fadd_rn(e.my, ry), kTilePad);
   const float x_lo = __fsub_rn(__fsub_rn(e.mx, rx), kTilePad);
   const float x_hi = __fadd_rn(__fadd_rn(e.mx, rx), kTilePad);
-  const float tw = (float)tile_w, th = (float)tile_h;
   // Clamp before converting to int: the extents of near-degenerate Gaussians can be huge.
-  const float fty0 = floorf(fminf(fmaxf(__fdiv_rn(y_lo, th), -1.0f), (float)tiles_y));
-  const float fty1 = floorf(fminf(fmaxf(__fdiv_rn(y_hi, th), -1.0f), (float)tiles_y));
-  const float ftx0 = floorf(fminf(fmaxf(__fdiv_rn(x_lo, tw), -1.0f), (float)tiles_x));
-  const float ftx1 = floorf(fminf(fmaxf(__fdiv_rn(x_hi, tw), -1.0f), (float)tiles_x));
+  const float fty0 = floorf(fminf(fmaxf(__fmul_rn(y_lo, inv_th), -1.0f), (float)tiles_y));
+  const float fty1 = floorf(fminf(fmaxf(__fmul_rn(y_hi, inv_th), -1.0f), (float)tiles_y));
+  const float ftx0 = floorf(fminf(fmaxf(__fmul_rn(x_lo, inv_tw), -1.0f), (float)tiles_x));
+  const float ftx1 = floorf(fminf(fmaxf(__fmul_rn(x_hi, inv_tw), -1.0f), (float)tiles_x));
   const int ty0 = max(0, (int)fty0), ty1 = min(tiles_y - 1, (int)fty1);
   const int bx0 = max(0, (int)ftx0), bx1 = min(tiles_x - 1, (int)ftx1);
   if (ty0 > ty1 || bx0 > bx1) return;
+  if (ty0 == ty1 || bx0 == bx1) {
+    // A single row or column of tiles: the padded box is the answer.
+    for (int ty = ty0; ty <= ty1; ++ty) fn(ty, bx0, bx1);
+    return;
+  }
   // x | y of the ellipse: centre mx + s dy, half-width h sqrt(kap - dy^2 / syy).
-  const float s = __fdiv_rn(e.sxy, e.syy);
-  const float h = __fsqrt_rn(fmaxf(__fsub_rn(e.sxx, __fmul_rn(e.sxy, s)), 0.0f));
-  const float dy_star = __fmul_rn(e.sxy, __fsqrt_rn(__fdiv_rn(kap, e.sxx)));  // rightmost point
+  const float inv_syy = __fdividef(1.0f, e.syy);
+  const float s = __fmul_rn(e.sxy, inv_syy);
+  const float h = sqrt_fixed(__fsub_rn(e.sxx, __fmul_rn(e.sxy, s)));
+  const float dy_star = __fmul_rn(__fmul_rn(e.sxy, rx), __fdividef(1.0f, e.sxx));  // rightmost
   for (int ty = ty0; ty <= ty1; ++ty) {
     const float b0 = fmaxf(__fsub_rn(__fsub_rn((float)(ty * tile_h), kTilePad), e.my), -ry);
     const float b1 =
@@ -198,25 +236,25 @@ __device__ __forceinline__ void for_each_tile_row(const Ellipse& e, int tile_w, 
         xmax = __fadd_rn(e.mx, rx);
       } else {
         const float d = fminf(fmaxf(dy_star, b0), b1);
-        const float hw = __fmul_rn(
-            h, __fsqrt_rn(fmaxf(__fsub_rn(kap, __fdiv_rn(__fmul_rn(d, d), e.syy)), 0.0f)));
+        const float hw =
+            __fmul_rn(h, sqrt_fixed(__fsub_rn(kap, __fmul_rn(__fmul_rn(d, d), inv_syy))));
         xmax = __fadd_rn(__fadd_rn(e.mx, __fmul_rn(s, d)), hw);
       }
       if (-dy_star >= b0 && -dy_star <= b1) {
         xmin = __fsub_rn(e.mx, rx);
       } else {
         const float d = fminf(fmaxf(-dy_star, b0), b1);
-        const float hw = __fmul_rn(
-            h, __fsqrt_rn(fmaxf(__fsub_rn(kap, __fdiv_rn(__fmul_rn(d, d), e.syy)), 0.0f)));
+        const float hw =
+            __fmul_rn(h, sqrt_fixed(__fsub_rn(kap, __fmul_rn(__fmul_rn(d, d), inv_syy))));
         xmin = __fsub_rn(__fadd_rn(e.mx, __fmul_rn(s, d)), hw);
       }
       xmax = __fadd_rn(xmax, kTilePad);
       xmin = __fsub_rn(xmin, kTilePad);
     }
     const int tx0 =
-        max(bx0, (int)floorf(fminf(fmaxf(__fdiv_rn(xmin, tw), -1.0f), (float)tiles_x)));
+        max(bx0, (int)floorf(fminf(fmaxf(__fmul_rn(xmin, inv_tw), -1.0f), (float)tiles_x)));
     const int tx1 =
-        min(bx1, (int)floorf(fminf(fmaxf(__fdiv_rn(xmax, tw), -1.0f), (float)tiles_x)));
+        min(bx1, (int)floorf(fminf(fmaxf(__fmul_rn(xmax, inv_tw), -1.0f), (float)tiles_x)));
     if (tx0 <= tx1) fn(ty, tx0, tx1);
   }
 }
@@ -257,8 +295,9 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixBins = 256;
 
 inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
-// Scratch for a sort of up to n_cap elements: histogram table and scan block sums (u32 counts).
-inline int64_t sort_hist_entries(int64_t n_cap) { return sort_blocks(n_cap) * kRadixBins; }
+// Scratch for a sort of up to n_cap elements: the digit-major histogram table plus one row
+// total per digit (u32 counts).
+inline int64_t sort_hist_entries(int64_t n_cap) { return (sort_blocks(n_cap) + 1) * kRadixBins; }
 
 // Stable LSD radix sort of (keys, vals) by bits [begin_bit, end_bit); ping-pongs between the
 // (keys, vals) and (keys_alt, vals_alt) buffers and returns in *result_in_alt whether the

@@ -170,10 +170,16 @@ cudaError_t run_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_de
 }
 
 // ------------------------------------------------------------------------------------------
-// Radix sort. Each block owns kSortTile consecutive keys; warp w of the block owns the
-// contiguous sub-range [w * 32 * kSortItems, (w + 1) * 32 * kSortItems) and walks it in rounds
-// of 32 keys (lane l takes element r * 32 + l), so warp order, round order and lane order
-// together follow the input order, which makes the ranks stable.
+// Radix sort, three kernels per pass:
+//   upsweep   per-block digit counts, stored digit-major: hist[d * n_blocks + b];
+//   row scan  one block per digit: exclusive scan of its row over the blocks, row total into
+//             hist[256 * n_blocks + d];
+//   downsweep stable ranks inside the block, a local sort through shared memory, then
+//             coalesced stores of each digit's run to its global offset.
+// Each block owns kSortTile consecutive keys; warp w of the block owns the contiguous sub-range
+// [w * 32 * kSortItems, (w + 1) * 32 * kSortItems) and walks it in rounds of 32 keys (lane l
+// takes element r * 32 + l), so warp order, round order and lane order together follow the
+// input order, which makes the ranks stable.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint32_t* keys,
                                                                      int64_t n_cap,
@@ -194,17 +200,47 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
     }
   }
   __syncthreads();
-  // Digit-major table: an exclusive scan over it yields each (digit, block) scatter offset.
   for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads)
     hist[(int64_t)d * n_blocks + blockIdx.x] = counts[d];
 }
 
+__global__ void __launch_bounds__(kSortThreads) radix_row_scan_kernel(uint32_t* hist,
+                                                                      int64_t n_blocks) {
+  const int d = blockIdx.x;
+  uint32_t* row = hist + (int64_t)d * n_blocks;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n_blocks; base += kSortThreads * 4) {
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * 4 + k;
+      v[k] = idx < n_blocks ? row[idx] : 0u;
+      s += v[k];
+    }
+    uint32_t chunk_total;
+    uint32_t pre = block_exclusive_scan<kSortThreads>(s, &chunk_total);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * 4 + k;
+      if (idx < n_blocks) row[idx] = carry + pre;
+      pre += v[k];
+    }
+    carry += chunk_total;
+  }
+  if (threadIdx.x == 0) hist[(int64_t)kRadixBins * n_blocks + d] = carry;
+}
+
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
-    int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* offsets,
+    int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* hist,
     int64_t n_blocks) {
+  static_assert(kSortThreads == kRadixBins, "one thread per digit in the digit scans");
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t warp_counts[kWarps][kRadixBins];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_digit_start[kRadixBins];   // block-local start of each digit's run
+  __shared__ int64_t s_digit_shift[kRadixBins];    // global position minus local position
   const uint32_t n = read_count(n_dev, n_cap);
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;
@@ -231,8 +267,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     rank[r] = valid ? prior + before : 0xffffffffu;
   }
   __syncthreads();
-  // Exclusive prefix over warps, per digit: keys of earlier warps come first.
-  for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) {
+  {
+    // Thread d: exclusive prefix of digit d over the warps, then the block-local and the
+    // global start of digit d's run.
+    const int d = threadIdx.x;
     uint32_t acc = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
@@ -240,16 +278,29 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
       warp_counts[w][d] = acc;
       acc += c;
     }
+    const uint32_t local_start = block_exclusive_scan<kSortThreads>(acc, nullptr);
+    const uint32_t row_total = hist[(int64_t)kRadixBins * n_blocks + d];
+    const uint32_t digit_base = block_exclusive_scan<kSortThreads>(row_total, nullptr);
+    s_digit_start[d] = local_start;
+    s_digit_shift[d] = (int64_t)digit_base + hist[(int64_t)d * n_blocks + blockIdx.x] -
+                       (int64_t)local_start;
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     if (rank[r] == 0xffffffffu) continue;
     const uint32_t digit = (key[r] >> shift) & mask;
-    const uint32_t pos =
-        offsets[(int64_t)digit * n_blocks + blockIdx.x] + warp_counts[warp][digit] + rank[r];
-    keys_out[pos] = key[r];
-    if (vals_out) vals_out[pos] = val[r];
+    const uint32_t local = s_digit_start[digit] + warp_counts[warp][digit] + rank[r];
+    s_keys[local] = key[r];
+    s_vals[local] = val[r];
+  }
+  __syncthreads();
+  const int count = (int)min((int64_t)kSortTile, (int64_t)n - base);
+  for (int t = threadIdx.x; t < count; t += kSortThreads) {
+    const uint32_t k = s_keys[t];
+    const int64_t pos = s_digit_shift[(k >> shift) & mask] + t;
+    keys_out[pos] = k;
+    if (vals_out) vals_out[pos] = s_vals[t];
   }
 }
 
@@ -279,6 +330,7 @@ cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
                               uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
                               int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
                               bool* result_in_alt, cudaStream_t stream) {
+  (void)block_sums;
   *result_in_alt = false;
   const int64_t nb = sort_blocks(n_cap);
   if (nb == 0 || end_bit <= begin_bit) return cudaSuccess;
@@ -293,9 +345,8 @@ cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
     radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(kin, n_cap, n_dev, shift,
                                                                     mask, hist, nb);
     RGS_LAUNCHED();
-    cudaError_t err = launch_exclusive_scan(hist, hist, nb * kRadixBins, nullptr, nullptr,
-                                            block_sums, stream);
-    if (err != cudaSuccess) return err;
+    radix_row_scan_kernel<<<kRadixBins, kSortThreads, 0, stream>>>(hist, nb);
+    RGS_LAUNCHED();
     radix_downsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
         kin, vin, kout, vout, n_cap, n_dev, shift, mask, hist, nb);
     RGS_LAUNCHED();

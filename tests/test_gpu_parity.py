@@ -89,12 +89,14 @@ def test_tiny_forward_and_all_gradients():
     print("tiny", info, errs, gpu["stats"])
 
 
-@pytest.mark.parametrize("tile", [(8, 8), (32, 8)])
-def test_tile_shape_does_not_change_results(tile):
+@pytest.mark.parametrize("tile", [(16, 16, 1), (16, 16, 2), (8, 8, 1), (8, 8, 2), (32, 8, 1),
+                                  (32, 8, 2), (32, 8, 4)])
+def test_tile_shape_and_pixels_per_thread_do_not_change_results(tile):
     wl = synthetic.tiny(seed=77)
     g, orc0, d_color, _ = _oracle_l1_case(wl)
-    ref = gpu_render(g, wl.cameras, d_color=d_color)
-    out = gpu_render(g, wl.cameras, d_color=d_color, tile_w=tile[0], tile_h=tile[1])
+    ref = gpu_render(g, wl.cameras, d_color=d_color)  # default: 16x16 tiles, 4 pixels per thread
+    out = gpu_render(g, wl.cameras, d_color=d_color, tile_w=tile[0], tile_h=tile[1],
+                     pixels_per_thread=tile[2])
     # Per-pixel compositing does not depend on the binning: the forward is bit-identical.
     for k in ("color", "depth", "alpha"):
         np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
