@@ -86,6 +86,8 @@ def _load():
             lib.oracle_render.argtypes = [I, I, P, P, P, P, P, I, P, P, P, I, I,
                                           P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.oracle_render.restype = I
+            lib.oracle_set_dense_limit.argtypes = [ctypes.c_double]
+            lib.oracle_set_dense_limit.restype = None
             _lib = lib
     return _lib
 
@@ -132,6 +134,11 @@ def _degree_of(sh) -> int:
 
 def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
+
+
+def set_dense_limit(nbytes: float) -> None:
+    """Byte limit of the dense per-thread gradient accumulators (above it: hash maps)."""
+    _load().oracle_set_dense_limit(float(nbytes))
 
 
 def sh_basis(degree: int, dirs) -> np.ndarray:

@@ -43,6 +43,7 @@
  * Jacobian clamp, the colour clamp), the pixel is flagged so that parity tests can leave it out.
  */
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -50,6 +51,7 @@
 #include <functional>
 #include <limits>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 namespace {
@@ -299,6 +301,33 @@ void gaussian_forward(const double* mean, const double* log_scale, const double*
   f.valid = true;
 }
 
+// The per-(view, Gaussian) quantities compositing needs (the backward recomputes the rest).
+struct Splat {
+  bool valid = false;
+  int flags = 0;
+  float zkey = 0.0f;
+  double mean2d[2], cov2d[3], conic[3], opacity, rgb[3], z;
+};
+
+Splat to_splat(const GaussFwd& f) {
+  Splat s;
+  s.valid = f.valid;
+  s.flags = f.flags;
+  s.zkey = f.zkey;
+  s.mean2d[0] = f.mean2d[0];
+  s.mean2d[1] = f.mean2d[1];
+  s.cov2d[0] = f.cov2d[0][0];
+  s.cov2d[1] = f.cov2d[0][1];
+  s.cov2d[2] = f.cov2d[1][1];
+  for (int k = 0; k < 3; ++k) {
+    s.conic[k] = f.conic[k];
+    s.rgb[k] = f.rgb[k];
+  }
+  s.opacity = f.opacity;
+  s.z = f.z;
+  return s;
+}
+
 // Screen-space gradient slots per (view, Gaussian).
 enum G2 { kMx = 0, kMy, kCa, kCb, kCc, kOp, kR, kG, kB, kZ, kG2Count };
 
@@ -425,6 +454,26 @@ void gaussian_backward(const GaussFwd& f, const double* mean, const double* sh, 
   g_pose[5] += Mx[1][0] - Mx[0][1];
 }
 
+// Per-thread screen-space gradient accumulators (dense array or hash map of touched Gaussians).
+struct DenseAcc {
+  std::vector<double> data;
+  void reset(int n) { data.assign(static_cast<size_t>(n) * kG2Count, 0.0); }
+  double* slots(int idx) { return data.data() + static_cast<size_t>(idx) * kG2Count; }
+};
+struct SparseAcc {
+  std::unordered_map<int, std::array<double, kG2Count>> map;
+  void reset(int) { map.clear(); }
+  double* slots(int idx) {
+    auto it = map.find(idx);
+    if (it == map.end()) {
+      std::array<double, kG2Count> z;
+      z.fill(0.0);
+      it = map.emplace(idx, z).first;
+    }
+    return it->second.data();
+  }
+};
+
 struct PixelOut {
   double color[3], depth, alpha, t_final;
   int n_contrib;
@@ -437,10 +486,10 @@ struct Cand {
 };
 
 // Composites one pixel (Eq. alpha). If `grad` is non-null, accumulates the screen-space gradients
-// of <g, outputs> into acc[idx * kG2Count + slot].
-void shade_pixel(const std::vector<GaussFwd>& F, const std::vector<int>& cands,
-                 double px, double py, const Config& cfg, PixelOut& out, const double* g /*5*/,
-                 double* acc) {
+// of <g, outputs> into the accumulator `acc` (slot kG2Count * idx + s).
+template <typename Acc>
+void shade_pixel(const std::vector<Splat>& F, const std::vector<int>& cands, double px, double py,
+                 const Config& cfg, PixelOut& out, const double* g /*5*/, Acc* acc) {
   struct Hit {
     float zkey;
     double z;
@@ -451,7 +500,7 @@ void shade_pixel(const std::vector<GaussFwd>& F, const std::vector<int>& cands,
   hits.reserve(cands.size());
   const double lo = cfg.alpha_min * (1.0 - cfg.margin_alpha);
   for (int idx : cands) {
-    const GaussFwd& f = F[idx];
+    const Splat& f = F[idx];
     if (!f.valid) continue;
     const double dx = px - f.mean2d[0], dy = py - f.mean2d[1];
     const double power = -0.5 * (f.conic[0] * dx * dx + f.conic[2] * dy * dy) - f.conic[1] * dx * dy;
@@ -507,7 +556,7 @@ void shade_pixel(const std::vector<GaussFwd>& F, const std::vector<int>& cands,
   double SD = 0.0;                                                    // sum over k > j of w_k z_k
   for (int j = n - 1; j >= 0; --j) {
     const Hit& h = hits[inc[j]];
-    const GaussFwd& f = F[h.idx];
+    const Splat& f = F[h.idx];
     const double Tj = Tpre[j];
     const double wj = h.alpha * Tj;
     const double om = 1.0 - h.alpha;
@@ -515,7 +564,7 @@ void shade_pixel(const std::vector<GaussFwd>& F, const std::vector<int>& cands,
     for (int ch = 0; ch < 3; ++ch) dL_dalpha += gC[ch] * (f.rgb[ch] * Tj - SC[ch] / om);
     dL_dalpha += gD * (h.z * Tj - SD / om);
     dL_dalpha += gA * TN / om;
-    double* a = acc + static_cast<size_t>(h.idx) * kG2Count;
+    double* a = acc->slots(h.idx);
     a[kR] += gC[0] * wj;
     a[kG] += gC[1] * wj;
     a[kB] += gC[2] * wj;
@@ -569,6 +618,10 @@ Camera read_camera(const double* c) {
   return cam;
 }
 
+// Largest total size of the dense per-thread accumulators before the oracle switches to hash
+// maps (settable for tests through oracle_set_dense_limit).
+double g_dense_limit_bytes = static_cast<double>(1u << 30);
+
 // Runs fn(thread, item) for item in [0, n_items) on n_threads threads (dynamic assignment;
 // callers make every result independent of which thread ran an item).
 void run_parallel(int n_threads, int n_items, const std::function<void(int, int)>& fn) {
@@ -591,6 +644,9 @@ void run_parallel(int n_threads, int n_items, const std::function<void(int, int)
 }  // namespace
 
 extern "C" {
+
+// Sets the byte limit of the dense per-thread gradient accumulators (results do not depend on it).
+void oracle_set_dense_limit(double bytes) { g_dense_limit_bytes = bytes; }
 
 // Real SH basis for n unit directions dirs[n,3] -> Y[n,16] (unused entries zero).
 void oracle_sh_basis(int degree, int n, const double* dirs, double* Y) {
@@ -673,8 +729,14 @@ int oracle_render(int n, int degree, const double* means, const double* log_scal
     std::memset(g_sh, 0, sizeof(double) * 3 * K * n);
     std::memset(g_pose, 0, sizeof(double) * 6 * n_views);
   }
-  std::vector<GaussFwd> F(n);
-  std::vector<std::vector<double>> acc(backward ? n_threads : 0);
+  std::vector<Splat> F(n);
+  // Per-thread screen-space gradient accumulators: dense arrays when they fit in 1 GiB in
+  // total, else hash maps of the Gaussians a thread's pixels touch (large scenes, few pixels).
+  const bool sparse = backward && static_cast<double>(n) * kG2Count * sizeof(double) * n_threads >
+                                      g_dense_limit_bytes;
+  std::vector<DenseAcc> dense(backward && !sparse ? n_threads : 0);
+  std::vector<SparseAcc> hashed(backward && sparse ? n_threads : 0);
+  std::vector<double> g2all(backward ? static_cast<size_t>(n) * kG2Count : 0);
   size_t pix_base = 0;
   for (int v = 0; v < n_views; ++v) {
     const Camera cam = read_camera(cams + 18 * v);
@@ -682,9 +744,12 @@ int oracle_render(int n, int degree, const double* means, const double* log_scal
     // Per-Gaussian forward quantities for this view.
     run_parallel(n_threads, (n + 1023) / 1024, [&](int, int blk) {
       const int i0 = blk * 1024, i1 = std::min(n, i0 + 1024);
-      for (int i = i0; i < i1; ++i)
+      GaussFwd f;
+      for (int i = i0; i < i1; ++i) {
         gaussian_forward(means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
-                         sh + static_cast<size_t>(3 * K) * i, degree, cam, cfg, F[i]);
+                         sh + static_cast<size_t>(3 * K) * i, degree, cam, cfg, f);
+        F[i] = to_splat(f);
+      }
     });
     // Candidate lists: a 16x16-pixel cell grid over the padded bounding box of the
     // alpha >= alpha_min ellipse (an accelerator only: candidates are tested exactly per pixel).
@@ -697,12 +762,12 @@ int oracle_render(int n, int degree, const double* means, const double* log_scal
         if (F[i].valid) all_valid.push_back(i);
     } else {
       for (int i = 0; i < n; ++i) {
-        const GaussFwd& f = F[i];
+        const Splat& f = F[i];
         if (!f.valid) continue;
         const double kap = 2.0 * std::log(f.opacity / (cfg.alpha_min * (1.0 - cfg.margin_alpha)));
         if (!(kap >= 0.0)) continue;
-        const double rx = std::sqrt(kap * f.cov2d[0][0]) + 2.0;
-        const double ry = std::sqrt(kap * f.cov2d[1][1]) + 2.0;
+        const double rx = std::sqrt(kap * f.cov2d[0]) + 2.0;
+        const double ry = std::sqrt(kap * f.cov2d[2]) + 2.0;
         const double x0 = f.mean2d[0] - rx, x1 = f.mean2d[0] + rx;
         const double y0 = f.mean2d[1] - ry, y1 = f.mean2d[1] + ry;
         if (x1 < 0.0 || y1 < 0.0 || x0 > W - 1.0 || y0 > H - 1.0) continue;
@@ -714,8 +779,10 @@ int oracle_render(int n, int degree, const double* means, const double* log_scal
           for (int cx = cx0; cx <= cx1; ++cx) cells[static_cast<size_t>(cy) * gx + cx].push_back(i);
       }
     }
-    if (backward)
-      for (auto& a : acc) a.assign(static_cast<size_t>(n) * kG2Count, 0.0);
+    if (backward) {
+      for (auto& a : dense) a.reset(n);
+      for (auto& a : hashed) a.reset(n);
+    }
     // Pixels. Thread t owns the rows y with y % n_threads == t, so the per-thread gradient
     // sums (and hence the results) do not depend on scheduling.
     run_parallel(n_threads, n_threads, [&](int, int tid) {
@@ -726,17 +793,19 @@ int oracle_render(int n, int degree, const double* means, const double* log_scal
         const std::vector<int>& cand =
             brute_force ? all_valid : cells[static_cast<size_t>(y / cell) * gx + (x / cell)];
         double g[5] = {0, 0, 0, 0, 0};
-        bool has_g = false;
         if (backward) {
           if (d_color)
             for (int ch = 0; ch < 3; ++ch) g[ch] = d_color[3 * p + ch];
           if (d_depth) g[3] = d_depth[p];
           if (d_alpha) g[4] = d_alpha[p];
-          has_g = true;
         }
         PixelOut po;
-        shade_pixel(F, cand, static_cast<double>(x), static_cast<double>(y), cfg, po,
-                    has_g ? g : nullptr, has_g ? acc[tid].data() : nullptr);
+        if (!backward)
+          shade_pixel<DenseAcc>(F, cand, x, y, cfg, po, nullptr, nullptr);
+        else if (sparse)
+          shade_pixel(F, cand, x, y, cfg, po, g, &hashed[tid]);
+        else
+          shade_pixel(F, cand, x, y, cfg, po, g, &dense[tid]);
         for (int ch = 0; ch < 3; ++ch) color[3 * p + ch] = po.color[ch];
         depth[p] = po.depth;
         alpha[p] = po.alpha;
@@ -746,24 +815,38 @@ int oracle_render(int n, int degree, const double* means, const double* log_scal
       }
     });
     if (backward) {
-      // Sum the per-thread screen-space gradients in thread order, then chain per Gaussian.
+      // Sum the per-thread screen-space gradients in thread order.
+      std::fill(g2all.begin(), g2all.end(), 0.0);
+      if (sparse) {
+        for (int t = 0; t < n_threads; ++t)
+          for (const auto& kv : hashed[t].map)
+            for (int s = 0; s < kG2Count; ++s)
+              g2all[static_cast<size_t>(kv.first) * kG2Count + s] += kv.second[s];
+      } else {
+        run_parallel(n_threads, (n + 1023) / 1024, [&](int, int blk) {
+          const size_t i0 = static_cast<size_t>(blk) * 1024;
+          const size_t i1 = std::min(static_cast<size_t>(n), i0 + 1024);
+          for (int t = 0; t < n_threads; ++t)
+            for (size_t j = i0 * kG2Count; j < i1 * kG2Count; ++j) g2all[j] += dense[t].data[j];
+        });
+      }
+      // Chain each touched Gaussian (forward quantities recomputed in full).
       const int n_blk = (n + 1023) / 1024;
       std::vector<double> pose_part(static_cast<size_t>(n_blk) * 6, 0.0);
       run_parallel(n_threads, n_blk, [&](int, int blk) {
         const int i0 = blk * 1024, i1 = std::min(n, i0 + 1024);
+        GaussFwd f;
         for (int i = i0; i < i1; ++i) {
-          double g2[kG2Count] = {0};
+          const double* g2 = g2all.data() + static_cast<size_t>(i) * kG2Count;
           bool any = false;
-          for (int t = 0; t < n_threads; ++t)
-            for (int s = 0; s < kG2Count; ++s) {
-              g2[s] += acc[t][static_cast<size_t>(i) * kG2Count + s];
-              any = any || g2[s] != 0.0;
-            }
+          for (int s = 0; s < kG2Count; ++s) any = any || g2[s] != 0.0;
           if (g_2d)
             for (int s = 0; s < kG2Count; ++s)
               g_2d[(static_cast<size_t>(v) * n + i) * kG2Count + s] = g2[s];
           if (!any || !F[i].valid) continue;
-          gaussian_backward(F[i], means + 3 * i, sh + static_cast<size_t>(3 * K) * i, degree, cam,
+          gaussian_forward(means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
+                           sh + static_cast<size_t>(3 * K) * i, degree, cam, cfg, f);
+          gaussian_backward(f, means + 3 * i, sh + static_cast<size_t>(3 * K) * i, degree, cam,
                             g2, g_means + 3 * i, g_log_scales + 3 * i, g_quats + 4 * i,
                             g_logits + i, g_sh + static_cast<size_t>(3 * K) * i,
                             pose_part.data() + 6 * blk);

@@ -7,6 +7,8 @@
 // thread recomputes each view's projection, chains that view's screen-space gradients to the
 // parameters, sums over views in registers (so every parameter gradient is written once, with no
 // atomics), and reduces the per-view twist gradient over the block.
+#include <algorithm>
+
 #include "rgs_internal.cuh"
 
 namespace rgs {
@@ -319,237 +321,285 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
 }
 
 // ------------------------------------------------------------------------------------------
-// Backward.
+// Backward, phase 1: one thread per visible (view, Gaussian) entry (grid-stride over the
+// compacted list). Chains the entry's screen-space gradients through Eq. proj and the colour
+// model to the view-dependent quantities that phase 2 needs, and reduces the view's twist
+// gradient over the block. The entry's gradient record is overwritten with
+//   [0..2] dL/dmu^W (projection and viewing-direction paths), [3..8] dL/dSigma^W (xx, xy, xz,
+//   yy, yz, zz; off-diagonal entries hold the sum of both symmetric partners), [9..11] dL/d(raw
+//   colour) after the clamp, [12] dL/do.
 // ------------------------------------------------------------------------------------------
+enum ViewSlot { kVMean = 0, kVSigma = 3, kVRgb = 9, kVOpacity = 12 };
+
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(
+__global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, const float* __restrict__ sh,
-    const uint32_t* __restrict__ ntiles, float* __restrict__ g2d, uint32_t grad_mask,
-    float* __restrict__ d_means, float* __restrict__ d_log_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_logits, float* __restrict__ d_sh, float* __restrict__ pose_partial) {
+    const uint32_t* __restrict__ order, const Counters* __restrict__ counters,
+    float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ pose_partial) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int kWarps = kPreThreads / 32;
-  __shared__ float red[kWarps][6];
-  const int i = blockIdx.x * kPreThreads + threadIdx.x;
-  const bool in_range = i < n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, shc[3 * K];
-  float logit = 0.0f;
+  __shared__ float s_pose[kMaxViews * 6];
+  const int nv = views.n_views;
+  for (int t = threadIdx.x; t < nv * 6; t += kPreThreads) s_pose[t] = 0.0f;
+  __syncthreads();
+  const uint32_t n_visible = counters->n_visible;
+  for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_visible;
+       k += gridDim.x * kPreThreads) {
+    const uint32_t vi = order[k];
+    const int v = (int)(vi / (uint32_t)n);
+    const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
+    float m[3], ls[3], q[4], shc[3 * K];
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) shc[k] = 0.0f;
-  if (in_range) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      m[k] = __ldg(means + 3 * (size_t)i + k);
-      ls[k] = __ldg(log_scales + 3 * (size_t)i + k);
+    for (int a = 0; a < 3; ++a) {
+      m[a] = __ldg(means + 3 * (size_t)i + a);
+      ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
     }
     const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
     q[0] = q4.x;
     q[1] = q4.y;
     q[2] = q4.z;
     q[3] = q4.w;
-    logit = __ldg(logits + i);
     load_sh<DEG>(sh, i, shc);
-  }
-  GaussianLocal g;
-  gaussian_local(m, ls, q, logit, g);
-
-  float gm[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
-  float gsh[3 * K];
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0f;
-  bool any_visible = false;
-  // Gradient of Sigma^W summed over views (chained to scale / rotation once at the end).
-  float gSw[6] = {0, 0, 0, 0, 0, 0};  // xx, xy, xz, yy, yz, zz (symmetric, off-diagonals once)
-
-  for (int v = 0; v < views.n_views; ++v) {
+    GaussianLocal g;
+    gaussian_local(m, ls, q, __ldg(logits + i), g);
     const ViewParams& vp = views.v[v];
-    float pose[6] = {0, 0, 0, 0, 0, 0};
-    const size_t vi = (size_t)v * n + i;
-    if (in_range && ntiles[vi] > 0u) {
-      any_visible = true;
-      float* gp = g2d + vi * kG2Stride;
-      const float4 ga = *reinterpret_cast<const float4*>(gp);
-      const float4 gb = *reinterpret_cast<const float4*>(gp + 4);
-      const float2 gc = *reinterpret_cast<const float2*>(gp + 8);
-      // Consume: leave the accumulator zeroed for the next backward.
-      *reinterpret_cast<float4*>(gp) = make_float4(0.f, 0.f, 0.f, 0.f);
-      *reinterpret_cast<float4*>(gp + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
-      *reinterpret_cast<float2*>(gp + 8) = make_float2(0.f, 0.f);
-      const float g_mx = ga.x, g_my = ga.y, g_ca = ga.z, g_cb = ga.w;
-      const float g_cc = gb.x, g_op = gb.y, g_r = gb.z, g_g = gb.w;
-      const float g_b = gc.x, g_zo = gc.y;
-      ViewProj p;
-      project_view(g, vp, c, p);
-      const float* R = vp.R;
-      // Opacity.
-      glogit += g_op * g.opacity * (1.0f - g.opacity);
-      // Conic -> Sigma^I: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]].
-      const float a = p.conic[0], b = p.conic[1], cc = p.conic[2];
-      const float hb = 0.5f * g_cb;
-      const float P00 = a * g_ca + b * hb, P01 = a * hb + b * g_cc;
-      const float P10 = b * g_ca + cc * hb, P11 = b * hb + cc * g_cc;
-      const float GS00 = -(P00 * a + P01 * b);
-      const float GS01 = -(P00 * b + P01 * cc);
-      const float GS11 = -(P10 * b + P11 * cc);
-      // Sigma^I = T Sigma^W T^T: G_T = 2 G_S (T Sigma^W); G_SigmaW += T^T G_S T.
-      float GT[6];
+    float* gp = g2d + (size_t)vi * kG2Stride;
+    const float4 ga = *reinterpret_cast<const float4*>(gp);
+    const float4 gb = *reinterpret_cast<const float4*>(gp + 4);
+    const float2 gc2 = *reinterpret_cast<const float2*>(gp + 8);
+    const float g_mx = ga.x, g_my = ga.y, g_ca = ga.z, g_cb = ga.w;
+    const float g_cc = gb.x, g_op = gb.y, g_r = gb.z, g_g = gb.w;
+    const float g_b = gc2.x, g_zo = gc2.y;
+    ViewProj p;
+    project_view(g, vp, c, p);
+    const float* R = vp.R;
+    // Conic -> Sigma^I: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]].
+    const float a = p.conic[0], b = p.conic[1], cc = p.conic[2];
+    const float hb = 0.5f * g_cb;
+    const float P00 = a * g_ca + b * hb, P01 = a * hb + b * g_cc;
+    const float P10 = b * g_ca + cc * hb, P11 = b * hb + cc * g_cc;
+    const float GS00 = -(P00 * a + P01 * b);
+    const float GS01 = -(P00 * b + P01 * cc);
+    const float GS11 = -(P10 * b + P11 * cc);
+    // Sigma^I = T Sigma^W T^T: G_T = 2 G_S (T Sigma^W); G_SigmaW = T^T G_S T.
+    float GT[6], U[6];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        GT[k] = 2.0f * (GS00 * p.TS[k] + GS01 * p.TS[3 + k]);
-        GT[3 + k] = 2.0f * (GS01 * p.TS[k] + GS11 * p.TS[3 + k]);
-      }
-      {
-        // (T^T G_S T)_{ab} = sum_rs T_ra GS_rs T_sb.
-        float U[6];  // G_S T, row-major 2x3
+    for (int a2 = 0; a2 < 3; ++a2) {
+      GT[a2] = 2.0f * (GS00 * p.TS[a2] + GS01 * p.TS[3 + a2]);
+      GT[3 + a2] = 2.0f * (GS01 * p.TS[a2] + GS11 * p.TS[3 + a2]);
+      U[a2] = GS00 * p.T[a2] + GS01 * p.T[3 + a2];
+      U[3 + a2] = GS01 * p.T[a2] + GS11 * p.T[3 + a2];
+    }
+    float out[13];
+    out[kVSigma + 0] = p.T[0] * U[0] + p.T[3] * U[3];
+    out[kVSigma + 1] = 2.0f * (p.T[0] * U[1] + p.T[3] * U[4]);
+    out[kVSigma + 2] = 2.0f * (p.T[0] * U[2] + p.T[3] * U[5]);
+    out[kVSigma + 3] = p.T[1] * U[1] + p.T[4] * U[4];
+    out[kVSigma + 4] = 2.0f * (p.T[1] * U[2] + p.T[4] * U[5]);
+    out[kVSigma + 5] = p.T[2] * U[2] + p.T[5] * U[5];
+    // T = J R: G_J = G_T R^T (all six entries, the structural zeros of J included).
+    float GJ[6];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          U[k] = GS00 * p.T[k] + GS01 * p.T[3 + k];
-          U[3 + k] = GS01 * p.T[k] + GS11 * p.T[3 + k];
-        }
-        gSw[0] += p.T[0] * U[0] + p.T[3] * U[3];
-        gSw[1] += 2.0f * (p.T[0] * U[1] + p.T[3] * U[4]);
-        gSw[2] += 2.0f * (p.T[0] * U[2] + p.T[3] * U[5]);
-        gSw[3] += p.T[1] * U[1] + p.T[4] * U[4];
-        gSw[4] += 2.0f * (p.T[1] * U[2] + p.T[4] * U[5]);
-        gSw[5] += p.T[2] * U[2] + p.T[5] * U[5];
-      }
-      // T = J R: G_J = G_T R^T (all six entries, the structural zeros of J included).
-      float GJ[6];
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int a2 = 0; a2 < 3; ++a2)
+        GJ[3 * r + a2] = GT[3 * r] * R[3 * a2] + GT[3 * r + 1] * R[3 * a2 + 1] +
+                         GT[3 * r + 2] * R[3 * a2 + 2];
+    // J(mu^C), with no gradient through a clamped x/z or y/z.
+    const float z = p.mc[2], rz = 1.0f / z, rz2 = rz * rz;
+    const float g_z = -vp.fx * rz2 * GJ[0] - vp.fy * rz2 * GJ[4] + vp.fx * p.uc * rz2 * GJ[2] +
+                      vp.fy * p.wc * rz2 * GJ[5];
+    float g_u = p.u_cl ? 0.0f : -vp.fx * rz * GJ[2];
+    float g_w = p.w_cl ? 0.0f : -vp.fy * rz * GJ[5];
+    // mu^I = (fx u + cx, fy w + cy); u = x/z, w = y/z; depth output z.
+    g_u += g_mx * vp.fx;
+    g_w += g_my * vp.fy;
+    float gmc[3];
+    gmc[0] = g_u * rz;
+    gmc[1] = g_w * rz;
+    gmc[2] = g_z - (g_u * p.mc[0] + g_w * p.mc[1]) * rz2 + g_zo;
+    // mu^C = R mu^W + t.
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-          GJ[3 * r + k] = GT[3 * r] * R[3 * k] + GT[3 * r + 1] * R[3 * k + 1] +
-                          GT[3 * r + 2] * R[3 * k + 2];
-      // J(mu^C), with no gradient through a clamped x/z or y/z.
-      const float z = p.mc[2], rz = 1.0f / z, rz2 = rz * rz;
-      float g_z = -vp.fx * rz2 * GJ[0] - vp.fy * rz2 * GJ[4] + vp.fx * p.uc * rz2 * GJ[2] +
-                  vp.fy * p.wc * rz2 * GJ[5];
-      float g_u = p.u_cl ? 0.0f : -vp.fx * rz * GJ[2];
-      float g_w = p.w_cl ? 0.0f : -vp.fy * rz * GJ[5];
-      // mu^I = (fx u + cx, fy w + cy).
-      g_u += g_mx * vp.fx;
-      g_w += g_my * vp.fy;
-      // u = x/z, w = y/z; depth output z.
-      float gmc[3];
-      gmc[0] = g_u * rz;
-      gmc[1] = g_w * rz;
-      gmc[2] = g_z - (g_u * p.mc[0] + g_w * p.mc[1]) * rz2 + g_zo;
-      // mu^C = R mu^W + t.
+    for (int a2 = 0; a2 < 3; ++a2)
+      out[kVMean + a2] = R[a2] * gmc[0] + R[3 + a2] * gmc[1] + R[6 + a2] * gmc[2];
+    // Colour: rgb = max(sum_k sh_k Y_k(dir) + 0.5, 0), dir = normalize(mu^W - c_W).
+    float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
+          d2 = g.m[2] - vp.cam_center[2];
+    const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 *= rn;
+    d1 *= rn;
+    d2 *= rn;
+    float Y[16];
+    sh_basis<DEG>(d0, d1, d2, Y);
+    float graw[3] = {g_r, g_g, g_b};
 #pragma unroll
-      for (int k = 0; k < 3; ++k) gm[k] += R[k] * gmc[0] + R[3 + k] * gmc[1] + R[6 + k] * gmc[2];
-      // Colour: rgb = max(sum_k sh_k Y_k(dir) + 0.5, 0), dir = normalize(mu^W - c_W).
-      float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
-            d2 = g.m[2] - vp.cam_center[2];
-      const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-      d0 *= rn;
-      d1 *= rn;
-      d2 *= rn;
-      float Y[16];
-      sh_basis<DEG>(d0, d1, d2, Y);
-      float graw[3] = {g_r, g_g, g_b};
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.5f;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc += shc[3 * k + ch] * Y[k];
-        if (!(acc > 0.0f)) graw[ch] = 0.0f;
-      }
+      for (int kk = 0; kk < K; ++kk) acc += shc[3 * kk + ch] * Y[kk];
+      if (!(acc > 0.0f)) graw[ch] = 0.0f;
+      out[kVRgb + ch] = graw[ch];
+    }
+    float gd[3] = {0.0f, 0.0f, 0.0f};
+    if (DEG > 0) {
       float wk[16];
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        gsh[3 * k + 0] += graw[0] * Y[k];
-        gsh[3 * k + 1] += graw[1] * Y[k];
-        gsh[3 * k + 2] += graw[2] * Y[k];
-        wk[k] = graw[0] * shc[3 * k] + graw[1] * shc[3 * k + 1] + graw[2] * shc[3 * k + 2];
-      }
-      float gd[3] = {0.0f, 0.0f, 0.0f};
-      if (DEG > 0) {
-        float gx, gy, gz;
-        sh_basis_vjp<DEG>(d0, d1, d2, wk, gx, gy, gz);
-        const float dd = gx * d0 + gy * d1 + gz * d2;
-        gd[0] = (gx - d0 * dd) * rn;
-        gd[1] = (gy - d1 * dd) * rn;
-        gd[2] = (gz - d2 * dd) * rn;
-        gm[0] += gd[0];
-        gm[1] += gd[1];
-        gm[2] += gd[2];
-      }
+      for (int kk = 0; kk < K; ++kk)
+        wk[kk] = graw[0] * shc[3 * kk] + graw[1] * shc[3 * kk + 1] + graw[2] * shc[3 * kk + 2];
+      float gx, gy, gz;
+      sh_basis_vjp<DEG>(d0, d1, d2, wk, gx, gy, gz);
+      const float dd = gx * d0 + gy * d1 + gz * d2;
+      gd[0] = (gx - d0 * dd) * rn;
+      gd[1] = (gy - d1 * dd) * rn;
+      gd[2] = (gz - d2 * dd) * rn;
+    }
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2) out[kVMean + a2] += gd[a2];
+    out[kVOpacity] = g_op;
+    // Overwrite the record for phase 2 (13 of its 16 slots).
+    *reinterpret_cast<float4*>(gp) = make_float4(out[0], out[1], out[2], out[3]);
+    *reinterpret_cast<float4*>(gp + 4) = make_float4(out[4], out[5], out[6], out[7]);
+    *reinterpret_cast<float4*>(gp + 8) = make_float4(out[8], out[9], out[10], out[11]);
+    gp[12] = out[12];
+    if (grad_mask & RGS_GRAD_POSE) {
       // Twist of the left update (Eq. leftupdate, Eq. muCjac, Eq. sigmaIjac):
       //   rho   = dL/dmu^C + R dL/d(dir-vector)            (the camera centre moves with -R^T t)
       //   omega = mu^C x dL/dmu^C + skew part of J^T G_J   (rotation of Sigma^I, dR = [w]_x R)
+      float pose[6];
       pose[0] = gmc[0] + R[0] * gd[0] + R[1] * gd[1] + R[2] * gd[2];
       pose[1] = gmc[1] + R[3] * gd[0] + R[4] * gd[1] + R[5] * gd[2];
       pose[2] = gmc[2] + R[6] * gd[0] + R[7] * gd[1] + R[8] * gd[2];
       pose[3] = p.mc[1] * gmc[2] - p.mc[2] * gmc[1] + p.J02 * GJ[1] + p.J12 * GJ[4] - p.J11 * GJ[5];
       pose[4] = p.mc[2] * gmc[0] - p.mc[0] * gmc[2] + p.J00 * GJ[2] - p.J02 * GJ[0] - p.J12 * GJ[3];
       pose[5] = p.mc[0] * gmc[1] - p.mc[1] * gmc[0] + p.J11 * GJ[3] - p.J00 * GJ[1];
-    }
-    if (grad_mask & RGS_GRAD_POSE) {
-      // Block reduction of the view's twist gradient -> one partial per (block, view).
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        float x = pose[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        pose[k] = x;
-      }
-      if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[warp][k] = pose[k];
-      __syncthreads();
-      if (threadIdx.x < 6) {
-        float s = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
-        pose_partial[((size_t)blockIdx.x * views.n_views + v) * 6 + threadIdx.x] = s;
-      }
-      __syncthreads();
+      for (int a2 = 0; a2 < 6; ++a2) atomicAdd(&s_pose[v * 6 + a2], pose[a2]);
     }
   }
-  if (!in_range) return;
-  // A Gaussian culled in every view (behind the near plane, degenerate or non-finite) gets zero
-  // gradients; its local quantities may be non-finite and must not enter the chain below.
-  const bool need_cov = any_visible && (grad_mask & (RGS_GRAD_SCALES | RGS_GRAD_QUATS)) != 0;
-  if (need_cov) {
-    // Sigma^W = M M^T, M = Rq diag(s): G_M = 2 G_Sym M with G_Sym the symmetric matrix whose
-    // off-diagonal entries are half the accumulated off-diagonal gradients.
-    const float S00 = gSw[0], S01 = 0.5f * gSw[1], S02 = 0.5f * gSw[2];
-    const float S11 = gSw[3], S12 = 0.5f * gSw[4], S22 = gSw[5];
-    float GM[9];
+  if (grad_mask & RGS_GRAD_POSE) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nv * 6; t += kPreThreads)
+      pose_partial[(size_t)blockIdx.x * nv * 6 + t] = s_pose[t];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward, phase 2: one thread per Gaussian. Sums the phase-1 records of the views that see
+// the Gaussian (and clears them for the next backward), accumulates the SH coefficient
+// gradients view by view, and chains dL/dSigma^W to the log-scales and the quaternion once.
+// Every parameter gradient is written exactly once.
+// ------------------------------------------------------------------------------------------
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
+    const __grid_constant__ Views views, int n, const float* __restrict__ means,
+    const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ logits, const uint32_t* __restrict__ ntiles,
+    float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ d_means,
+    float* __restrict__ d_log_scales, float* __restrict__ d_quats, float* __restrict__ d_logits,
+    float* __restrict__ d_sh) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const int i = blockIdx.x * kPreThreads + threadIdx.x;
+  if (i >= n) return;
+  float m[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      GM[k] = 2.0f * (S00 * g.M[k] + S01 * g.M[3 + k] + S02 * g.M[6 + k]);
-      GM[3 + k] = 2.0f * (S01 * g.M[k] + S11 * g.M[3 + k] + S12 * g.M[6 + k]);
-      GM[6 + k] = 2.0f * (S02 * g.M[k] + S12 * g.M[3 + k] + S22 * g.M[6 + k]);
+  for (int a = 0; a < 3; ++a) m[a] = __ldg(means + 3 * (size_t)i + a);
+  float gm[3] = {0, 0, 0}, gSw[6] = {0, 0, 0, 0, 0, 0}, gop = 0.0f;
+  float gsh[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0f;
+  bool any_visible = false;
+  for (int v = 0; v < views.n_views; ++v) {
+    const size_t vi = (size_t)v * n + i;
+    if (ntiles[vi] == 0u) continue;
+    any_visible = true;
+    float* gp = g2d + vi * kG2Stride;
+    const float4 r0 = *reinterpret_cast<const float4*>(gp);
+    const float4 r1 = *reinterpret_cast<const float4*>(gp + 4);
+    const float4 r2 = *reinterpret_cast<const float4*>(gp + 8);
+    const float r3 = gp[12];
+    // Consume: leave the record zeroed for the next backward.
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(gp) = zero;
+    *reinterpret_cast<float4*>(gp + 4) = zero;
+    *reinterpret_cast<float4*>(gp + 8) = zero;
+    gp[12] = 0.0f;
+    gm[0] += r0.x;
+    gm[1] += r0.y;
+    gm[2] += r0.z;
+    gSw[0] += r0.w;
+    gSw[1] += r1.x;
+    gSw[2] += r1.y;
+    gSw[3] += r1.z;
+    gSw[4] += r1.w;
+    gSw[5] += r2.x;
+    gop += r3;
+    if (grad_mask & RGS_GRAD_SH) {
+      const ViewParams& vp = views.v[v];
+      float d0 = m[0] - vp.cam_center[0], d1 = m[1] - vp.cam_center[1],
+            d2 = m[2] - vp.cam_center[2];
+      const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      float Y[16];
+      sh_basis<DEG>(d0 * rn, d1 * rn, d2 * rn, Y);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        gsh[3 * k + 0] += r2.y * Y[k];
+        gsh[3 * k + 1] += r2.z * Y[k];
+        gsh[3 * k + 2] += r2.w * Y[k];
+      }
     }
+  }
+  float gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
+  // A Gaussian culled in every view gets zero gradients; its local quantities may be
+  // non-finite and must not enter the chain below.
+  if (any_visible) {
+    float ls[3], q[4];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      gls[k] = (GM[k] * g.Rq[k] + GM[3 + k] * g.Rq[3 + k] + GM[6 + k] * g.Rq[6 + k]) * g.s[k];
-    float G[9];
+    for (int a = 0; a < 3; ++a) ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
+    q[0] = q4.x;
+    q[1] = q4.y;
+    q[2] = q4.z;
+    q[3] = q4.w;
+    GaussianLocal g;
+    gaussian_local(m, ls, q, __ldg(logits + i), g);
+    glogit = gop * g.opacity * (1.0f - g.opacity);
+    if (grad_mask & (RGS_GRAD_SCALES | RGS_GRAD_QUATS)) {
+      // Sigma^W = M M^T, M = Rq diag(s): G_M = 2 G_Sym M with G_Sym the symmetric matrix whose
+      // off-diagonal entries are half the accumulated off-diagonal gradients.
+      const float S00 = gSw[0], S01 = 0.5f * gSw[1], S02 = 0.5f * gSw[2];
+      const float S11 = gSw[3], S12 = 0.5f * gSw[4], S22 = gSw[5];
+      float GM[9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 3; ++k) {
+        GM[k] = 2.0f * (S00 * g.M[k] + S01 * g.M[3 + k] + S02 * g.M[6 + k]);
+        GM[3 + k] = 2.0f * (S01 * g.M[k] + S11 * g.M[3 + k] + S12 * g.M[6 + k]);
+        GM[6 + k] = 2.0f * (S02 * g.M[k] + S12 * g.M[3 + k] + S22 * g.M[6 + k]);
+      }
 #pragma unroll
-      for (int b = 0; b < 3; ++b) G[3 * a + b] = GM[3 * a + b] * g.s[b];
-    const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
-    const float gw = 2.0f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
-    const float gx = 2.0f * (y * G[1] + z * G[2] + y * G[3] - 2.0f * x * G[4] - w * G[5] +
-                             z * G[6] + w * G[7] - 2.0f * x * G[8]);
-    const float gy = 2.0f * (-2.0f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] -
-                             w * G[6] + z * G[7] - 2.0f * y * G[8]);
-    const float gz = 2.0f * (-2.0f * z * G[0] - w * G[1] + x * G[2] + w * G[3] -
-                             2.0f * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
-    // Normalisation q / |q|.
-    const float dot = gw * w + gx * x + gy * y + gz * z;
-    const float iq = 1.0f / g.qnorm;
-    gq[0] = (gw - w * dot) * iq;
-    gq[1] = (gx - x * dot) * iq;
-    gq[2] = (gy - y * dot) * iq;
-    gq[3] = (gz - z * dot) * iq;
+      for (int k = 0; k < 3; ++k)
+        gls[k] = (GM[k] * g.Rq[k] + GM[3 + k] * g.Rq[3 + k] + GM[6 + k] * g.Rq[6 + k]) * g.s[k];
+      float G[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) G[3 * a + b] = GM[3 * a + b] * g.s[b];
+      const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+      const float gw = 2.0f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+      const float gx = 2.0f * (y * G[1] + z * G[2] + y * G[3] - 2.0f * x * G[4] - w * G[5] +
+                               z * G[6] + w * G[7] - 2.0f * x * G[8]);
+      const float gy = 2.0f * (-2.0f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] -
+                               w * G[6] + z * G[7] - 2.0f * y * G[8]);
+      const float gz = 2.0f * (-2.0f * z * G[0] - w * G[1] + x * G[2] + w * G[3] -
+                               2.0f * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+      // Normalisation q / |q|.
+      const float dot = gw * w + gx * x + gy * y + gz * z;
+      const float iq = 1.0f / g.qnorm;
+      gq[0] = (gw - w * dot) * iq;
+      gq[1] = (gx - x * dot) * iq;
+      gq[2] = (gy - y * dot) * iq;
+      gq[3] = (gz - z * dot) * iq;
+    }
   }
   if ((grad_mask & RGS_GRAD_MEANS) && d_means)
 #pragma unroll
@@ -619,32 +669,51 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   return cudaGetLastError();
 }
 
-int preprocess_backward_blocks(int n) { return (n + kPreThreads - 1) / kPreThreads; }
+// Phase-1 grid: a fixed number of blocks (grid-stride over the visible entries), so the
+// per-block twist partials stay small at any scene size.
+int preprocess_backward_blocks(int64_t vn) {
+  const int64_t need = (vn + kPreThreads - 1) / kPreThreads;
+  return (int)std::min<int64_t>(std::max<int64_t>(need, 1), 8 * 152);
+}
 
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, const uint32_t* ntiles,
-                                       float* g2d, uint32_t grad_mask, float* d_means,
-                                       float* d_log_scales, float* d_quats, float* d_logits,
-                                       float* d_sh, float* pose_partial, float* d_pose,
-                                       cudaStream_t stream) {
-  const int blocks = preprocess_backward_blocks(g.n);
-  if (blocks > 0) {
-#define RGS_PRE_BWD(D)                                                                       \
-  preprocess_backward_kernel<D><<<blocks, kPreThreads, 0, stream>>>(                         \
-      views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, ntiles, g2d,   \
-      grad_mask, d_means, d_log_scales, d_quats, d_logits, d_sh, pose_partial)
+                                       const uint32_t* order, const Counters* counters,
+                                       int64_t vn, float* g2d, uint32_t grad_mask,
+                                       float* d_means, float* d_log_scales, float* d_quats,
+                                       float* d_logits, float* d_sh, float* pose_partial,
+                                       float* d_pose, cudaStream_t stream) {
+  const int blocks1 = preprocess_backward_blocks(vn);
+  if (g.n > 0) {
+#define RGS_BWD_VIEW(D)                                                                      \
+  backward_view_kernel<D><<<blocks1, kPreThreads, 0, stream>>>(                              \
+      views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, order, counters, \
+      g2d, grad_mask, pose_partial)
     switch (g.sh_degree) {
-      case 0: RGS_PRE_BWD(0); break;
-      case 1: RGS_PRE_BWD(1); break;
-      case 2: RGS_PRE_BWD(2); break;
-      default: RGS_PRE_BWD(3); break;
+      case 0: RGS_BWD_VIEW(0); break;
+      case 1: RGS_BWD_VIEW(1); break;
+      case 2: RGS_BWD_VIEW(2); break;
+      default: RGS_BWD_VIEW(3); break;
     }
     RGS_LAUNCHED();
-#undef RGS_PRE_BWD
+#undef RGS_BWD_VIEW
+    const int blocks2 = (g.n + kPreThreads - 1) / kPreThreads;
+#define RGS_BWD_GAUSS(D)                                                                      \
+  backward_gaussian_kernel<D><<<blocks2, kPreThreads, 0, stream>>>(                           \
+      views, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, ntiles, g2d, grad_mask,   \
+      d_means, d_log_scales, d_quats, d_logits, d_sh)
+    switch (g.sh_degree) {
+      case 0: RGS_BWD_GAUSS(0); break;
+      case 1: RGS_BWD_GAUSS(1); break;
+      case 2: RGS_BWD_GAUSS(2); break;
+      default: RGS_BWD_GAUSS(3); break;
+    }
+    RGS_LAUNCHED();
+#undef RGS_BWD_GAUSS
   }
   if ((grad_mask & RGS_GRAD_POSE) && d_pose) {
-    if (blocks > 0) {
-      pose_finalize_kernel<<<views.n_views * 6, 256, 0, stream>>>(pose_partial, blocks,
+    if (g.n > 0) {
+      pose_finalize_kernel<<<views.n_views * 6, 256, 0, stream>>>(pose_partial, blocks1,
                                                                   views.n_views, d_pose);
       RGS_LAUNCHED();
     } else {

@@ -27,13 +27,14 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
                                       float4* rec2, uint32_t* ntiles, Counters* counters,
                                       cudaStream_t stream);
-int preprocess_backward_blocks(int n);
+int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, const uint32_t* ntiles,
-                                       float* g2d, uint32_t grad_mask, float* d_means,
-                                       float* d_log_scales, float* d_quats, float* d_logits,
-                                       float* d_sh, float* pose_partial, float* d_pose,
-                                       cudaStream_t stream);
+                                       const uint32_t* order, const Counters* counters,
+                                       int64_t vn, float* g2d, uint32_t grad_mask,
+                                       float* d_means, float* d_log_scales, float* d_quats,
+                                       float* d_logits, float* d_sh, float* pose_partial,
+                                       float* d_pose, cudaStream_t stream);
 cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
                              const float4* rec1, const float4* rec2, int64_t visible_cap,
@@ -488,7 +489,7 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   st = get_or_create_state(ctx, handle, &s);
   if (st != RGS_OK) return st;
   s->has_forward = false;
-  const int64_t pose_entries = (int64_t)preprocess_backward_blocks(g->n) * n_views * 6;
+  const int64_t pose_entries = (int64_t)preprocess_backward_blocks(vn) * n_views * 6;
   st = ensure_vn(ctx, *s, vn, pose_entries, capturing, stream);
   if (st != RGS_OK) return st;
   st = ensure_pix_tiles(ctx, *s, views.total_pixels, views.total_tiles, capturing);
@@ -621,8 +622,9 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_gr
                         s->g2d, s->counters, stream),
            "blend backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 1, stream, capturing), "event");
-  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->ntiles, s->g2d, grad_mask,
-                                      d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->ntiles, s->order,
+                                      s->counters, s->vn, s->g2d, grad_mask, d_means,
+                                      d_log_scales, d_quats, d_opacity_logits, d_sh,
                                       s->pose_partial, d_pose, stream),
            "preprocess backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 2, stream, capturing), "event");

@@ -5,7 +5,8 @@
 //   rec1[vi] = (qa, qb, qc, log2 o)                        float4, base-2 conic (see below)
 //   rec2[vi] = (r, g, b, kappa)                            float4, kappa = 2 ln(o / alpha_min)
 //   ntiles[vi]: tiles touched (0 = culled / invisible)
-//   g2d[vi * 12 + s]: screen-space gradient slots (mean2d x/y, conic a/b/c, opacity, rgb, z)
+//   g2d[vi * 16 + s]: screen-space gradient slots (mean2d x/y, conic a/b/c, opacity, rgb, z),
+//              reused by the backward preprocess for its per-view intermediate results
 //   pair list: key = global tile id, value = vi; sorted so that each tile's run is in
 //              (depth, index) order; ranges[gtile] = [first, last + 1) of the run.
 #pragma once
@@ -18,7 +19,7 @@
 namespace rgs {
 
 constexpr int kMaxViews = RGS_MAX_VIEWS;
-constexpr int kG2Stride = 12;  // floats per (view, Gaussian) screen-space gradient record
+constexpr int kG2Stride = 16;  // floats per (view, Gaussian) gradient record (64 bytes)
 
 // Screen-space gradient slots.
 enum G2Slot { kGMx = 0, kGMy, kGCa, kGCb, kGCc, kGOp, kGR, kGG, kGB, kGZ };

@@ -253,6 +253,21 @@ def test_thread_count_changes_only_summation_order():
         np.testing.assert_array_equal(b[k], c[k], err_msg=k)
 
 
+def test_sparse_accumulators_equal_dense_ones():
+    g, cams = _tiny_scene(9)
+    up = np.random.default_rng(4).standard_normal((48 * 36, 3))
+    mask = synthetic.patch_mask(cams, fraction=0.3, patch=8, seed=1)
+    a = oracle.render(g, cams, d_color=up, pixel_mask=mask, threads=3)
+    oracle.set_dense_limit(0.0)
+    try:
+        b = oracle.render(g, cams, d_color=up, pixel_mask=mask, threads=3)
+    finally:
+        oracle.set_dense_limit(float(1 << 30))
+    for k in ("color", "g_means", "g_log_scales", "g_quats", "g_opacity_logits", "g_sh", "g_pose"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert np.abs(a["g_means"]).sum() > 0
+
+
 def test_input_permutation_invariance():
     g, cams = _tiny_scene(12)
     n = g["means"].shape[0]
