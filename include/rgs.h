@@ -213,6 +213,20 @@ rgs_status rgs_set_phase_timing(rgs_ctx* ctx, int32_t enable);
  * the pair list. */
 rgs_status rgs_phase_times(rgs_ctx* ctx, uint64_t state, float* ms, int32_t n, void* stream);
 
+/* ---- Diagnostics: copies of a state's binning results (synchronise `stream`). ----
+ * rgs_copy_tile_lists: the sorted pair list (the (view, Gaussian) index vi = view * n + i of each
+ * pair, tile runs in near-to-far order) into host_vals (capacity vals_cap entries; the number of
+ * pairs is written to *n_pairs even when it exceeds vals_cap, in which case nothing is copied),
+ * and the [first, last + 1) range of every global tile into host_ranges (2 u32 per tile; global
+ * tile ids count view by view, row-major inside a view).
+ * rgs_copy_records: the projected records of every (view, Gaussian) into host_rec
+ * ([n_views * n][12] floats: mean2d hi x, y, lo x, y; base-2 conic qa, qb, qc and log2 o;
+ * r, g, b and camera-space depth), and the touched-tile counts into host_ntiles (may be NULL). */
+rgs_status rgs_copy_tile_lists(rgs_ctx* ctx, uint64_t state, uint32_t* host_vals, int64_t vals_cap,
+                               uint32_t* host_ranges, int64_t* n_pairs, void* stream);
+rgs_status rgs_copy_records(rgs_ctx* ctx, uint64_t state, float* host_rec, uint32_t* host_ntiles,
+                            void* stream);
+
 /* ---- Primitives of the binning stage, exposed for testing (Section 3.1: the front-to-back
  * ordered covering set is built by a key sort). Device pointers, caller-owned. ---- */
 

@@ -43,13 +43,15 @@ DEFAULT_CONFIG = dict(
     margin_z=1e-12,
     margin_g=1e-5,
     margin_effect=1e-5,
+    margin_cont=3e-5,
 )
 
 # Pixel ambiguity bits (see rgs_oracle.cpp). FORWARD_AMBIGUOUS marks pixels whose rendered values
 # an FP32 renderer may legitimately compute differently; BACKWARD_AMBIGUOUS adds gradient kinks.
-AMB_ALPHA_MIN, AMB_ALPHA_MAX, AMB_T_MIN, AMB_DEPTH_TIE, AMB_NEAR, AMB_GRAD_KINK = 1, 2, 4, 8, 16, 32
-FORWARD_AMBIGUOUS = AMB_ALPHA_MIN | AMB_T_MIN | AMB_DEPTH_TIE | AMB_NEAR
-BACKWARD_AMBIGUOUS = 63
+AMB_ALPHA_MIN, AMB_ALPHA_MAX, AMB_T_MIN, AMB_DEPTH_TIE, AMB_NEAR, AMB_GRAD_KINK, AMB_COND = (
+    1, 2, 4, 8, 16, 32, 64)
+FORWARD_AMBIGUOUS = AMB_ALPHA_MIN | AMB_T_MIN | AMB_DEPTH_TIE | AMB_NEAR | AMB_COND
+BACKWARD_AMBIGUOUS = 127
 
 _lock = threading.Lock()
 _lib = None
@@ -121,7 +123,8 @@ def _cfg_array(config) -> np.ndarray:
     bg = tuple(c["bg"])
     return np.array([c["alpha_min"], c["alpha_max"], c["t_min"], c["znear"], c["eps2d"],
                      c["jac_clamp"], bg[0], bg[1], bg[2], c["margin_alpha"], c["margin_t"],
-                     c["margin_z"], c["margin_g"], c["margin_effect"]], dtype=np.float64)
+                     c["margin_z"], c["margin_g"], c["margin_effect"], c["margin_cont"]],
+                    dtype=np.float64)
 
 
 def _degree_of(sh) -> int:

@@ -67,6 +67,7 @@ struct Config {
   double margin_g;      // relative margin for per-Gaussian branch points (znear, clamps)
   double margin_effect; // smallest image change a flipped alpha_min decision must be able to
                         // cause for the pixel to be flagged
+  double margin_cont;   // largest float32 error bound of a pixel's colour tolerated unflagged
 };
 
 struct Camera {
@@ -85,7 +86,16 @@ enum AmbiguityBits {
   kAmbDepthTie = 8,     // a covering Gaussian's depth within margin_z of a float32 rounding midpoint
   kAmbNear = 16,        // a covering Gaussian's depth within margin_g of znear (cull decision)
   kAmbGradKink = 32,    // a covering Gaussian at the Jacobian clamp or colour clamp (gradient kink)
+  kAmbCond = 64,        // the float32 evaluation error bound of the pixel exceeds margin_cont
 };
+
+// Unit roundoff of float32. A float32 renderer evaluates ln(o G) at a pixel with an error of a
+// few units of it times the magnitude of the quadratic form's terms, plus the error of the conic
+// itself, which grows like sqrt(cond(Sigma^I)) times |ln G| (rounding J, R and the scales perturbs
+// the thin axis of the projected ellipse by that much). The oracle uses this bound, with a
+// safety factor of 8, to widen its decision margins and to flag pixels whose float32 value
+// cannot be expected within the tolerance.
+constexpr double kUnitRoundoff32 = 5.9604644775390625e-08;
 
 // ---------------------------------------------------------------------------------------------
 // Real spherical harmonics, degree <= 3 (Appendix C.1, Eq. app-sh).
@@ -307,6 +317,7 @@ struct Splat {
   int flags = 0;
   float zkey = 0.0f;
   double mean2d[2], cov2d[3], conic[3], opacity, rgb[3], z;
+  double cond_sqrt;  // sqrt of the condition number of Sigma^I (dilation included)
 };
 
 Splat to_splat(const GaussFwd& f) {
@@ -325,6 +336,14 @@ Splat to_splat(const GaussFwd& f) {
   }
   s.opacity = f.opacity;
   s.z = f.z;
+  s.cond_sqrt = 1.0;
+  if (f.valid) {
+    const double tr = f.cov2d[0][0] + f.cov2d[1][1];
+    const double disc = std::sqrt(std::max(0.25 * tr * tr - f.det, 0.0));
+    const double lmax = 0.5 * tr + disc;
+    const double lmin = f.det / lmax;
+    s.cond_sqrt = std::sqrt(lmax / lmin);
+  }
   return s;
 }
 
@@ -495,19 +514,23 @@ void shade_pixel(const std::vector<Splat>& F, const std::vector<int>& cands, dou
     double z;
     int idx;
     double G, oG, alpha, dx, dy;
+    double err;  // float32 error bound of ln(o G) at this pixel
   };
   std::vector<Hit> hits;
   hits.reserve(cands.size());
-  const double lo = cfg.alpha_min * (1.0 - cfg.margin_alpha);
+  const double ln_amin = std::log(cfg.alpha_min), ln_amax = std::log(cfg.alpha_max);
   for (int idx : cands) {
     const Splat& f = F[idx];
     if (!f.valid) continue;
     const double dx = px - f.mean2d[0], dy = py - f.mean2d[1];
     const double power = -0.5 * (f.conic[0] * dx * dx + f.conic[2] * dy * dy) - f.conic[1] * dx * dy;
+    const double mag = 0.5 * (std::fabs(f.conic[0]) * dx * dx + std::fabs(f.conic[2]) * dy * dy) +
+                       std::fabs(f.conic[1] * dx * dy);
+    const double err = kUnitRoundoff32 * (8.0 * mag + 8.0 * std::fabs(power) * f.cond_sqrt + 16.0);
     const double G = std::exp(power);
     const double oG = f.opacity * G;
-    if (oG < lo) continue;
-    hits.push_back({f.zkey, f.z, idx, G, oG, std::min(cfg.alpha_max, oG), dx, dy});
+    if (std::log(oG) < ln_amin - cfg.margin_alpha - err) continue;
+    hits.push_back({f.zkey, f.z, idx, G, oG, std::min(cfg.alpha_max, oG), dx, dy, err});
   }
   std::sort(hits.begin(), hits.end(), [](const Hit& a, const Hit& b) {
     return a.zkey < b.zkey || (a.zkey == b.zkey && a.idx < b.idx);
@@ -515,29 +538,36 @@ void shade_pixel(const std::vector<Splat>& F, const std::vector<int>& cands, dou
   uint8_t amb = 0;
   double T = 1.0;
   double C[3] = {0, 0, 0}, D = 0.0;
+  double errT = 0.0;  // float32 error bound of ln T
+  double errC = 0.0;  // float32 error bound of the colour
   std::vector<int> inc;  // positions in `hits` of the included Gaussians
   for (size_t k = 0; k < hits.size(); ++k) {
     const Hit& h = hits[k];
     const double* c = F[h.idx].rgb;
     const double cmax = std::max(1.0, std::max(c[0], std::max(c[1], c[2])));
+    const double ln_oG = std::log(h.oG);
     // Including or skipping a Gaussian at the threshold changes the image by about alpha_min T c.
-    if (std::fabs(h.oG - cfg.alpha_min) <= cfg.margin_alpha * cfg.alpha_min &&
+    if (std::fabs(ln_oG - ln_amin) <= cfg.margin_alpha + h.err &&
         cfg.alpha_min * T * cmax >= cfg.margin_effect)
       amb |= kAmbAlphaMin;
     if (h.oG < cfg.alpha_min) continue;
     if (F[h.idx].flags & 8) amb |= kAmbDepthTie;
     if (F[h.idx].flags & 1) amb |= kAmbNear;
     if (F[h.idx].flags & 6) amb |= kAmbGradKink;
-    if (std::fabs(h.oG - cfg.alpha_max) <= cfg.margin_alpha * cfg.alpha_max) amb |= kAmbAlphaMax;
+    if (std::fabs(ln_oG - ln_amax) <= cfg.margin_alpha + h.err) amb |= kAmbAlphaMax;
     const double Tn = T * (1.0 - h.alpha);
-    if (std::fabs(Tn - cfg.t_min) <= cfg.margin_t * cfg.t_min) amb |= kAmbTMin;
+    const double errTn = errT + h.err * h.alpha / (1.0 - h.alpha);
+    if (std::fabs(std::log(Tn / cfg.t_min)) <= cfg.margin_t + errTn) amb |= kAmbTMin;
     if (Tn < cfg.t_min) break;
     const double w = h.alpha * T;
+    errC += w * cmax * (h.err + errT);
     for (int ch = 0; ch < 3; ++ch) C[ch] += w * F[h.idx].rgb[ch];
     D += w * h.z;
     T = Tn;
+    errT = errTn;
     inc.push_back(static_cast<int>(k));
   }
+  if (errC > cfg.margin_cont) amb |= kAmbCond;
   for (int ch = 0; ch < 3; ++ch) out.color[ch] = C[ch] + T * cfg.bg[ch];
   out.depth = D;
   out.alpha = 1.0 - T;
@@ -601,6 +631,7 @@ Config read_config(const double* c) {
   cfg.margin_z = c[11];
   cfg.margin_g = c[12];
   cfg.margin_effect = c[13];
+  cfg.margin_cont = c[14];
   return cfg;
 }
 
@@ -697,8 +728,8 @@ void oracle_project(int n, int degree, const double* means, const double* log_sc
 /*
  * Renders n_views views and optionally back-propagates upstream image gradients.
  *   cams[V, 18]: width, height, fx, fy, cx, cy, R (row-major 3x3), t (world-to-camera).
- *   cfg[14]: alpha_min, alpha_max, t_min, znear, eps2d, jac_clamp, bg[3], margin_alpha,
- *            margin_t, margin_z, margin_g, margin_effect.
+ *   cfg[15]: alpha_min, alpha_max, t_min, znear, eps2d, jac_clamp, bg[3], margin_alpha,
+ *            margin_t, margin_z, margin_g, margin_effect, margin_cont.
  *   Images are concatenated over views, view v row-major at pixel offset sum_{u<v} W_u H_u.
  *   pixel_mask[P] (nullable): only pixels with a non-zero mask are rendered / back-propagated.
  *   brute_force != 0: every Gaussian is a candidate at every pixel (no bounding-box skip).

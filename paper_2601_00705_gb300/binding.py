@@ -25,7 +25,8 @@ GRAD_ALL = 63
 EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_render_forward", "rgs_render_backward", "rgs_release_state", "rgs_reserve",
             "rgs_query_stats", "rgs_set_phase_timing", "rgs_phase_times", "rgs_radix_sort_u32",
-            "rgs_exclusive_scan_u32", "rgs_exclusive_scan_u32_static")
+            "rgs_exclusive_scan_u32", "rgs_exclusive_scan_u32_static", "rgs_copy_tile_lists",
+            "rgs_copy_records")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -107,6 +108,8 @@ def load(build_if_needed: bool = True):
             "rgs_radix_sort_u32": (S, [P, P, P, I64, I32, I32, P]),
             "rgs_exclusive_scan_u32": (S, [P, P, P, I64, P, P]),
             "rgs_exclusive_scan_u32_static": (S, [P, P, I64, P, P]),
+            "rgs_copy_tile_lists": (S, [P, U64, P, I64, P, ctypes.POINTER(I64), P]),
+            "rgs_copy_records": (S, [P, U64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -220,6 +223,28 @@ class Context:
         self._check(self.lib.rgs_phase_times(self.handle, ctypes.c_uint64(state), ms, len(PHASES),
                                              ctypes.c_void_p(stream)))
         return dict(zip(PHASES, [float(x) for x in ms]))
+
+    def tile_lists(self, state: int, total_tiles: int, stream: int = 0):
+        """(pair values [P] u32, ranges [total_tiles, 2] u32) of a state's sorted pair list."""
+        n = ctypes.c_int64()
+        self._check(self.lib.rgs_copy_tile_lists(self.handle, ctypes.c_uint64(state), None, 0,
+                                                 None, ctypes.byref(n), ctypes.c_void_p(stream)))
+        vals = np.zeros(max(n.value, 1), dtype=np.uint32)
+        ranges = np.zeros((max(total_tiles, 1), 2), dtype=np.uint32)
+        self._check(self.lib.rgs_copy_tile_lists(
+            self.handle, ctypes.c_uint64(state), vals.ctypes.data_as(ctypes.c_void_p), vals.size,
+            ranges.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n), ctypes.c_void_p(stream)))
+        return vals[:n.value], ranges[:total_tiles]
+
+    def records(self, state: int, vn: int, stream: int = 0):
+        """(records [vn, 12] f32, tile counts [vn] u32) of a state."""
+        rec = np.zeros((max(vn, 1), 12), dtype=np.float32)
+        nt = np.zeros(max(vn, 1), dtype=np.uint32)
+        self._check(self.lib.rgs_copy_records(self.handle, ctypes.c_uint64(state),
+                                              rec.ctypes.data_as(ctypes.c_void_p),
+                                              nt.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.c_void_p(stream)))
+        return rec[:vn], nt[:vn]
 
     def radix_sort_u32(self, keys: int, vals: int, n: int, begin_bit: int, end_bit: int,
                        stream: int = 0):

@@ -165,21 +165,42 @@ struct ViewProj {
   float TS[6];             // T Sigma^W
   float cov[3];            // Sigma^I + eps: xx, xy, yy
   float conic[3];          // a, b, c
-  float mean2d[2];
+  float mean2d[2];         // projected mean, hi parts
+  float mean2d_lo[2];      // and lo parts (mean2d + mean2d_lo = fx u + cx, fy w + cy)
 };
 
 // Returns false if the Gaussian is culled in this view (behind znear or degenerate).
 __device__ __forceinline__ bool project_view(const GaussianLocal& g, const ViewParams& vp,
                                              const Consts& c, ViewProj& p) {
   const float* R = vp.R;
-  p.mc[0] = dot3_plus_accurate(R[0], R[1], R[2], g.m[0], g.m[1], g.m[2], vp.t[0]);
-  p.mc[1] = dot3_plus_accurate(R[3], R[4], R[5], g.m[0], g.m[1], g.m[2], vp.t[1]);
-  p.mc[2] = dot3_plus_accurate(R[6], R[7], R[8], g.m[0], g.m[1], g.m[2], vp.t[2]);
+  float lo[3];
+  p.mc[0] = dot3_plus_dd(R[0], R[1], R[2], g.m[0], g.m[1], g.m[2], vp.t[0], lo[0]);
+  p.mc[1] = dot3_plus_dd(R[3], R[4], R[5], g.m[0], g.m[1], g.m[2], vp.t[1], lo[1]);
+  p.mc[2] = dot3_plus_dd(R[6], R[7], R[8], g.m[0], g.m[1], g.m[2], vp.t[2], lo[2]);
   const float z = p.mc[2];
   if (!(z > c.znear)) return false;
   const float rz = 1.0f / z;
   p.u = __fdiv_rn(p.mc[0], z);
   p.w = __fdiv_rn(p.mc[1], z);
+  // Projected mean in double-float: u = x / z to about 2^-44 from the double-float x and z,
+  // then fx u + cx with error-free products and sums.
+  {
+    const float uq[2] = {p.u, p.w};
+    const float f[2] = {vp.fx, vp.fy}, cc[2] = {vp.cx, vp.cy};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      float r = __fmaf_rn(-uq[a], z, p.mc[a]);           // exact remainder of the hi parts
+      r = __fsub_rn(__fadd_rn(r, lo[a]), __fmul_rn(uq[a], lo[2]));
+      const float ul = __fmul_rn(r, rz);                  // u = uq + ul
+      float ph, pl, sh, sl;
+      two_prod(f[a], uq[a], ph, pl);
+      pl = __fmaf_rn(f[a], ul, pl);
+      two_sum(ph, cc[a], sh, sl);
+      sl = __fadd_rn(sl, pl);
+      p.mean2d[a] = __fadd_rn(sh, sl);
+      p.mean2d_lo[a] = __fsub_rn(sl, __fsub_rn(p.mean2d[a], sh));
+    }
+  }
   p.uc = p.u;
   p.wc = p.w;
   p.u_cl = p.w_cl = false;
@@ -208,17 +229,30 @@ __device__ __forceinline__ bool project_view(const GaussianLocal& g, const ViewP
     p.TS[3 * r + 1] = t0 * S[1] + t1 * S[3] + t2 * S[4];
     p.TS[3 * r + 2] = t0 * S[2] + t1 * S[4] + t2 * S[5];
   }
-  p.cov[0] = p.TS[0] * p.T[0] + p.TS[1] * p.T[1] + p.TS[2] * p.T[2] + c.eps2d;
-  p.cov[1] = p.TS[0] * p.T[3] + p.TS[1] * p.T[4] + p.TS[2] * p.T[5];
-  p.cov[2] = p.TS[3] * p.T[3] + p.TS[4] * p.T[4] + p.TS[5] * p.T[5] + c.eps2d;
-  const float det = p.cov[0] * p.cov[2] - p.cov[1] * p.cov[1];
+  // Sigma^I = A A^T + eps I with A = T M (M = Rq diag(s), so that Sigma^W = M M^T). Its
+  // determinant comes from the Cauchy-Binet sum of squared 2x2 minors of A, each minor a
+  // difference of products evaluated with Kahan's FMA scheme: no cancellation between the two
+  // large products ac and b^2, so the conic of a thin, far-stretched ellipse keeps its accuracy.
+  float A[6];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      A[3 * r + k] = p.T[3 * r] * g.M[k] + p.T[3 * r + 1] * g.M[3 + k] + p.T[3 * r + 2] * g.M[6 + k];
+  const float sxx = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+  const float syy = A[3] * A[3] + A[4] * A[4] + A[5] * A[5];
+  p.cov[0] = sxx + c.eps2d;
+  p.cov[1] = A[0] * A[3] + A[1] * A[4] + A[2] * A[5];
+  p.cov[2] = syy + c.eps2d;
+  const float m01 = diff_of_products(A[0], A[4], A[1], A[3]);
+  const float m02 = diff_of_products(A[0], A[5], A[2], A[3]);
+  const float m12 = diff_of_products(A[1], A[5], A[2], A[4]);
+  const float det = m01 * m01 + m02 * m02 + m12 * m12 + c.eps2d * (sxx + syy) + c.eps2d * c.eps2d;
   if (!(det > 0.0f)) return false;
   const float idet = 1.0f / det;
   p.conic[0] = p.cov[2] * idet;
   p.conic[1] = -p.cov[1] * idet;
   p.conic[2] = p.cov[0] * idet;
-  p.mean2d[0] = __fmaf_rn(vp.fx, p.u, vp.cx);
-  p.mean2d[1] = __fmaf_rn(vp.fy, p.w, vp.cy);
   return true;
 }
 
@@ -287,7 +321,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
     uint32_t count = 0;
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     if (finite && kappa >= 0.0f && project_view(g, vp, c, p)) {
-      r0 = make_float4(p.mean2d[0], p.mean2d[1], g.opacity, p.mc[2]);
+      r0 = make_float4(p.mean2d[0], p.mean2d[1], p.mean2d_lo[0], p.mean2d_lo[1]);
       r1 = make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
                        __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
       // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
@@ -307,9 +341,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
         for (int k = 0; k < K; ++k) acc += shc[3 * k + ch] * Y[k];
         rgb[ch] = fmaxf(acc, 0.0f);
       }
-      r2 = make_float4(rgb[0], rgb[1], rgb[2], kappa);
+      r2 = make_float4(rgb[0], rgb[1], rgb[2], p.mc[2]);
       Ellipse e;
-      if (make_ellipse(r0, r1, r2, e))
+      if (make_ellipse(r0, r1, c.log2_alpha_min, e))
         for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
                           [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
     }

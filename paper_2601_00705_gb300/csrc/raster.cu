@@ -18,8 +18,8 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const __grid_constant__ Views views, int n, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ntiles,
     const float4* __restrict__ rec0, const float4* __restrict__ rec1,
-    const float4* __restrict__ rec2, const Counters* __restrict__ counters_in, uint32_t capacity,
-    uint32_t* __restrict__ keys,
+    const float4* __restrict__ rec2, float log2_alpha_min, const Counters* __restrict__ counters_in,
+    uint32_t capacity, uint32_t* __restrict__ keys,
     uint32_t* __restrict__ vals, Counters* __restrict__ counters) {
   const uint32_t k = blockIdx.x * kDupThreads + threadIdx.x;
   if (k >= counters_in->n_visible) return;
@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   const ViewParams& vp = views.v[v];
   uint32_t off = begin;
   Ellipse e;
-  if (make_ellipse(rec0[vi], rec1[vi], rec2[vi], e)) {
+  if (make_ellipse(rec0[vi], rec1[vi], log2_alpha_min, e)) {
     for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
                       [&](int ty, int tx0, int tx1) {
                         const uint32_t row = (uint32_t)(vp.tile_base + ty * vp.tiles_x);
@@ -122,13 +122,13 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     for (int g = 0; g < cnt && !all_done; ++g) {
       const float4 g0 = s0[g];
       const float4 g1 = s1[g];
-      const ColumnTerms ct = column_terms(__fsub_rn(fx, g0.x), g1.x, g1.y, g1.w);
+      const ColumnTerms ct = column_terms(__fsub_rn(__fsub_rn(fx, g0.x), g0.z), g1.x, g1.y, g1.w);
       all_done = true;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (!done[k]) {
           ++evals;
-          const float dy = __fsub_rn((float)(py0 + k), g0.y);
+          const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
           const float a = fminf(c.alpha_max, opacity_times_gauss(ct, g1.z, dy));
           if (a >= c.alpha_min) {
             const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, a));
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
               C0[k] = fmaf(w, g2.x, C0[k]);
               C1[k] = fmaf(w, g2.y, C1[k]);
               C2[k] = fmaf(w, g2.z, C2[k]);
-              D[k] = fmaf(w, g0.w, D[k]);
+              D[k] = fmaf(w, g2.w, D[k]);
               T[k] = Tn;
               ++contribs;
               last[k] = (int32_t)(start + g);
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
         const float4 g0 = s0[g];
         const float4 g1 = s1[g];
         const float4 g2 = s2[g];
-        const float dx = __fsub_rn(fx, g0.x);
+        const float dx = __fsub_rn(__fsub_rn(fx, g0.x), g0.z);
         const ColumnTerms ct = column_terms(dx, g1.x, g1.y, g1.w);
         // Per-thread moments of dL/dpower over the thread's pixels (all share dx):
         // sdp = sum dp, sdy = sum dp dy, sdy2 = sum dp dy^2.
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (jj > last[k]) continue;
-          const float dy = __fsub_rn((float)(py0 + k), g0.y);
+          const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
           const float oG = opacity_times_gauss(ct, g1.z, dy);
           const float a = fminf(c.alpha_max, oG);
           if (a < c.alpha_min) continue;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
           acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
           acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
-          const float q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g0.w)));
+          const float q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g2.w)));
           const float dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
           U[k] = fmaf(w, q, U[k]);
           if (oG < c.alpha_max) {
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
         if (contrib) {
           // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = p - mu^I, alpha = o exp(power).
           const float ca = g1.x * (-2.0f * kLn2), cb = g1.y * (-kLn2), cc = g1.z * (-2.0f * kLn2);
-          acc[kGOp] = sdp * rcp_approx(g0.z);  // d alpha / d o = G = alpha / o
+          acc[kGOp] = sdp * ex2_approx(-g1.w);  // d alpha / d o = G = alpha / o, 1/o = 2^-log2 o
           acc[kGMx] = fmaf(ca * dx, sdp, cb * sdy);
           acc[kGMy] = fmaf(cb * dx, sdp, cc * sdy);
           acc[kGCa] = -0.5f * dx * dx * sdp;
@@ -404,15 +404,15 @@ cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
 
 cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
-                             const float4* rec1, const float4* rec2, int64_t visible_cap,
-                             uint32_t capacity,
+                             const float4* rec1, const float4* rec2, float log2_alpha_min,
+                             int64_t visible_cap, uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream) {
   if (visible_cap > 0) {
     const unsigned blocks = (unsigned)((visible_cap + kDupThreads - 1) / kDupThreads);
     duplicate_kernel<<<blocks, kDupThreads, 0, stream>>>(views, n, order, offsets, ntiles, rec0,
-                                                         rec1, rec2, counters, capacity, keys,
-                                                         vals, counters);
+                                                         rec1, rec2, log2_alpha_min, counters,
+                                                         capacity, keys, vals, counters);
     RGS_LAUNCHED();
   }
   store_pair_count_kernel<<<1, 1, 0, stream>>>(counters, capacity);

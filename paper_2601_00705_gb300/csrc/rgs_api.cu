@@ -37,8 +37,8 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        float* d_pose, cudaStream_t stream);
 cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
-                             const float4* rec1, const float4* rec2, int64_t visible_cap,
-                             uint32_t capacity,
+                             const float4* rec1, const float4* rec2, float log2_alpha_min,
+                             int64_t visible_cap, uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream);
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
@@ -364,6 +364,7 @@ rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const 
   consts.znear = cfg.znear;
   consts.eps2d = cfg.eps2d;
   for (int k = 0; k < 3; ++k) consts.bg[k] = cfg.bg[k];
+  consts.log2_alpha_min = (float)std::log2((double)cfg.alpha_min);
   if (!(cfg.alpha_min > 0.0f) || !(cfg.alpha_max > cfg.alpha_min) || !(cfg.alpha_max < 1.0f) ||
       !(cfg.t_min > 0.0f) || !(cfg.eps2d >= 0.0f) || !(cfg.znear > 0.0f) ||
       !std::isfinite(cfg.znear))
@@ -517,7 +518,7 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
            "preprocess");
   RGS_CUDA(mark(ctx, *s, 1, stream, capturing), "event");
   // 2. Visible entries with depth keys, in (view, Gaussian) order.
-  RGS_CUDA(launch_compact_visible(s->ntiles, s->rec0, vn, s->vis_keys[0], s->vis_vals[0],
+  RGS_CUDA(launch_compact_visible(s->ntiles, s->rec2, vn, s->vis_keys[0], s->vis_vals[0],
                                   &cnt->n_visible, s->block_sums, stream),
            "compact");
   RGS_CUDA(mark(ctx, *s, 2, stream, capturing), "event");
@@ -552,7 +553,7 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   const uint32_t capacity = (uint32_t)s->pair_cap;
   // 5. Duplicate (tile, vi) pairs in depth order.
   RGS_CUDA(launch_duplicate(views, g->n, s->order, s->offsets, s->ntiles, s->rec0, s->rec1,
-                            s->rec2, vn, capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
+                            s->rec2, consts.log2_alpha_min, vn, capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
            "duplicate");
   RGS_CUDA(mark(ctx, *s, 5, stream, capturing), "event");
   // 6. Stable sort by global tile id.
@@ -683,6 +684,55 @@ rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t handle, rgs_stats* out, void* 
   out->n_nonfinite = c.n_nonfinite;
   out->status = c.status;
   out->kernel_launches = s->fwd_launches + s->bwd_launches;
+  return RGS_OK;
+}
+
+rgs_status rgs_copy_tile_lists(rgs_ctx* ctx, uint64_t handle, uint32_t* host_vals,
+                               int64_t vals_cap, uint32_t* host_ranges, int64_t* n_pairs,
+                               void* stream_ptr) {
+  if (!ctx || !n_pairs) return RGS_ERR_INVALID_ARG;
+  State* s = find_state(ctx, handle);
+  if (!s || !s->has_forward) return fail(ctx, RGS_ERR_STATE, "state holds no completed forward");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  cudaSetDevice(ctx->device);
+  RGS_CUDA(cudaMemcpyAsync(ctx->host_counters, s->counters, sizeof(Counters),
+                           cudaMemcpyDeviceToHost, stream),
+           "read counters");
+  RGS_CUDA(cudaStreamSynchronize(stream), "sync");
+  const int64_t np = ctx->host_counters->n_pairs_stored;
+  *n_pairs = np;
+  if (host_vals && np <= vals_cap && np > 0)
+    RGS_CUDA(cudaMemcpyAsync(host_vals, s->sorted_vals, sizeof(uint32_t) * np,
+                             cudaMemcpyDeviceToHost, stream),
+             "copy pair list");
+  if (host_ranges && s->views.total_tiles > 0)
+    RGS_CUDA(cudaMemcpyAsync(host_ranges, s->ranges, sizeof(uint2) * s->views.total_tiles,
+                             cudaMemcpyDeviceToHost, stream),
+             "copy tile ranges");
+  RGS_CUDA(cudaStreamSynchronize(stream), "sync");
+  return RGS_OK;
+}
+
+rgs_status rgs_copy_records(rgs_ctx* ctx, uint64_t handle, float* host_rec,
+                            uint32_t* host_ntiles, void* stream_ptr) {
+  if (!ctx || !host_rec) return RGS_ERR_INVALID_ARG;
+  State* s = find_state(ctx, handle);
+  if (!s || !s->has_forward) return fail(ctx, RGS_ERR_STATE, "state holds no completed forward");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  cudaSetDevice(ctx->device);
+  const int64_t vn = s->vn;
+  if (vn > 0) {
+    const float4* recs[3] = {s->rec0, s->rec1, s->rec2};
+    for (int k = 0; k < 3; ++k)
+      RGS_CUDA(cudaMemcpy2DAsync(host_rec + 4 * k, 12 * sizeof(float), recs[k], sizeof(float4),
+                                 sizeof(float4), (size_t)vn, cudaMemcpyDeviceToHost, stream),
+               "copy records");
+    if (host_ntiles)
+      RGS_CUDA(cudaMemcpyAsync(host_ntiles, s->ntiles, sizeof(uint32_t) * vn,
+                               cudaMemcpyDeviceToHost, stream),
+               "copy tile counts");
+  }
+  RGS_CUDA(cudaStreamSynchronize(stream), "sync");
   return RGS_OK;
 }
 

@@ -1,9 +1,11 @@
 // rgs_internal.cuh -- shared declarations and device helpers of the sm_103a rasterizer.
 //
 // Layout in HBM (V views, N Gaussians, "vi" = v * N + i):
-//   rec0[vi] = (mean2d.x, mean2d.y, opacity, depth z)      float4
+//   rec0[vi] = (mean2d.x hi, mean2d.y hi, mean2d.x lo, mean2d.y lo)   float4, the projected
+//              mean as an unevaluated double-float sum, so that p - mu^I is accurate to ~1e-7 px
+//              even at 1080p coordinates
 //   rec1[vi] = (qa, qb, qc, log2 o)                        float4, base-2 conic (see below)
-//   rec2[vi] = (r, g, b, kappa)                            float4, kappa = 2 ln(o / alpha_min)
+//   rec2[vi] = (r, g, b, depth z)                          float4
 //   ntiles[vi]: tiles touched (0 = culled / invisible)
 //   g2d[vi * 16 + s]: screen-space gradient slots (mean2d x/y, conic a/b/c, opacity, rgb, z),
 //              reused by the backward preprocess for its per-view intermediate results
@@ -52,6 +54,7 @@ struct Views {
 struct Consts {
   float alpha_min, alpha_max, t_min, znear, eps2d;
   float bg[3];
+  float log2_alpha_min;  // log2(alpha_min), rounded once on the host
 };
 
 // Device status bits.
@@ -100,12 +103,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// a b - c d with Kahan's FMA scheme: within about one ulp of the exact value even when the two
+// products nearly cancel.
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = __fmaf_rn(-c, d, w);
+  const float f = __fmaf_rn(a, b, -w);
+  return __fadd_rn(f, e);
+}
+
 // r . m + t with the compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci.
-// Comput. 26(6), 2005): as accurate as evaluation in twice the working precision, then rounded
-// once. The camera-space depth computed this way is the float32 rounding of the exact value, so
-// the near-to-far sort key does not depend on the order of the floating-point operations.
-__device__ __forceinline__ float dot3_plus_accurate(float r0, float r1, float r2, float m0,
-                                                    float m1, float m2, float t) {
+// Comput. 26(6), 2005): as accurate as evaluation in twice the working precision. Returns the
+// result as an unevaluated sum hi + lo (|lo| <= ulp(hi) / 2), hi being the float32 rounding of
+// the accurate value. The camera-space depth taken from hi is therefore the float32 rounding of
+// the exact depth, so the near-to-far sort key does not depend on operation order.
+__device__ __forceinline__ float dot3_plus_dd(float r0, float r1, float r2, float m0, float m1,
+                                              float m2, float t, float& lo) {
   float p, s, h, e, q;
   two_prod(r0, m0, p, s);
   two_prod(r1, m1, h, e);
@@ -116,7 +129,9 @@ __device__ __forceinline__ float dot3_plus_accurate(float r0, float r1, float r2
   s = __fadd_rn(s, __fadd_rn(q, e));
   two_sum(p, t, p, q);
   s = __fadd_rn(s, q);
-  return __fadd_rn(p, s);
+  const float hi = __fadd_rn(p, s);
+  lo = __fsub_rn(s, __fsub_rn(hi, p));
+  return hi;
 }
 
 // Hardware base-2 exponential and reciprocal (PTX ex2.approx / rcp.approx): fixed instruction
@@ -168,19 +183,22 @@ struct Ellipse {
   float kappa;
 };
 
-// From the stored records: rec0 = (mx, my, o, z), rec1 = base-2 conic and log2 o, rec2.w = kappa.
-__device__ __forceinline__ bool make_ellipse(float4 r0, float4 r1, float4 r2, Ellipse& e) {
+// From the stored records (rec0.xy = mean hi parts, rec1 = base-2 conic and log2 o), with
+// kappa = 2 ln(o / alpha_min) = 2 ln 2 (log2 o - log2 alpha_min).
+__device__ __forceinline__ bool make_ellipse(float4 r0, float4 r1, float log2_alpha_min,
+                                             Ellipse& e) {
   const float a = __fmul_rn(r1.x, -2.0f * kLn2), b = __fmul_rn(r1.y, -kLn2),
               c = __fmul_rn(r1.z, -2.0f * kLn2);
   const float detq = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
-  if (!(detq > 0.0f) || !(r2.w >= 0.0f)) return false;
+  const float kappa = __fmul_rn(2.0f * kLn2, __fsub_rn(r1.w, log2_alpha_min));
+  if (!(detq > 0.0f) || !(kappa >= 0.0f)) return false;
   e.mx = r0.x;
   e.my = r0.y;
   const float inv = __fdividef(1.0f, detq);
   e.sxx = __fmul_rn(c, inv);
   e.sxy = __fmul_rn(-b, inv);
   e.syy = __fmul_rn(a, inv);
-  e.kappa = r2.w;
+  e.kappa = kappa;
   return true;
 }
 
@@ -280,8 +298,8 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_c
                                   cudaStream_t stream);
 
 // Compaction of visible entries: for vi in [0, n) with ntiles[vi] > 0, writes
-// keys[pos] = float bits of rec0[vi].w (depth), vals[pos] = vi, count into *n_out.
-cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec0, int64_t n,
+// keys[pos] = float bits of rec2[vi].w (depth), vals[pos] = vi, count into *n_out.
+cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec2, int64_t n,
                                    uint32_t* keys, uint32_t* vals, uint32_t* n_out,
                                    uint32_t* block_sums, cudaStream_t stream);
 

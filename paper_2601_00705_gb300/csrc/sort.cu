@@ -114,12 +114,12 @@ struct PlainStore {
   }
 };
 struct CompactStore {
-  const float4* rec0;
+  const float4* rec2;  // .w = depth
   uint32_t* keys;
   uint32_t* vals;
   __device__ void operator()(uint32_t k, uint32_t value, uint32_t prefix) const {
     if (value) {
-      keys[prefix] = __float_as_uint(rec0[k].w);
+      keys[prefix] = __float_as_uint(rec2[k].w);
       vals[prefix] = k;
     }
   }
@@ -312,10 +312,10 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_c
   return run_scan(PlainLoad{in}, PlainStore{out}, n_cap, n_dev, total, block_sums, stream);
 }
 
-cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec0, int64_t n,
+cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec2, int64_t n,
                                    uint32_t* keys, uint32_t* vals, uint32_t* n_out,
                                    uint32_t* block_sums, cudaStream_t stream) {
-  return run_scan(FlagLoad{ntiles}, CompactStore{rec0, keys, vals}, n, nullptr, n_out,
+  return run_scan(FlagLoad{ntiles}, CompactStore{rec2, keys, vals}, n, nullptr, n_out,
                   block_sums, stream);
 }
 
