@@ -159,7 +159,8 @@ def render(renderer: Renderer, cameras, means, log_scales, quats, opacity_logits
     """
     if twist is None:
         twist = torch.zeros((len(cameras), 6), dtype=torch.float32, device=renderer.device)
-    if not any(t.requires_grad for t in (means, log_scales, quats, opacity_logits, sh, twist)):
+    if not torch.is_grad_enabled() or not any(
+            t.requires_grad for t in (means, log_scales, quats, opacity_logits, sh, twist)):
         color, depth, alpha, state = renderer.forward_raw(means, log_scales, quats,
                                                           opacity_logits, sh, cameras)
         renderer.release(state)
