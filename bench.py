@@ -70,6 +70,22 @@ def dist_setup(args):
     return world, rank, local
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of x over all ranks (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world: int, pixels_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job Mpix/s: every rank renders pixels_per_step per step; time is the max over ranks."""
+    return world * pixels_per_step * steps / (total_ms / 1e3) / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -251,6 +267,7 @@ def run_ours(args, world, rank, local):
         ups[1] = None
     cams = binding.make_cameras(wl.cameras)
     r = Renderer(dev)
+    tuned = r.autotune(*params, cams)
     r.ctx.set_phase_timing(True)
     images = (torch.empty((pixels, 3), device=dev), torch.empty(pixels, device=dev),
               torch.empty(pixels, device=dev))
@@ -304,12 +321,9 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * pixels * args.steps / (total_ms / 1e3) / 1e6
+    value = throughput(world, pixels, args.steps, total_ms)
     phases = {k: v / args.steps for k, v in phase_sum.items()}
     stats = r.stats(state)
 
@@ -399,12 +413,8 @@ def run_ours(args, world, rank, local):
         e1.record()
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = float(np.sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * pixels * args.steps / (e2e_total / 1e3) / 1e6
+    e2e_total = reduce_max(float(np.sum(e2e_ms)), world, dev)
+    e2e_value = throughput(world, pixels, args.steps, e2e_total)
 
     # Roofline of the dominant kernel (the blend phases are single launches per step).
     peaks, peak_src = measured_peaks()
@@ -436,6 +446,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD_NAMES[args.workload], "n_gaussians": n, "views": V,
                    "pixels_per_step": pixels, "sh_degree": int(round(K ** 0.5)) - 1,
                    "grad": wl.grad_mask, "cuda_graph": True,
+                   "tile": f"{tuned['tile_w']}x{tuned['tile_h']}",
+                   "pixels_per_thread": tuned["pixels_per_thread"], "autotuned": True,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "clocks": clk,

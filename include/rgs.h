@@ -179,6 +179,20 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t state, const rgs_image_gra
                                float* d_quats, float* d_opacity_logits, float* d_sh,
                                float* d_pose, void* stream);
 
+/* Autotuner: picks the blend tile shape and pixels per thread (the per-thread batch depth of the
+ * blends) that make one forward + backward of this exact workload fastest on this GPU. Every
+ * supported combination (16x16, 8x8, 32x8 tiles; 1, 2 or 4 pixels per thread) is timed with
+ * CUDA events (one warm-up and three timed runs of forward + backward with a zero upstream
+ * gradient, all gradients requested) in scratch buffers of its own. The fastest is written into
+ * cfg->tile_w, cfg->tile_h and cfg->pixels_per_thread (other fields are kept) and cached in the
+ * context under (n, sh_degree, the views' sizes); a later call with the same key returns the
+ * cached choice without timing. Results do not depend on the choice beyond atomics-order
+ * rounding of the gradients. Synchronises `stream`; allocates and frees device memory. Under
+ * stream capture it returns RGS_ERR_INVALID_ARG. ms_out (may be NULL) receives the winner's
+ * forward + backward time in milliseconds (0 when served from the cache). */
+rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                        int32_t n_views, rgs_config* cfg, float* ms_out, void* stream);
+
 /* Frees a state's device memory (after its queued work completes). */
 rgs_status rgs_release_state(rgs_ctx* ctx, uint64_t state);
 

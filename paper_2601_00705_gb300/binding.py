@@ -26,7 +26,7 @@ EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_render_forward", "rgs_render_backward", "rgs_release_state", "rgs_reserve",
             "rgs_query_stats", "rgs_set_phase_timing", "rgs_phase_times", "rgs_radix_sort_u32",
             "rgs_exclusive_scan_u32", "rgs_exclusive_scan_u32_static", "rgs_copy_tile_lists",
-            "rgs_copy_records")
+            "rgs_copy_records", "rgs_autotune")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -110,6 +110,8 @@ def load(build_if_needed: bool = True):
             "rgs_exclusive_scan_u32_static": (S, [P, P, I64, P, P]),
             "rgs_copy_tile_lists": (S, [P, U64, P, I64, P, ctypes.POINTER(I64), P]),
             "rgs_copy_records": (S, [P, U64, P, P, P]),
+            "rgs_autotune": (S, [P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), I32,
+                                 ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -198,6 +200,16 @@ class Context:
             self.handle, ctypes.c_uint64(state), ctypes.byref(grads), ctypes.c_uint32(grad_mask),
             P(d_means or None), P(d_log_scales or None), P(d_quats or None),
             P(d_opacity_logits or None), P(d_sh or None), P(d_pose or None), P(stream)))
+
+    def autotune(self, g: Gaussians, cams, cfg: Config, stream: int) -> float:
+        """Times every tile shape / pixels-per-thread choice and writes the fastest into cfg;
+        returns its forward + backward milliseconds (0 when served from the cache)."""
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        ms = ctypes.c_float(0.0)
+        self._check(self.lib.rgs_autotune(self.handle, ctypes.byref(g), cam_arr, len(cam_arr),
+                                          ctypes.byref(cfg), ctypes.byref(ms),
+                                          ctypes.c_void_p(stream)))
+        return ms.value
 
     def release(self, state: int):
         if state:

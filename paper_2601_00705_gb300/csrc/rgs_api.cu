@@ -107,9 +107,14 @@ struct State {
 
 }  // namespace
 
+struct TuneChoice {
+  int tile_w, tile_h, ppt;
+};
+
 struct rgs_ctx {
   int device = 0;
   bool timing = false;
+  std::map<std::string, TuneChoice> tune_cache;
   std::string last_error;
   std::map<uint64_t, State*> states;
   uint64_t next_id = 1;
@@ -431,6 +436,113 @@ void rgs_destroy(rgs_ctx* ctx) {
 }
 
 const char* rgs_last_error(const rgs_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                        int32_t n_views, rgs_config* cfg, float* ms_out, void* stream_ptr) {
+  if (!ctx || !g || !cams || !cfg) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (ms_out) *ms_out = 0.0f;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  if (is_capturing(stream)) return fail(ctx, RGS_ERR_INVALID_ARG, "autotune under stream capture");
+  if (n_views < 1 || n_views > kMaxViews)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n_views must be in 1..RGS_MAX_VIEWS");
+  std::string key = std::to_string(g->n) + ":" + std::to_string(g->sh_degree);
+  int64_t pixels = 0;
+  for (int v = 0; v < n_views; ++v) {
+    key += ":" + std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height);
+    pixels += (int64_t)cams[v].width * cams[v].height;
+  }
+  auto hit = ctx->tune_cache.find(key);
+  if (hit != ctx->tune_cache.end()) {
+    cfg->tile_w = hit->second.tile_w;
+    cfg->tile_h = hit->second.tile_h;
+    cfg->pixels_per_thread = hit->second.ppt;
+    return RGS_OK;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice");
+  const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
+  const int64_t n = g->n;
+  // Scratch: images [P,5], upstream colour gradient [P,3] (zero), parameter and pose gradients.
+  const int64_t n1 = std::max<int64_t>(n, 1);
+  const size_t bytes = align_up(sizeof(float) * 5 * pixels) + align_up(sizeof(float) * 3 * pixels) +
+                       3 * align_up(sizeof(float) * 4 * n1) + align_up(sizeof(float) * n1) +
+                       align_up(sizeof(float) * 3 * K * n1) + align_up(sizeof(float) * 6 * n_views);
+  char* base = nullptr;
+  RGS_CUDA(cudaMalloc(&base, bytes), "autotune scratch");
+  char* p = base;
+  float* img = carve<float>(p, 5 * pixels);
+  float* upc = carve<float>(p, 3 * pixels);
+  float* d_means = carve<float>(p, 4 * n1);
+  float* d_ls = carve<float>(p, 4 * n1);
+  float* d_q = carve<float>(p, 4 * n1);
+  float* d_o = carve<float>(p, n1);
+  float* d_sh = carve<float>(p, 3 * K * n1);
+  float* dpose = carve<float>(p, 6 * n_views);
+  rgs_status result = RGS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  uint64_t state = 0;
+  do {
+    if (cudaMemsetAsync(upc, 0, sizeof(float) * 3 * pixels, stream) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      result = fail(ctx, RGS_ERR_CUDA, "autotune setup");
+      break;
+    }
+    rgs_images out{img, img + 3 * pixels, img + 4 * pixels};
+    rgs_image_grads up{upc, nullptr, nullptr};
+    const uint32_t mask = RGS_GRAD_ALL;
+    const TuneChoice cands[] = {{16, 16, 4}, {16, 16, 2}, {16, 16, 1}, {8, 8, 2},
+                                {8, 8, 1},   {32, 8, 4},  {32, 8, 2},  {32, 8, 1}};
+    float best = 1e30f;
+    TuneChoice choice = cands[0];
+    for (const TuneChoice& c : cands) {
+      rgs_config trial = *cfg;
+      trial.tile_w = c.tile_w;
+      trial.tile_h = c.tile_h;
+      trial.pixels_per_thread = c.ppt;
+      float total = 0.0f;
+      rgs_status st = RGS_OK;
+      for (int it = 0; it < 4 && st == RGS_OK; ++it) {
+        if (it == 1) cudaEventRecord(e0, stream);
+        st = rgs_render_forward(ctx, g, cams, n_views, &trial, &out, &state, stream);
+        if (st == RGS_OK)
+          st = rgs_render_backward(ctx, state, &up, mask, d_means, d_ls, d_q, d_o, d_sh, dpose,
+                                   stream);
+      }
+      if (st != RGS_OK) {
+        result = st;
+        break;
+      }
+      cudaEventRecord(e1, stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&total, e0, e1) != cudaSuccess) {
+        result = fail(ctx, RGS_ERR_CUDA, "autotune timing");
+        break;
+      }
+      if (total < best) {
+        best = total;
+        choice = c;
+      }
+    }
+    if (result != RGS_OK) break;
+    ctx->tune_cache[key] = choice;
+    cfg->tile_w = choice.tile_w;
+    cfg->tile_h = choice.tile_h;
+    cfg->pixels_per_thread = choice.ppt;
+    if (ms_out) *ms_out = best / 3.0f;
+  } while (false);
+  cudaStreamSynchronize(stream);
+  if (state) {
+    auto it = ctx->states.find(state);
+    if (it != ctx->states.end()) {
+      destroy_state(it->second);
+      ctx->states.erase(it);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(base);
+  return result;
+}
 
 rgs_status rgs_release_state(rgs_ctx* ctx, uint64_t handle) {
   if (!ctx) return RGS_ERR_INVALID_ARG;

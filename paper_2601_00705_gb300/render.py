@@ -113,6 +113,22 @@ class Renderer:
                           ptr["opacity_logits"], ptr["sh"], ptr["pose"], self.stream_handle())
         return out
 
+    def autotune(self, means, log_scales, quats, opacity_logits, sh, cameras) -> dict:
+        """Lets the library pick the fastest tile shape and pixels per thread for this workload
+        (cached per scene size and view sizes) and keeps it in this renderer's config."""
+        n = int(means.shape[0])
+        K = int(sh.shape[1])
+        deg = int(round(K ** 0.5)) - 1
+        dev = self.device
+        t = [_check_param(means, "means", (3,), dev), _check_param(log_scales, "log_scales", (3,), dev),
+             _check_param(quats, "quats", (4,), dev),
+             _check_param(opacity_logits.reshape(n, 1), "opacity_logits", (1,), dev),
+             _check_param(sh, "sh", (K, 3), dev)]
+        g = binding.Gaussians(n, deg, *[x.data_ptr() for x in t])
+        ms = self.ctx.autotune(g, cameras, self.config, self.stream_handle())
+        return dict(tile_w=self.config.tile_w, tile_h=self.config.tile_h,
+                    pixels_per_thread=self.config.pixels_per_thread, ms=ms)
+
     def release(self, state: int):
         self.ctx.release(state)
 

@@ -170,3 +170,22 @@ def test_nonfinite_gaussians_are_culled_and_counted():
     g2 = {k: v[keep] for k, v in g.items()}
     ref = gpu_render(g2, wl.cameras)
     np.testing.assert_allclose(gpu["color"], ref["color"], atol=1e-6)
+
+
+def test_autotuner_choice_is_valid_cached_and_leaves_results_unchanged():
+    from paper_2601_00705_gb300.render import Renderer
+    wl = synthetic.tiny(seed=3)
+    g = wl.gaussians.as_dict()
+    r = Renderer(0)
+    params = [to_dev(g[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    first = r.autotune(*params, wl.cameras)
+    assert (first["tile_w"], first["tile_h"]) in {(16, 16), (8, 8), (32, 8)}
+    assert first["pixels_per_thread"] in (1, 2, 4) and first["ms"] > 0
+    second = r.autotune(*params, wl.cameras)
+    assert second["ms"] == 0 and {k: second[k] for k in ("tile_w", "tile_h", "pixels_per_thread")} \
+        == {k: first[k] for k in ("tile_w", "tile_h", "pixels_per_thread")}
+    tuned = gpu_render(g, wl.cameras, tile_w=first["tile_w"], tile_h=first["tile_h"],
+                       pixels_per_thread=first["pixels_per_thread"])
+    ref = gpu_render(g, wl.cameras)
+    for k in ("color", "depth", "alpha"):
+        np.testing.assert_array_equal(tuned[k], ref[k], err_msg=k)
