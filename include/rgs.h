@@ -235,7 +235,8 @@ rgs_status rgs_phase_times(rgs_ctx* ctx, uint64_t state, float* ms, int32_t n, v
  * tile ids count view by view, row-major inside a view).
  * rgs_copy_records: the projected records of every (view, Gaussian) into host_rec
  * ([n_views * n][12] floats: mean2d hi x, y, lo x, y; base-2 conic qa, qb, qc and log2 o;
- * r, g, b and camera-space depth), and the touched-tile counts into host_ntiles (may be NULL). */
+ * r, g, b and camera-space depth), and the touched-tile counts into host_ntiles (may be NULL).
+ * A record is meaningful only where its tile count is non-zero. */
 rgs_status rgs_copy_tile_lists(rgs_ctx* ctx, uint64_t state, uint32_t* host_vals, int64_t vals_cap,
                                uint32_t* host_ranges, int64_t* n_pairs, void* stream);
 rgs_status rgs_copy_records(rgs_ctx* ctx, uint64_t state, float* host_rec, uint32_t* host_ntiles,

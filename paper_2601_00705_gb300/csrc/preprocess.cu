@@ -114,6 +114,7 @@ struct GaussianLocal {
   float s[3];        // scales exp(log_scale)
   float M[9];        // Rq diag(s)
   float Sw[6];       // Sigma^W = M M^T: xx, xy, xz, yy, yz, zz
+  float smax2;       // largest squared scale (largest eigenvalue of Sigma^W)
   float opacity;
 };
 
@@ -140,6 +141,8 @@ __device__ __forceinline__ void gaussian_local(const float* m, const float* ls, 
   g.Rq[8] = 1.0f - 2.0f * (x * x + y * y);
 #pragma unroll
   for (int k = 0; k < 3; ++k) g.s[k] = expf(ls[k]);
+  g.smax2 = fmaxf(g.s[0], fmaxf(g.s[1], g.s[2]));
+  g.smax2 *= g.smax2;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -276,77 +279,157 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, flo
   }
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(kPreThreads) preprocess_forward_kernel(
+// Forward, pass 1 (cull): one thread per (Gaussian, chunk of views). Only the camera-space mean,
+// the projected centre and the footprint-radius bound of project_view are computed; every entry
+// gets ntiles = 0, and the entries that may touch the image are appended to `cand` (warp-
+// aggregated atomics; their order does not matter). Pass 2 then projects only those, so its
+// warps are not held up by the large majority of entries that fall outside the image.
+__global__ void __launch_bounds__(kPreThreads) cull_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ logits, const float* __restrict__ sh, float4* __restrict__ rec0,
-    float4* __restrict__ rec1, float4* __restrict__ rec2, uint32_t* __restrict__ ntiles,
+    const float* __restrict__ logits, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ cand,
     Counters* __restrict__ counters, int views_per_chunk) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
-  if (i >= n) return;
-  // blockIdx.y selects a chunk of views, so small scenes still fill the GPU.
+  const bool in_range = i < n;
+  const int lane = threadIdx.x & 31;
   const int v_begin = blockIdx.y * views_per_chunk;
   const int v_end = min(views.n_views, v_begin + views_per_chunk);
-  float m[3], ls[3], q[4], shc[3 * K];
+  float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, logit = 0.0f;
+  if (in_range) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    m[k] = __ldg(means + 3 * (size_t)i + k);
-    ls[k] = __ldg(log_scales + 3 * (size_t)i + k);
+    for (int k = 0; k < 3; ++k) {
+      m[k] = __ldg(means + 3 * (size_t)i + k);
+      ls[k] = __ldg(log_scales + 3 * (size_t)i + k);
+    }
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
+    q[0] = q4.x;
+    q[1] = q4.y;
+    q[2] = q4.z;
+    q[3] = q4.w;
+    logit = __ldg(logits + i);
   }
-  const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
-  q[0] = q4.x;
-  q[1] = q4.y;
-  q[2] = q4.z;
-  q[3] = q4.w;
-  const float logit = __ldg(logits + i);
-  load_sh<DEG>(sh, i, shc);
-  bool finite = isfinite(logit);
+  bool finite = in_range && isfinite(logit);
 #pragma unroll
   for (int k = 0; k < 3; ++k) finite = finite && isfinite(m[k]) && isfinite(ls[k]);
 #pragma unroll
   for (int k = 0; k < 4; ++k) finite = finite && isfinite(q[k]);
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) finite = finite && isfinite(shc[k]);
-  GaussianLocal g;
-  if (finite) gaussian_local(m, ls, q, logit, g);
-  finite = finite && g.qnorm > 0.0f && isfinite(g.qnorm);
-  if (!finite) atomicAdd(&counters->n_nonfinite, (uint32_t)(v_end - v_begin));
-  const float kappa = finite ? 2.0f * logf(g.opacity / c.alpha_min) : -1.0f;
+  const float qn2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  finite = finite && qn2 > 0.0f && isfinite(qn2);
+  if (in_range && !finite) atomicAdd(&counters->n_nonfinite, (uint32_t)(v_end - v_begin));
+  float smax = fmaxf(ls[0], fmaxf(ls[1], ls[2]));
+  const float smax2 = finite ? expf(2.0f * smax) : 0.0f;
+  const float opacity = 1.0f / (1.0f + expf(-logit));
+  const float kappa = finite ? 2.0f * logf(opacity / c.alpha_min) : -1.0f;
   for (int v = v_begin; v < v_end; ++v) {
     const ViewParams& vp = views.v[v];
     const size_t vi = (size_t)v * n + i;
-    ViewProj p;
-    uint32_t count = 0;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-    if (finite && kappa >= 0.0f && project_view(g, vp, c, p)) {
-      r0 = make_float4(p.mean2d[0], p.mean2d[1], p.mean2d_lo[0], p.mean2d_lo[1]);
-      r1 = make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
-                       __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
-      // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
-      float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
-            d2 = g.m[2] - vp.cam_center[2];
-      const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-      d0 *= rn;
-      d1 *= rn;
-      d2 *= rn;
-      float Y[16];
-      sh_basis<DEG>(d0, d1, d2, Y);
-      float rgb[3];
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc += shc[3 * k + ch] * Y[k];
-        rgb[ch] = fmaxf(acc, 0.0f);
+    bool keep = false;
+    if (finite && kappa >= 0.0f) {
+      const float* R = vp.R;
+      float lo;
+      const float z = dot3_plus_dd(R[6], R[7], R[8], m[0], m[1], m[2], vp.t[2], lo);
+      if (z > c.znear) {
+        const float x = dot3_plus_dd(R[0], R[1], R[2], m[0], m[1], m[2], vp.t[0], lo);
+        const float y = dot3_plus_dd(R[3], R[4], R[5], m[0], m[1], m[2], vp.t[1], lo);
+        const float rz = 1.0f / z;
+        const float u = x * rz, w = y * rz;
+        float uc = u, wc = w;
+        if (vp.lim_u > 0.0f) {
+          uc = fminf(fmaxf(u, -vp.lim_u), vp.lim_u);
+          wc = fminf(fmaxf(w, -vp.lim_w), vp.lim_w);
+        }
+        const float jf2 = (vp.fx * vp.fx * (1.0f + uc * uc) + vp.fy * vp.fy * (1.0f + wc * wc)) *
+                          (rz * rz);
+        // A rigorous bound of the alpha >= alpha_min footprint radius: the largest eigenvalue of
+        // Sigma^I is at most ||J||_F^2 smax^2 + eps, so the radius is at most
+        // sqrt(kappa (||J||_F^2 smax^2 + eps)); widened by 2 % and 4 px, beyond the 1-px padding
+        // of the tile coverage and the rounding of this cheaper mean.
+        const float rad = sqrtf(kappa * fmaf(jf2, smax2, c.eps2d)) * 1.02f + 4.0f;
+        const float mx = fmaf(vp.fx, u, vp.cx), my = fmaf(vp.fy, w, vp.cy);
+        keep = !(mx + rad < 0.0f || mx - rad > (float)(vp.width - 1) || my + rad < 0.0f ||
+                 my - rad > (float)(vp.height - 1));
       }
-      r2 = make_float4(rgb[0], rgb[1], rgb[2], p.mc[2]);
-      Ellipse e;
-      if (make_ellipse(r0, r1, c.log2_alpha_min, e))
-        for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
-                          [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
     }
+    if (in_range) ntiles[vi] = 0u;
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    if (ballot) {
+      const int leader = __ffs(ballot) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters->n_candidates, (uint32_t)__popc(ballot));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (keep) cand[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)vi;
+    }
+  }
+}
+
+// Forward, pass 2 (project): one thread per candidate entry (grid-stride). Full projection
+// (Eq. proj), colour (Eq. app-sh) and tile count; writes the entry's records and tile count.
+// Entries that are not candidates keep ntiles = 0 and unwritten records.
+template <int DEG>
+__global__ void __launch_bounds__(kPreThreads) project_kernel(
+    const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
+    const float* __restrict__ log_scales, const float* __restrict__ quats,
+    const float* __restrict__ logits, const float* __restrict__ sh,
+    const uint32_t* __restrict__ cand, float4* __restrict__ rec0, float4* __restrict__ rec1,
+    float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, Counters* __restrict__ counters) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const uint32_t n_cand = counters->n_candidates;
+  for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_cand;
+       k += gridDim.x * kPreThreads) {
+    const uint32_t vi = cand[k];
+    const int v = (int)(vi / (uint32_t)n);
+    const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
+    float m[3], ls[3], q[4], shc[3 * K];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      m[a] = __ldg(means + 3 * (size_t)i + a);
+      ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
+    }
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
+    q[0] = q4.x;
+    q[1] = q4.y;
+    q[2] = q4.z;
+    q[3] = q4.w;
+    load_sh<DEG>(sh, i, shc);
+    bool sh_finite = true;
+#pragma unroll
+    for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
+    if (!sh_finite) {
+      atomicAdd(&counters->n_nonfinite, 1u);
+      continue;
+    }
+    GaussianLocal g;
+    gaussian_local(m, ls, q, __ldg(logits + i), g);
+    const ViewParams& vp = views.v[v];
+    ViewProj p;
+    if (!project_view(g, vp, c, p)) continue;
+    const float4 r0 = make_float4(p.mean2d[0], p.mean2d[1], p.mean2d_lo[0], p.mean2d_lo[1]);
+    const float4 r1 =
+        make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
+                    __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
+    // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
+    float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
+          d2 = g.m[2] - vp.cam_center[2];
+    const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    d0 *= rn;
+    d1 *= rn;
+    d2 *= rn;
+    float Y[16];
+    sh_basis<DEG>(d0, d1, d2, Y);
+    float rgb[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float acc = 0.5f;
+#pragma unroll
+      for (int a = 0; a < K; ++a) acc += shc[3 * a + ch] * Y[a];
+      rgb[ch] = fmaxf(acc, 0.0f);
+    }
+    const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], p.mc[2]);
+    uint32_t count = 0;
+    Ellipse e;
+    if (make_ellipse(r0, r1, c.log2_alpha_min, e))
+      for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
+                        [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
     rec0[vi] = r0;
     rec1[vi] = r1;
     rec2[vi] = r2;
@@ -542,11 +625,16 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
   float gsh[3 * K];
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0f;
-  bool any_visible = false;
-  for (int v = 0; v < views.n_views; ++v) {
+  // Visible views as a bit mask, read with independent loads (no load waits on another).
+  uint64_t vis = 0;
+#pragma unroll 8
+  for (int v = 0; v < views.n_views; ++v)
+    vis |= (uint64_t)(__ldg(ntiles + (size_t)v * n + i) != 0u) << v;
+  const bool any_visible = vis != 0;
+  while (vis) {
+    const int v = __ffsll((long long)vis) - 1;
+    vis &= vis - 1;
     const size_t vi = (size_t)v * n + i;
-    if (ntiles[vi] == 0u) continue;
-    any_visible = true;
     float* gp = g2d + vi * kG2Stride;
     const float4 r0 = *reinterpret_cast<const float4*>(gp);
     const float4 r1 = *reinterpret_cast<const float4*>(gp + 4);
@@ -678,28 +766,35 @@ __global__ void pose_finalize_kernel(const float* __restrict__ partial, int n_bl
 
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
-                                      float4* rec2, uint32_t* ntiles, Counters* counters,
-                                      cudaStream_t stream) {
+                                      float4* rec2, uint32_t* ntiles, uint32_t* cand,
+                                      Counters* counters, cudaStream_t stream) {
   if (g.n == 0) return cudaSuccess;
-  // One thread per (Gaussian, chunk of views): enough threads to fill every SM a few times
-  // over, while a thread still reads its Gaussian's parameters once for several views.
+  // Pass 1: one thread per (Gaussian, chunk of views), enough threads to fill every SM a few
+  // times over.
   const int blocks_x = (g.n + kPreThreads - 1) / kPreThreads;
   const int target_blocks = 8 * 152;
   const int chunks = max(1, min(views.n_views, (target_blocks + blocks_x - 1) / blocks_x));
   const int per_chunk = (views.n_views + chunks - 1) / chunks;
   const dim3 grid((unsigned)blocks_x, (unsigned)((views.n_views + per_chunk - 1) / per_chunk));
-#define RGS_PRE_FWD(D)                                                                     \
-  preprocess_forward_kernel<D><<<grid, kPreThreads, 0, stream>>>(                          \
-      views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, rec0, rec1, rec2, \
-      ntiles, counters, per_chunk)
+  cull_kernel<<<grid, kPreThreads, 0, stream>>>(views, c, g.n, g.means, g.log_scales, g.quats,
+                                                g.opacity_logits, ntiles, cand, counters,
+                                                per_chunk);
+  RGS_LAUNCHED();
+  // Pass 2: grid-stride over the candidates.
+  const int64_t vn = (int64_t)views.n_views * g.n;
+  const int blocks2 = (int)std::min<int64_t>((vn + kPreThreads - 1) / kPreThreads, 16 * 152);
+#define RGS_PROJECT(D)                                                                        \
+  project_kernel<D><<<blocks2, kPreThreads, 0, stream>>>(views, c, g.n, g.means, g.log_scales, \
+                                                         g.quats, g.opacity_logits, g.sh, cand, \
+                                                         rec0, rec1, rec2, ntiles, counters)
   switch (g.sh_degree) {
-    case 0: RGS_PRE_FWD(0); break;
-    case 1: RGS_PRE_FWD(1); break;
-    case 2: RGS_PRE_FWD(2); break;
-    default: RGS_PRE_FWD(3); break;
+    case 0: RGS_PROJECT(0); break;
+    case 1: RGS_PROJECT(1); break;
+    case 2: RGS_PROJECT(2); break;
+    default: RGS_PROJECT(3); break;
   }
   RGS_LAUNCHED();
-#undef RGS_PRE_FWD
+#undef RGS_PROJECT
   return cudaGetLastError();
 }
 

@@ -25,8 +25,8 @@
 namespace rgs {
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
-                                      float4* rec2, uint32_t* ntiles, Counters* counters,
-                                      cudaStream_t stream);
+                                      float4* rec2, uint32_t* ntiles, uint32_t* cand,
+                                      Counters* counters, cudaStream_t stream);
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, const uint32_t* ntiles,
@@ -172,7 +172,10 @@ bool is_capturing(cudaStream_t s) {
 
 // Scratch for the scans and sorts of up to `items` elements.
 rgs_status ensure_scratch(rgs_ctx* ctx, State& s, int64_t items, bool capturing) {
-  const int64_t hist = sort_hist_entries(std::max<int64_t>(items, 1));
+  // The depth sort runs with small blocks over the per-Gaussian capacity, the tile sort with
+  // large blocks over the pair capacity; the table must fit either.
+  const int64_t hist = std::max(sort_hist_entries(std::max<int64_t>(s.vn_cap, 1), kSortItemsSmall),
+                                sort_hist_entries(std::max<int64_t>(items, 1)));
   const int64_t sums = std::max(scan_blocks(hist), scan_blocks(std::max<int64_t>(items, 1))) + 1;
   if (hist <= s.hist_cap && sums <= s.sums_cap) return RGS_OK;
   if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "scratch too small during stream capture");
@@ -625,8 +628,10 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   RGS_CUDA(mark(ctx, *s, 0, stream, capturing), "event");
 
   // 1. Projection.
-  RGS_CUDA(launch_preprocess_forward(views, consts, *g, s->rec0, s->rec1, s->rec2, s->ntiles, cnt,
-                                     stream),
+  // The cull pass's candidate list lives in the depth sort's second key buffer, which is free
+  // until the sort starts.
+  RGS_CUDA(launch_preprocess_forward(views, consts, *g, s->rec0, s->rec1, s->rec2, s->ntiles,
+                                     s->vis_keys[1], cnt, stream),
            "preprocess");
   RGS_CUDA(mark(ctx, *s, 1, stream, capturing), "event");
   // 2. Visible entries with depth keys, in (view, Gaussian) order.
@@ -637,7 +642,8 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   // 3. Stable sort by depth (positive float bits order like the values; the sign bit is 0).
   bool alt = false;
   RGS_CUDA(launch_radix_sort(s->vis_keys[0], s->vis_vals[0], s->vis_keys[1], s->vis_vals[1], vn,
-                             &cnt->n_visible, 0, 31, s->hist, s->block_sums, &alt, stream),
+                             &cnt->n_visible, 0, 31, s->hist, s->block_sums, &alt, stream,
+                             kSortItemsSmall),
            "depth sort");
   s->order = s->vis_vals[alt ? 1 : 0];
   RGS_CUDA(mark(ctx, *s, 3, stream, capturing), "event");

@@ -67,7 +67,8 @@ struct Counters {
   uint32_t n_pairs_stored;  // min(n_pairs, capacity)
   uint32_t status;
   uint32_t n_nonfinite;
-  uint32_t pad[3];
+  uint32_t n_candidates;    // entries the cull pass keeps for full projection
+  uint32_t pad[2];
   unsigned long long n_eval;     // (pixel, Gaussian) positions the forward blend visited
   unsigned long long n_contrib;  // of which composited (covering, before the stop)
 };
@@ -309,14 +310,18 @@ cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, in
                                uint32_t* block_sums, cudaStream_t stream);
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortItems = 16;      // keys per thread for large sorts (4096 per block)
+constexpr int kSortItemsSmall = 4;  // for sorts whose live count is far below the capacity
 constexpr int kRadixBins = 256;
 
-inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+inline int64_t sort_blocks(int64_t n, int items = kSortItems) {
+  return (n + kSortThreads * items - 1) / (kSortThreads * items);
+}
 // Scratch for a sort of up to n_cap elements: the digit-major histogram table plus one row
 // total per digit (u32 counts).
-inline int64_t sort_hist_entries(int64_t n_cap) { return (sort_blocks(n_cap) + 1) * kRadixBins; }
+inline int64_t sort_hist_entries(int64_t n_cap, int items = kSortItems) {
+  return (sort_blocks(n_cap, items) + 1) * kRadixBins;
+}
 
 // Stable LSD radix sort of (keys, vals) by bits [begin_bit, end_bit); ping-pongs between the
 // (keys, vals) and (keys_alt, vals_alt) buffers and returns in *result_in_alt whether the
@@ -324,6 +329,7 @@ inline int64_t sort_hist_entries(int64_t n_cap) { return (sort_blocks(n_cap) + 1
 cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                               uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
                               int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
-                              bool* result_in_alt, cudaStream_t stream);
+                              bool* result_in_alt, cudaStream_t stream,
+                              int items = kSortItems);
 
 }  // namespace rgs

@@ -181,6 +181,7 @@ cudaError_t run_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_de
 // takes element r * 32 + l), so warp order, round order and lane order together follow the
 // input order, which makes the ranks stable.
 // ------------------------------------------------------------------------------------------
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint32_t* keys,
                                                                      int64_t n_cap,
                                                                      const uint32_t* n_dev,
@@ -191,10 +192,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
   const uint32_t n = read_count(n_dev, n_cap);
   for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) counts[d] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * ITEMS);
   if (base < n) {
 #pragma unroll 4
-    for (int k = 0; k < kSortItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
       if (idx < n) atomicAdd(&counts[(keys[idx] >> shift) & mask], 1u);
     }
@@ -230,28 +231,30 @@ __global__ void __launch_bounds__(kSortThreads) radix_row_scan_kernel(uint32_t* 
   if (threadIdx.x == 0) hist[(int64_t)kRadixBins * n_blocks + d] = carry;
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
     int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* hist,
     int64_t n_blocks) {
   static_assert(kSortThreads == kRadixBins, "one thread per digit in the digit scans");
   constexpr int kWarps = kSortThreads / 32;
+  constexpr int kTile = kSortThreads * ITEMS;
   __shared__ uint32_t warp_counts[kWarps][kRadixBins];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_keys[kTile];
+  __shared__ uint32_t s_vals[kTile];
   __shared__ uint32_t s_digit_start[kRadixBins];   // block-local start of each digit's run
   __shared__ int64_t s_digit_shift[kRadixBins];    // global position minus local position
   const uint32_t n = read_count(n_dev, n_cap);
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int64_t base = (int64_t)blockIdx.x * kTile;
   if (base >= n) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = lane; d < kRadixBins; d += 32) warp_counts[warp][d] = 0;
   __syncwarp();
-  const int64_t wbase = base + (int64_t)warp * 32 * kSortItems;
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
+  uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     const int64_t idx = wbase + r * 32 + lane;
     const bool valid = idx < n;
     key[r] = valid ? keys_in[idx] : 0u;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     if (rank[r] == 0xffffffffu) continue;
     const uint32_t digit = (key[r] >> shift) & mask;
     const uint32_t local = s_digit_start[digit] + warp_counts[warp][digit] + rank[r];
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     s_vals[local] = val[r];
   }
   __syncthreads();
-  const int count = (int)min((int64_t)kSortTile, (int64_t)n - base);
+  const int count = (int)min((int64_t)kTile, (int64_t)n - base);
   for (int t = threadIdx.x; t < count; t += kSortThreads) {
     const uint32_t k = s_keys[t];
     const int64_t pos = s_digit_shift[(k >> shift) & mask] + t;
@@ -326,13 +329,12 @@ cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, in
                   stream);
 }
 
-cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
-                              uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
-                              int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
-                              bool* result_in_alt, cudaStream_t stream) {
-  (void)block_sums;
+template <int ITEMS>
+cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                         int64_t n_cap, const uint32_t* n_dev, int begin_bit, int end_bit,
+                         uint32_t* hist, bool* result_in_alt, cudaStream_t stream) {
   *result_in_alt = false;
-  const int64_t nb = sort_blocks(n_cap);
+  const int64_t nb = sort_blocks(n_cap, ITEMS);
   if (nb == 0 || end_bit <= begin_bit) return cudaSuccess;
   const int bits = end_bit - begin_bit;
   const int passes = (bits + 7) / 8;
@@ -342,12 +344,12 @@ cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
     const int shift = begin_bit + p * per_pass;
     const int w = (shift + per_pass <= end_bit) ? per_pass : end_bit - shift;
     const uint32_t mask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
-    radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(kin, n_cap, n_dev, shift,
-                                                                    mask, hist, nb);
+    radix_upsweep_kernel<ITEMS><<<(unsigned)nb, kSortThreads, 0, stream>>>(kin, n_cap, n_dev,
+                                                                           shift, mask, hist, nb);
     RGS_LAUNCHED();
     radix_row_scan_kernel<<<kRadixBins, kSortThreads, 0, stream>>>(hist, nb);
     RGS_LAUNCHED();
-    radix_downsweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
+    radix_downsweep_kernel<ITEMS><<<(unsigned)nb, kSortThreads, 0, stream>>>(
         kin, vin, kout, vout, n_cap, n_dev, shift, mask, hist, nb);
     RGS_LAUNCHED();
     uint32_t* t = kin;
@@ -359,6 +361,18 @@ cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
     *result_in_alt = !*result_in_alt;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                              uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
+                              int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
+                              bool* result_in_alt, cudaStream_t stream, int items) {
+  (void)block_sums;
+  if (items == kSortItemsSmall)
+    return radix_sort_t<kSortItemsSmall>(keys, vals, keys_alt, vals_alt, n_cap, n_dev, begin_bit,
+                                         end_bit, hist, result_in_alt, stream);
+  return radix_sort_t<kSortItems>(keys, vals, keys_alt, vals_alt, n_cap, n_dev, begin_bit,
+                                  end_bit, hist, result_in_alt, stream);
 }
 
 }  // namespace rgs

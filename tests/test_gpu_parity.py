@@ -156,17 +156,23 @@ def test_everything_behind_the_near_plane():
 def test_nonfinite_gaussians_are_culled_and_counted():
     wl = synthetic.tiny(n=300)
     g = {k: v.copy() for k, v in wl.gaussians.as_dict().items()}
-    g["means"][3, 0] = np.nan
-    g["log_scales"][10, 1] = np.inf
-    g["sh"][20, 0, 2] = -np.inf
+    # Three Gaussians that the view sees, each with one non-finite parameter.
+    proj = oracle.project(g, wl.cameras)
+    m2 = proj["mean2d"][0]
+    on = np.nonzero(proj["valid"][0] & (m2[:, 0] > 10) & (m2[:, 0] < 150) & (m2[:, 1] > 10) &
+                    (m2[:, 1] < 110))[0]
+    bad = [int(on[3]), int(on[10]), int(on[20])]
+    g["means"][bad[0], 0] = np.nan
+    g["log_scales"][bad[1], 1] = np.inf
+    g["sh"][bad[2], 0, 2] = -np.inf
     gpu = gpu_render(g, wl.cameras, d_color=np.ones((wl.n_pixels, 3), np.float32) / wl.n_pixels)
     assert gpu["stats"]["n_nonfinite"] == 3
     for k in ("color", "alpha", "depth", "g_means", "g_sh", "g_pose"):
         assert np.isfinite(gpu[k]).all(), k
-    for i in (3, 10, 20):
+    for i in bad:
         assert not gpu["g_means"][i].any()
     # The remaining Gaussians render exactly as without the three bad ones.
-    keep = np.setdiff1d(np.arange(300), [3, 10, 20])
+    keep = np.setdiff1d(np.arange(300), bad)
     g2 = {k: v[keep] for k, v in g.items()}
     ref = gpu_render(g2, wl.cameras)
     np.testing.assert_allclose(gpu["color"], ref["color"], atol=1e-6)
