@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
 
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
   int32_t last[PPT];
+  uint32_t visited_end[PPT];  // one past the last list position the pixel visited
   bool done[PPT];
   bool all_done = true;
 #pragma unroll
@@ -105,9 +106,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
     last[k] = -1;
     done[k] = !(px < vp.width && py0 + k < vp.height);
+    visited_end[k] = done[k] ? range.x : range.y;
     all_done = all_done && done[k];
   }
-  uint32_t evals = 0, contribs = 0;
+  uint32_t contribs = 0;
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
     if (__syncthreads_count(all_done) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
@@ -122,28 +124,30 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     for (int g = 0; g < cnt && !all_done; ++g) {
       const float4 g0 = s0[g];
       const float4 g1 = s1[g];
+      const float4 g2 = s2[g];
       const ColumnTerms ct = column_terms(__fsub_rn(__fsub_rn(fx, g0.x), g0.z), g1.x, g1.y, g1.w);
+      const uint32_t pos = start + g;
       all_done = true;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (!done[k]) {
-          ++evals;
           const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
           const float a = fminf(c.alpha_max, opacity_times_gauss(ct, g1.z, dy));
           if (a >= c.alpha_min) {
-            const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, a));
+            // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha).
+            const float w = __fmul_rn(a, T[k]);
+            const float Tn = __fsub_rn(T[k], w);
             if (Tn < c.t_min) {
               done[k] = true;
+              visited_end[k] = pos + 1;
             } else {
-              const float w = a * T[k];
-              const float4 g2 = s2[g];
               C0[k] = fmaf(w, g2.x, C0[k]);
               C1[k] = fmaf(w, g2.y, C1[k]);
               C2[k] = fmaf(w, g2.z, C2[k]);
               D[k] = fmaf(w, g2.w, D[k]);
               T[k] = Tn;
               ++contribs;
-              last[k] = (int32_t)(start + g);
+              last[k] = (int32_t)pos;
             }
           }
         }
@@ -151,8 +155,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       }
     }
   }
+  uint32_t evals = 0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
+    evals += visited_end[k] - range.x;
     const int py = py0 + k;
     if (px < vp.width && py < vp.height) {
       const long long pix = vp.pixel_offset + (long long)py * vp.width + px;
