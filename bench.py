@@ -1,10 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark of the batched differentiable Gaussian-splatting rasterizer on GB300.
 
-One step = one forward + backward of the whole hot path over one batch: preprocess, depth sort,
-pair duplication, tile sort, tile ranges, forward blend, backward blend, backward preprocess with
-the per-view SE(3) twist gradient, for every view of the batch in one launch sequence, replayed
-as one CUDA graph. Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed
+One step = one forward + backward of the whole hot path over one batch: preprocess (cull and
+projection), compaction, depth sort, pair duplication, tile sort, tile ranges, forward blend,
+backward blend, backward preprocess with the per-view SE(3) twist gradient, for every view of the
+batch in one launch sequence, replayed as one CUDA graph. Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed
 steps. The default workload is the TUM-shaped mapping window: 10 keyframes at 640x480 over
 150k Gaussians with SH degree 3, all parameter gradients and the per-view pose gradients.
 
@@ -278,7 +278,6 @@ def run_ours(args, world, rank, local):
     cams = binding.make_cameras(wl.cameras)
     r = Renderer(dev)
     tuned = r.autotune(*params, cams)
-    r.ctx.set_phase_timing(True)
     images = (torch.empty((pixels, 3), device=dev), torch.empty(pixels, device=dev),
               torch.empty(pixels, device=dev))
     shapes = dict(means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity_logits=(n,),
@@ -290,19 +289,25 @@ def run_ours(args, world, rank, local):
         r.backward_raw(state, n, K, V, ups[0], ups[1], None, mask, out=grads)
         return state
 
-    # Size every buffer outside capture, then capture one fwd+bwd as a graph.
+    # Size every buffer outside capture, then capture one fwd+bwd as a graph. The timed graph
+    # holds the kernels only; a second capture with per-phase events gives the phase breakdown.
     state = 0
     for _ in range(2):
         state = step_eager(state)
     torch.cuda.synchronize()
     stats = r.stats(state)
-    graph = torch.cuda.CUDAGraph()
     cap_stream = torch.cuda.Stream(dev)
-    cap_stream.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(cap_stream):
-        with torch.cuda.graph(graph, stream=cap_stream):
-            step_eager(state)
-    torch.cuda.current_stream(dev).wait_stream(cap_stream)
+
+    def capture():
+        g_ = torch.cuda.CUDAGraph()
+        cap_stream.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(cap_stream):
+            with torch.cuda.graph(g_, stream=cap_stream):
+                step_eager(state)
+        torch.cuda.current_stream(dev).wait_stream(cap_stream)
+        return g_
+
+    graph = capture()
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
@@ -326,16 +331,29 @@ def run_ours(args, world, rank, local):
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        for k, v in r.ctx.phase_times(state).items():
-            phase_sum[k] = phase_sum.get(k, 0.0) + v
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
     total_ms = reduce_max(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
     value = throughput(world, pixels, args.steps, total_ms)
-    phases = {k: v / args.steps for k, v in phase_sum.items()}
     stats = r.stats(state)
+
+    # Phase breakdown (outside the timed region): the same step captured with an event at every
+    # phase boundary, replayed with the same L2 flush.
+    r.ctx.set_phase_timing(True)
+    graph_phases = capture()
+    for _ in range(2):
+        graph_phases.replay()
+    phase_reps = max(5, min(args.steps, 20))
+    for _ in range(phase_reps):
+        flush.zero_()
+        graph_phases.replay()
+        for k, v in r.ctx.phase_times(state).items():
+            phase_sum[k] = phase_sum.get(k, 0.0) + v
+    phases = {k: v / phase_reps for k, v in phase_sum.items()}
+    r.ctx.set_phase_timing(False)
+    del graph_phases
 
     # Per-view loop: the same kernels, one view per forward / backward, in one graph.
     loop_states = []

@@ -1,12 +1,13 @@
 // preprocess.cu -- per-Gaussian projection (forward) and its adjoint with the SE(3) pose
 // gradient (backward).
 //
-// Forward (Section 3.1, Eq. proj; Appendix C.1, Eq. app-sh): one thread per Gaussian reads the
-// parameters once and loops over all views of the batch, writing one projected record per
-// (view, Gaussian). Backward (Section 3.2.3, Eq. muCjac, Eq. muIjac, Eq. sigmaIjac): the same
-// thread recomputes each view's projection, chains that view's screen-space gradients to the
-// parameters, sums over views in registers (so every parameter gradient is written once, with no
-// atomics), and reduces the per-view twist gradient over the block.
+// Forward (Section 3.1, Eq. proj; Appendix C.1, Eq. app-sh), two passes: a cull pass over every
+// (view, Gaussian) that keeps the entries whose footprint may reach the image, then a full
+// projection of those candidates that writes the projected records and tile counts.
+// Backward (Section 3.2.3, Eq. muCjac, Eq. muIjac, Eq. sigmaIjac), two phases: per visible entry,
+// the view-dependent chain rule and the block-reduced twist gradient of the view; then per
+// Gaussian, the sum over the views that see it and the chain to the parameters, so every
+// parameter gradient is written once, with no atomics.
 #include <algorithm>
 
 #include "rgs_internal.cuh"

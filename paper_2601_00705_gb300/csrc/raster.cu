@@ -2,53 +2,171 @@
 //
 // Forward blend (Section 3.1, Eq. alpha; Section 3.2.2): one CTA per (view, tile); the tile's
 // Gaussians, already in near-to-far order, are staged through shared memory in batches of one
-// Gaussian per thread and every thread composites its own pixel front to back with early exit.
+// Gaussian per thread and every thread composites its pixels front to back with early exit.
 // Backward blend: the same tiles are walked back to front from each pixel's last contributor,
 // recovering the transmittance by division from the saved final value, so no per-pixel list is
 // stored; per-Gaussian screen-space gradients are reduced across the warp before one atomic per
 // value and warp.
+#include <algorithm>
+
 #include "rgs_internal.cuh"
 
 namespace rgs {
 namespace {
 
 constexpr int kDupThreads = 256;
+constexpr int kDupWarps = kDupThreads / 32;
+// Footprints of up to this many tiles are walked by their own lane into a per-warp staging
+// buffer in shared memory, from which the warp writes them out coalesced; larger ones are walked
+// by the whole warp, up to 32 tile rows at a time with the rows' tiles dealt out over the lanes.
+constexpr uint32_t kDupSerialMax = 32;
+constexpr int kDupStage = 32 * kDupSerialMax;  // staged pairs per warp and round
 
+// First lane whose inclusive count exceeds idx (idx < the warp total).
+__device__ __forceinline__ int lane_of(int incl, int idx) {
+  int lo = 0, hi = 31;
+#pragma unroll
+  for (int step = 0; step < 5; ++step) {
+    const int mid = (lo + hi) >> 1;
+    if (__shfl_sync(0xffffffffu, incl, mid) > idx) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// One (tile, vi) pair per tile touched by each visible entry, into the entry's slots
+// [offsets[k], offsets[k] + ntiles[vi]) of the pair list (so the list is in the entries' depth
+// order). The counting pass in the projection visits the same tiles, so every slot is written;
+// if that ever failed, the unused slots get the out-of-range key total_tiles, which sorts last
+// and owns no tile range.
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const __grid_constant__ Views views, int n, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ntiles,
-    const float4* __restrict__ rec0, const float4* __restrict__ rec1,
-    const float4* __restrict__ rec2, float log2_alpha_min, const Counters* __restrict__ counters_in,
-    uint32_t capacity, uint32_t* __restrict__ keys,
-    uint32_t* __restrict__ vals, Counters* __restrict__ counters) {
-  const uint32_t k = blockIdx.x * kDupThreads + threadIdx.x;
-  if (k >= counters_in->n_visible) return;
-  const uint32_t vi = order[k];
-  const int v = (int)(vi / (uint32_t)n);
-  const uint32_t begin = offsets[k];
-  const uint32_t cnt = ntiles[vi];
-  const uint32_t end = begin + cnt;  // this entry's slots: [begin, end)
-  if (end > capacity) atomicOr(&counters->status, (uint32_t)kStatusPairOverflow);
-  const ViewParams& vp = views.v[v];
-  uint32_t off = begin;
-  Ellipse e;
-  if (make_ellipse(rec0[vi], rec1[vi], log2_alpha_min, e)) {
-    for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
-                      [&](int ty, int tx0, int tx1) {
-                        const uint32_t row = (uint32_t)(vp.tile_base + ty * vp.tiles_x);
-                        for (int tx = tx0; tx <= tx1; ++tx, ++off) {
-                          if (off < end && off < capacity) {
-                            keys[off] = row + (uint32_t)tx;
-                            vals[off] = vi;
-                          }
-                        }
-                      });
-  }
-  // The counting pass visits the same tiles, so this never runs; if it ever did, the unused
-  // slots get the out-of-range key total_tiles, which sorts last and owns no tile range.
-  for (; off < end && off < capacity; ++off) {
-    keys[off] = (uint32_t)views.total_tiles;
-    vals[off] = vi;
+    const float4* __restrict__ rec0, const float4* __restrict__ rec1, float log2_alpha_min,
+    uint32_t capacity, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+    Counters* __restrict__ counters) {
+  __shared__ uint32_t s_stage[kDupWarps][kDupStage];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* stage = s_stage[warp];
+  const uint32_t n_visible = counters->n_visible;
+  const uint32_t sentinel = (uint32_t)views.total_tiles;
+  // Lane l of global warp w takes entry k = round * 32 W + l W + w (W warps in the grid): the
+  // nearest entries, whose footprints are the largest, come first in the depth order and are
+  // spread one per warp instead of filling the first warps.
+  const uint32_t n_warps = gridDim.x * kDupWarps;
+  const uint32_t gwarp = blockIdx.x * kDupWarps + warp;
+  for (uint64_t round_base = 0; round_base + gwarp < n_visible; round_base += 32ull * n_warps) {
+    const uint64_t k64 = round_base + (uint64_t)lane * n_warps + gwarp;
+    const uint32_t k = k64 < n_visible ? (uint32_t)k64 : n_visible;
+    uint32_t vi = 0, begin = 0, cnt = 0;
+    Ellipse e{};
+    bool ok = false;
+    if (k < n_visible) {
+      vi = order[k];
+      begin = offsets[k];
+      cnt = ntiles[vi];
+      if ((uint64_t)begin + cnt > capacity)
+        atomicOr(&counters->status, (uint32_t)kStatusPairOverflow);
+      ok = make_ellipse(rec0[vi], rec1[vi], log2_alpha_min, e);
+    }
+    const int v = (int)(vi / (uint32_t)max(n, 1));
+    // Small footprints: stage, then write out.
+    const bool small = k < n_visible && cnt <= kDupSerialMax;
+    const int c_small = small ? (int)cnt : 0;
+    int incl = c_small;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int staged = __shfl_sync(0xffffffffu, incl, 31);
+    if (small) {
+      int q = incl - c_small;
+      const int q_end = incl;
+      if (ok) {
+        const ViewParams& vp = views.v[v];
+        for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
+                          [&](int ty, int tx0, int tx1) {
+                            const uint32_t row = (uint32_t)(vp.tile_base + ty * vp.tiles_x);
+                            for (int tx = tx0; tx <= tx1 && q < q_end; ++tx) stage[q++] = row + tx;
+                          });
+      }
+      for (; q < q_end; ++q) stage[q] = sentinel;
+    }
+    __syncwarp();
+    for (int b = 0; b < staged; b += 32) {
+      const int idx = b + lane;
+      const int src = lane_of(incl, idx);
+      const int src_incl = __shfl_sync(0xffffffffu, incl, src);
+      const int src_cnt = __shfl_sync(0xffffffffu, c_small, src);
+      const uint32_t src_begin = __shfl_sync(0xffffffffu, begin, src);
+      const uint32_t src_vi = __shfl_sync(0xffffffffu, vi, src);
+      if (idx < staged) {
+        const uint32_t off = src_begin + (uint32_t)(idx - (src_incl - src_cnt));
+        if (off < capacity) {
+          keys[off] = stage[idx];
+          vals[off] = src_vi;
+        }
+      }
+    }
+    __syncwarp();
+    // Large footprints: the whole warp, one entry at a time.
+    unsigned big = __ballot_sync(0xffffffffu, k < n_visible && cnt > kDupSerialMax);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const uint32_t vib = __shfl_sync(0xffffffffu, vi, src);
+      const uint32_t bbeg = __shfl_sync(0xffffffffu, begin, src);
+      const uint32_t bend = min(bbeg + __shfl_sync(0xffffffffu, cnt, src), capacity);
+      uint32_t done = 0;  // pairs written so far (rows before the current chunk)
+      if (__shfl_sync(0xffffffffu, (int)ok, src)) {
+        Ellipse eb;
+        eb.mx = __shfl_sync(0xffffffffu, e.mx, src);
+        eb.my = __shfl_sync(0xffffffffu, e.my, src);
+        eb.sxx = __shfl_sync(0xffffffffu, e.sxx, src);
+        eb.sxy = __shfl_sync(0xffffffffu, e.sxy, src);
+        eb.syy = __shfl_sync(0xffffffffu, e.syy, src);
+        eb.kappa = __shfl_sync(0xffffffffu, e.kappa, src);
+        const ViewParams& vp = views.v[__shfl_sync(0xffffffffu, v, src)];
+        TileCover tc;
+        if (tc.init(eb, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y)) {
+          for (int r0 = tc.ty0; r0 <= tc.ty1; r0 += 32) {
+            // Lane l takes tile row r0 + l; the rows' tiles are then dealt out 32 at a time.
+            const int ty = r0 + lane;
+            int tx0 = 0, tx1 = -1;
+            if (ty > tc.ty1 || !tc.span(ty, tx0, tx1)) {
+              tx0 = 0;
+              tx1 = -1;
+            }
+            const int w = tx1 - tx0 + 1;
+            int rincl = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, rincl, o);
+              if (lane >= o) rincl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, rincl, 31);
+            for (int b = 0; b < total; b += 32) {
+              const int idx = b + lane;
+              const int row = lane_of(rincl, idx);
+              const int r_incl = __shfl_sync(0xffffffffu, rincl, row);
+              const int r_w = __shfl_sync(0xffffffffu, w, row);
+              const int r_tx0 = __shfl_sync(0xffffffffu, tx0, row);
+              const uint32_t off = bbeg + done + (uint32_t)idx;
+              if (idx < total && off < bend) {
+                keys[off] = (uint32_t)(vp.tile_base + (r0 + row) * vp.tiles_x + r_tx0 + idx -
+                                       (r_incl - r_w));
+                vals[off] = vib;
+              }
+            }
+            done += (uint32_t)total;
+          }
+        }
+      }
+      for (uint32_t off = bbeg + done + lane; off < bend; off += 32) {
+        keys[off] = sentinel;
+        vals[off] = vib;
+      }
+    }
   }
 }
 
@@ -414,11 +532,13 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              int64_t visible_cap, uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream) {
+  (void)rec2;
   if (visible_cap > 0) {
-    const unsigned blocks = (unsigned)((visible_cap + kDupThreads - 1) / kDupThreads);
+    const int64_t need = (visible_cap + kDupThreads - 1) / kDupThreads;
+    const unsigned blocks = (unsigned)std::min<int64_t>(need, 8 * 152);
     duplicate_kernel<<<blocks, kDupThreads, 0, stream>>>(views, n, order, offsets, ntiles, rec0,
-                                                         rec1, rec2, log2_alpha_min, counters,
-                                                         capacity, keys, vals, counters);
+                                                         rec1, log2_alpha_min, capacity, keys,
+                                                         vals, counters);
     RGS_LAUNCHED();
   }
   store_pair_count_kernel<<<1, 1, 0, stream>>>(counters, capacity);
@@ -430,10 +550,11 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, u
                                int total_tiles, uint32_t capacity, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, stream);
   if (e != cudaSuccess) return e;
-  if (capacity > 0)
+  if (capacity > 0) {
     tile_ranges_kernel<<<(capacity + 255) / 256, 256, 0, stream>>>(keys, counters,
                                                                    (uint32_t)total_tiles, ranges);
     RGS_LAUNCHED();
+  }
   return cudaGetLastError();
 }
 

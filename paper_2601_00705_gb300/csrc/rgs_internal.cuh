@@ -211,41 +211,63 @@ __device__ __forceinline__ float sqrt_fixed(float x) {
 
 // Every operation below is a single instruction with no contraction (explicitly rounded
 // arithmetic, hardware approximations of reciprocals and square roots), so the counting pass in
-// the preprocess and the emitting pass in the duplication visit exactly the same tiles. The
+// the projection and the emitting pass of the duplication visit exactly the same tiles. The
 // approximations err by a few ulp, far inside the 1-pixel padding.
-template <typename RowFn>
-__device__ __forceinline__ void for_each_tile_row(const Ellipse& e, int tile_w, int tile_h,
-                                                  int tiles_x, int tiles_y, RowFn&& fn) {
-  const float kap = __fadd_rn(__fmul_rn(e.kappa, 1.0001f), 1e-6f);
-  const float rx = sqrt_fixed(__fmul_rn(kap, e.sxx));
-  const float ry = sqrt_fixed(__fmul_rn(kap, e.syy));
-  const float inv_tw = 1.0f / (float)tile_w, inv_th = 1.0f / (float)tile_h;  // powers of two
-  const float y_lo = __fsub_rn(__fsub_rn(e.my, ry), kTilePad);
-  const float y_hi = __fadd_rn(__fadd_rn(e.my, ry), kTilePad);
-  const float x_lo = __fsub_rn(__fsub_rn(e.mx, rx), kTilePad);
-  const float x_hi = __fadd_rn(__fadd_rn(e.mx, rx), kTilePad);
-  // Clamp before converting to int: the extents of near-degenerate Gaussians can be huge.
-  const float fty0 = floorf(fminf(fmaxf(__fmul_rn(y_lo, inv_th), -1.0f), (float)tiles_y));
-  const float fty1 = floorf(fminf(fmaxf(__fmul_rn(y_hi, inv_th), -1.0f), (float)tiles_y));
-  const float ftx0 = floorf(fminf(fmaxf(__fmul_rn(x_lo, inv_tw), -1.0f), (float)tiles_x));
-  const float ftx1 = floorf(fminf(fmaxf(__fmul_rn(x_hi, inv_tw), -1.0f), (float)tiles_x));
-  const int ty0 = max(0, (int)fty0), ty1 = min(tiles_y - 1, (int)fty1);
-  const int bx0 = max(0, (int)ftx0), bx1 = min(tiles_x - 1, (int)ftx1);
-  if (ty0 > ty1 || bx0 > bx1) return;
-  if (ty0 == ty1 || bx0 == bx1) {
-    // A single row or column of tiles: the padded box is the answer.
-    for (int ty = ty0; ty <= ty1; ++ty) fn(ty, bx0, bx1);
-    return;
+//
+// TileCover holds the per-footprint constants; span(ty) gives the column span of one tile row,
+// so that rows can be walked in sequence (for_each_tile_row) or in parallel, one per lane.
+struct TileCover {
+  int ty0, ty1, bx0, bx1;
+  bool box_only;  // a single row or column of tiles: every row spans the padded box
+  int tile_w, tile_h, tiles_x;
+  float mx, my, kap, rx, ry, inv_tw, x_lo, x_hi, inv_syy, s, h, dy_star;
+
+  // False when the footprint touches no tile.
+  __device__ __forceinline__ bool init(const Ellipse& e, int tw, int th, int tiles_x_,
+                                       int tiles_y) {
+    tile_w = tw;
+    tile_h = th;
+    tiles_x = tiles_x_;
+    mx = e.mx;
+    my = e.my;
+    kap = __fadd_rn(__fmul_rn(e.kappa, 1.0001f), 1e-6f);
+    rx = sqrt_fixed(__fmul_rn(kap, e.sxx));
+    ry = sqrt_fixed(__fmul_rn(kap, e.syy));
+    inv_tw = 1.0f / (float)tw;  // powers of two
+    const float inv_th = 1.0f / (float)th;
+    const float y_lo = __fsub_rn(__fsub_rn(e.my, ry), kTilePad);
+    const float y_hi = __fadd_rn(__fadd_rn(e.my, ry), kTilePad);
+    x_lo = __fsub_rn(__fsub_rn(e.mx, rx), kTilePad);
+    x_hi = __fadd_rn(__fadd_rn(e.mx, rx), kTilePad);
+    // Clamp before converting to int: the extents of near-degenerate Gaussians can be huge.
+    const float fty0 = floorf(fminf(fmaxf(__fmul_rn(y_lo, inv_th), -1.0f), (float)tiles_y));
+    const float fty1 = floorf(fminf(fmaxf(__fmul_rn(y_hi, inv_th), -1.0f), (float)tiles_y));
+    const float ftx0 = floorf(fminf(fmaxf(__fmul_rn(x_lo, inv_tw), -1.0f), (float)tiles_x));
+    const float ftx1 = floorf(fminf(fmaxf(__fmul_rn(x_hi, inv_tw), -1.0f), (float)tiles_x));
+    ty0 = max(0, (int)fty0);
+    ty1 = min(tiles_y - 1, (int)fty1);
+    bx0 = max(0, (int)ftx0);
+    bx1 = min(tiles_x - 1, (int)ftx1);
+    if (ty0 > ty1 || bx0 > bx1) return false;
+    box_only = ty0 == ty1 || bx0 == bx1;
+    // x | y of the ellipse: centre mx + s dy, half-width h sqrt(kap - dy^2 / syy).
+    inv_syy = __fdividef(1.0f, e.syy);
+    s = __fmul_rn(e.sxy, inv_syy);
+    h = sqrt_fixed(__fsub_rn(e.sxx, __fmul_rn(e.sxy, s)));
+    dy_star = __fmul_rn(__fmul_rn(e.sxy, rx), __fdividef(1.0f, e.sxx));  // rightmost point
+    return true;
   }
-  // x | y of the ellipse: centre mx + s dy, half-width h sqrt(kap - dy^2 / syy).
-  const float inv_syy = __fdividef(1.0f, e.syy);
-  const float s = __fmul_rn(e.sxy, inv_syy);
-  const float h = sqrt_fixed(__fsub_rn(e.sxx, __fmul_rn(e.sxy, s)));
-  const float dy_star = __fmul_rn(__fmul_rn(e.sxy, rx), __fdividef(1.0f, e.sxx));  // rightmost
-  for (int ty = ty0; ty <= ty1; ++ty) {
-    const float b0 = fmaxf(__fsub_rn(__fsub_rn((float)(ty * tile_h), kTilePad), e.my), -ry);
+
+  // Column span [tx0, tx1] of tile row ty (ty0 <= ty <= ty1); false if the row is not touched.
+  __device__ __forceinline__ bool span(int ty, int& tx0, int& tx1) const {
+    if (box_only) {
+      tx0 = bx0;
+      tx1 = bx1;
+      return true;
+    }
+    const float b0 = fmaxf(__fsub_rn(__fsub_rn((float)(ty * tile_h), kTilePad), my), -ry);
     const float b1 =
-        fminf(__fsub_rn(__fadd_rn((float)(ty * tile_h + tile_h - 1), kTilePad), e.my), ry);
+        fminf(__fsub_rn(__fadd_rn((float)(ty * tile_h + tile_h - 1), kTilePad), my), ry);
     float xmax, xmin;
     if (b0 > b1) {
       // The band lies in the padding only: keep the whole padded width.
@@ -253,29 +275,38 @@ __device__ __forceinline__ void for_each_tile_row(const Ellipse& e, int tile_w, 
       xmin = x_lo;
     } else {
       if (dy_star >= b0 && dy_star <= b1) {
-        xmax = __fadd_rn(e.mx, rx);
+        xmax = __fadd_rn(mx, rx);
       } else {
         const float d = fminf(fmaxf(dy_star, b0), b1);
         const float hw =
             __fmul_rn(h, sqrt_fixed(__fsub_rn(kap, __fmul_rn(__fmul_rn(d, d), inv_syy))));
-        xmax = __fadd_rn(__fadd_rn(e.mx, __fmul_rn(s, d)), hw);
+        xmax = __fadd_rn(__fadd_rn(mx, __fmul_rn(s, d)), hw);
       }
       if (-dy_star >= b0 && -dy_star <= b1) {
-        xmin = __fsub_rn(e.mx, rx);
+        xmin = __fsub_rn(mx, rx);
       } else {
         const float d = fminf(fmaxf(-dy_star, b0), b1);
         const float hw =
             __fmul_rn(h, sqrt_fixed(__fsub_rn(kap, __fmul_rn(__fmul_rn(d, d), inv_syy))));
-        xmin = __fsub_rn(__fadd_rn(e.mx, __fmul_rn(s, d)), hw);
+        xmin = __fsub_rn(__fadd_rn(mx, __fmul_rn(s, d)), hw);
       }
       xmax = __fadd_rn(xmax, kTilePad);
       xmin = __fsub_rn(xmin, kTilePad);
     }
-    const int tx0 =
-        max(bx0, (int)floorf(fminf(fmaxf(__fmul_rn(xmin, inv_tw), -1.0f), (float)tiles_x)));
-    const int tx1 =
-        min(bx1, (int)floorf(fminf(fmaxf(__fmul_rn(xmax, inv_tw), -1.0f), (float)tiles_x)));
-    if (tx0 <= tx1) fn(ty, tx0, tx1);
+    tx0 = max(bx0, (int)floorf(fminf(fmaxf(__fmul_rn(xmin, inv_tw), -1.0f), (float)tiles_x)));
+    tx1 = min(bx1, (int)floorf(fminf(fmaxf(__fmul_rn(xmax, inv_tw), -1.0f), (float)tiles_x)));
+    return tx0 <= tx1;
+  }
+};
+
+template <typename RowFn>
+__device__ __forceinline__ void for_each_tile_row(const Ellipse& e, int tile_w, int tile_h,
+                                                  int tiles_x, int tiles_y, RowFn&& fn) {
+  TileCover tc;
+  if (!tc.init(e, tile_w, tile_h, tiles_x, tiles_y)) return;
+  for (int ty = tc.ty0; ty <= tc.ty1; ++ty) {
+    int tx0, tx1;
+    if (tc.span(ty, tx0, tx1)) fn(ty, tx0, tx1);
   }
 }
 

@@ -31,7 +31,7 @@ import numpy as np
 ROOM = np.array([6.0, 5.0, 3.0])
 
 WORKLOADS = ("tiny", "replica", "tum", "uneven", "large")
-SEEDS = dict(tiny=1001, replica=1002, tum=1003, uneven=1004, large=1005)
+SEEDS = dict(tiny=1001, replica=1002, tum=1003, uneven=1004, large=1005, crowded=1006)
 
 # Intrinsics per resolution: TUM RGB-D (640x480) and half of it, Replica (1200x680), 1080p.
 INTRINSICS = {
@@ -264,8 +264,26 @@ def large(seed=SEEDS["large"], n=3_000_000, n_views=16) -> Workload:
     return Workload("large", g, cams, grad_mask="all", depth_weight=0.0)
 
 
+def crowded(seed=SEEDS["crowded"], n=12000, depth_levels=300) -> Workload:
+    """A test scene for long tile lists: n small, faint Gaussians crowded in front of the centre
+    of a 160x120 view (identity pose), so that a few tiles are each covered by thousands of
+    them, and on only `depth_levels` distinct float32 depths, so that equal depths are common."""
+    rng = np.random.default_rng(seed)
+    z = (2.0 + 0.01 * rng.integers(0, depth_levels, size=n)).astype(np.float32)
+    xy = rng.uniform(-0.01, 0.01, size=(n, 2)) * z[:, None]
+    g = Gaussians(
+        means=np.concatenate([xy, z[:, None]], axis=1).astype(np.float32),
+        log_scales=(math.log(0.004) + rng.normal(0.0, 0.2, size=(n, 3))).astype(np.float32),
+        quats=_unit_quats(rng, n).astype(np.float32),
+        opacity_logits=np.full(n, -3.0, dtype=np.float32),
+        sh=_dc_from_rgb(rng.random((n, 1, 3))).astype(np.float32))
+    cam = camera(160, 120, 150.0, 150.0, 79.5, 59.5, np.eye(3), np.zeros(3))
+    return Workload("crowded", g, [cam], grad_mask="all", depth_weight=0.0)
+
+
 def make(name: str, **kw) -> Workload:
-    return dict(tiny=tiny, replica=replica, tum=tum, uneven=uneven, large=large)[name](**kw)
+    return dict(tiny=tiny, replica=replica, tum=tum, uneven=uneven, large=large,
+                crowded=crowded)[name](**kw)
 
 
 def upstream(workload: Workload, seed: int = 2001):
