@@ -40,12 +40,19 @@ WORKLOAD_NAMES = {
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic FP32 work of the blend kernels per evaluated (pixel, Gaussian) position (the
-# positions the forward visits until each pixel stops), as the hot-path scope table counts it:
-# the forward's coverage test and compositing, 15 FP32 operations (plus one exp); the backward's
-# recomputation, transmittance recovery and screen-space gradients, 40 FP32 operations (plus
-# two MUFU operations and the atomics after the warp reduction).
+# positions the forward visits until each pixel stops): the forward's coverage test and
+# compositing, 15 FP32 operations (plus one exp); the backward's recomputation, transmittance
+# recovery and screen-space gradients, 40 FP32 operations (plus two MUFU operations and the
+# atomics after the warp reduction).
 FWD_FLOP_PER_EVAL = 15
 BWD_FLOP_PER_EVAL = 40
+
+# DRAM bytes (read + written) per launch of a dominant kernel, from one ncu capture of exactly
+# this kernel build on exactly this workload and tile configuration; any other combination
+# reports null. Keyed by (workload, kernel, tile_w x tile_h x pixels per thread).
+MEASURED_TRAFFIC = {
+    ("tum", "blend_backward", "16x16x4"): 79.7e6,
+}
 
 
 def parse():
@@ -457,8 +464,11 @@ def run_ours(args, world, rank, local):
     dominant = max(phases, key=phases.get)
     if dominant in work:
         achieved = work[dominant] / (phases[dominant] / 1e3) / 1e12
+        traffic = MEASURED_TRAFFIC.get(
+            (args.workload, dominant,
+             f"{tuned['tile_w']}x{tuned['tile_h']}x{tuned['pixels_per_thread']}"))
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                     "peak_source": f"FP32 FMA pipe: 128 lanes x 2 FLOP x {props.multi_processor_count}"
                                    f" SMs x {sm_max:.0f} MHz ({peak_src} max SM clock)"}
     else:
