@@ -132,7 +132,9 @@ typedef struct {
   int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs */
   int64_t pair_capacity;   /* allocated pair-list capacity */
   int64_t state_bytes;     /* device bytes held by the state */
-  uint32_t status;         /* device status bits: 1 = pair list overflowed its capacity */
+  uint32_t status;         /* device status bits: 1 = pair list overflowed its capacity;
+                              2 = more visible entries than the sorted-list capacity (both only
+                              under stream capture; the output is then incomplete) */
   uint32_t kernel_launches; /* kernels launched by the last forward plus the last backward */
 } rgs_stats;
 
@@ -158,9 +160,11 @@ const char* rgs_last_error(const rgs_ctx* ctx);
  *   state: in/out. If *state is 0 a new state is created and its handle written back; otherwise
  *     the named state is reused (its previous contents are replaced). The state keeps the data
  *     the backward needs.
- * Outside stream capture the call synchronises the stream once (after binning) to size the
- * pair list. Under stream capture it never synchronises; if the pair list would overflow, the
- * kernels record it, output is incomplete and rgs_query_stats reports status bit 1. */
+ * Outside stream capture the call synchronises the stream twice (after the visibility
+ * compaction and after the pair count) to size the sorted list of visible entries and the pair
+ * list. Under stream capture it never synchronises and keeps the sizes of the last call outside
+ * capture; if a list would overflow, the kernels record it, the output is incomplete and
+ * rgs_query_stats reports status bit 1 (pairs) or 2 (visible entries). */
 rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
                               int32_t n_views, const rgs_config* cfg, rgs_images* out,
                               uint64_t* state, void* stream);
@@ -223,8 +227,8 @@ rgs_status rgs_set_phase_timing(rgs_ctx* ctx, int32_t enable);
 
 /* Device milliseconds of each phase of the most recent forward and backward on `state`
  * (ms[RGS_PHASE_COUNT]; a phase that did not run reads 0). Synchronises `stream`. Outside stream
- * capture, the duplicate phase of a forward includes the one host synchronisation that sizes
- * the pair list. */
+ * capture, the depth-sort and duplicate phases of a forward include the host synchronisations
+ * that size the visible list and the pair list. */
 rgs_status rgs_phase_times(rgs_ctx* ctx, uint64_t state, float* ms, int32_t n, void* stream);
 
 /* ---- Diagnostics: copies of a state's binning results (synchronise `stream`). ----

@@ -46,12 +46,17 @@ DEFAULT_CONFIG = dict(
     margin_cont=3e-5,
 )
 
-# Pixel ambiguity bits (see rgs_oracle.cpp). FORWARD_AMBIGUOUS marks pixels whose rendered values
-# an FP32 renderer may legitimately compute differently; BACKWARD_AMBIGUOUS adds gradient kinks.
+# Pixel ambiguity bits (see rgs_oracle.cpp). FORWARD_AMBIGUOUS marks pixels where a discrete
+# decision (coverage, stop, order, near plane) lies within FP32 rounding of its threshold, so an
+# FP32 renderer may legitimately take the other branch; BACKWARD_AMBIGUOUS adds gradient kinks.
+# AMB_COND (the propagated FP32 error bound of the colour exceeds margin_cont) involves no
+# decision: such pixels are compared in the forward at the full tolerance, but get no upstream
+# gradient in the backward comparison, where derivatives of their ill-conditioned covariances
+# amplify the FP32 error further.
 AMB_ALPHA_MIN, AMB_ALPHA_MAX, AMB_T_MIN, AMB_DEPTH_TIE, AMB_NEAR, AMB_GRAD_KINK, AMB_COND = (
     1, 2, 4, 8, 16, 32, 64)
-FORWARD_AMBIGUOUS = AMB_ALPHA_MIN | AMB_T_MIN | AMB_DEPTH_TIE | AMB_NEAR | AMB_COND
-BACKWARD_AMBIGUOUS = 127
+FORWARD_AMBIGUOUS = AMB_ALPHA_MIN | AMB_T_MIN | AMB_DEPTH_TIE | AMB_NEAR
+BACKWARD_AMBIGUOUS = FORWARD_AMBIGUOUS | AMB_ALPHA_MAX | AMB_GRAD_KINK | AMB_COND
 
 _lock = threading.Lock()
 _lib = None

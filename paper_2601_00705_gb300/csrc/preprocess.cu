@@ -455,7 +455,8 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, const float* __restrict__ sh,
     const uint32_t* __restrict__ order, const Counters* __restrict__ counters,
-    float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ pose_partial) {
+    float* __restrict__ g2d, unsigned long long* __restrict__ vis_mask, uint32_t grad_mask,
+    float* __restrict__ pose_partial) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ float s_pose[kMaxViews * 6];
   const int nv = views.n_views;
@@ -575,11 +576,13 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
 #pragma unroll
     for (int a2 = 0; a2 < 3; ++a2) out[kVMean + a2] += gd[a2];
     out[kVOpacity] = g_op;
-    // Overwrite the record for phase 2 (13 of its 16 slots).
+    // Overwrite the record for phase 2 (13 of its 16 slots) and mark the view in the
+    // Gaussian's visibility mask.
     *reinterpret_cast<float4*>(gp) = make_float4(out[0], out[1], out[2], out[3]);
     *reinterpret_cast<float4*>(gp + 4) = make_float4(out[4], out[5], out[6], out[7]);
     *reinterpret_cast<float4*>(gp + 8) = make_float4(out[8], out[9], out[10], out[11]);
     gp[12] = out[12];
+    atomicOr(vis_mask + i, 1ull << v);
     if (grad_mask & RGS_GRAD_POSE) {
       // Twist of the left update (Eq. leftupdate, Eq. muCjac, Eq. sigmaIjac):
       //   rho   = dL/dmu^C + R dL/d(dir-vector)            (the camera centre moves with -R^T t)
@@ -604,15 +607,16 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
 
 // ------------------------------------------------------------------------------------------
 // Backward, phase 2: one thread per Gaussian. Sums the phase-1 records of the views that see
-// the Gaussian (and clears them for the next backward), accumulates the SH coefficient
-// gradients view by view, and chains dL/dSigma^W to the log-scales and the quaternion once.
-// Every parameter gradient is written exactly once.
+// the Gaussian (their bits in the visibility mask phase 1 set; records and mask are cleared for
+// the next backward), accumulates the SH coefficient gradients view by view, and chains
+// dL/dSigma^W to the log-scales and the quaternion once. Every parameter gradient is written
+// exactly once.
 // ------------------------------------------------------------------------------------------
 template <int DEG>
 __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     const __grid_constant__ Views views, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ logits, const uint32_t* __restrict__ ntiles,
+    const float* __restrict__ logits, unsigned long long* __restrict__ vis_mask,
     float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ d_means,
     float* __restrict__ d_log_scales, float* __restrict__ d_quats, float* __restrict__ d_logits,
     float* __restrict__ d_sh) {
@@ -626,37 +630,55 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
   float gsh[3 * K];
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0f;
-  // Visible views as a bit mask, read with independent loads (no load waits on another).
-  uint64_t vis = 0;
-#pragma unroll 8
-  for (int v = 0; v < views.n_views; ++v)
-    vis |= (uint64_t)(__ldg(ntiles + (size_t)v * n + i) != 0u) << v;
+  // Views that see the Gaussian, as marked by phase 1 (consumed: left zero for the next call).
+  uint64_t vis = vis_mask[i];
+  if (vis) vis_mask[i] = 0ull;
   const bool any_visible = vis != 0;
-  while (vis) {
-    const int v = __ffsll((long long)vis) - 1;
+  // The records are gathered one view ahead: the next view's loads are issued before the
+  // current record is cleared and accumulated.
+  struct Rec {
+    float4 r0, r1, r2;
+    float r3;
+  };
+  auto load_rec = [&](int v, Rec& r) {
+    const float* gp = g2d + ((size_t)v * n + i) * kG2Stride;
+    r.r0 = *reinterpret_cast<const float4*>(gp);
+    r.r1 = *reinterpret_cast<const float4*>(gp + 4);
+    r.r2 = *reinterpret_cast<const float4*>(gp + 8);
+    r.r3 = gp[12];
+  };
+  int v = -1;
+  Rec cur{};
+  if (vis) {
+    v = __ffsll((long long)vis) - 1;
     vis &= vis - 1;
-    const size_t vi = (size_t)v * n + i;
-    float* gp = g2d + vi * kG2Stride;
-    const float4 r0 = *reinterpret_cast<const float4*>(gp);
-    const float4 r1 = *reinterpret_cast<const float4*>(gp + 4);
-    const float4 r2 = *reinterpret_cast<const float4*>(gp + 8);
-    const float r3 = gp[12];
+    load_rec(v, cur);
+  }
+  while (v >= 0) {
+    int v_next = -1;
+    Rec nxt{};
+    if (vis) {
+      v_next = __ffsll((long long)vis) - 1;
+      vis &= vis - 1;
+      load_rec(v_next, nxt);
+    }
     // Consume: leave the record zeroed for the next backward.
+    float* gp = g2d + ((size_t)v * n + i) * kG2Stride;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     *reinterpret_cast<float4*>(gp) = zero;
     *reinterpret_cast<float4*>(gp + 4) = zero;
     *reinterpret_cast<float4*>(gp + 8) = zero;
     gp[12] = 0.0f;
-    gm[0] += r0.x;
-    gm[1] += r0.y;
-    gm[2] += r0.z;
-    gSw[0] += r0.w;
-    gSw[1] += r1.x;
-    gSw[2] += r1.y;
-    gSw[3] += r1.z;
-    gSw[4] += r1.w;
-    gSw[5] += r2.x;
-    gop += r3;
+    gm[0] += cur.r0.x;
+    gm[1] += cur.r0.y;
+    gm[2] += cur.r0.z;
+    gSw[0] += cur.r0.w;
+    gSw[1] += cur.r1.x;
+    gSw[2] += cur.r1.y;
+    gSw[3] += cur.r1.z;
+    gSw[4] += cur.r1.w;
+    gSw[5] += cur.r2.x;
+    gop += cur.r3;
     if (grad_mask & RGS_GRAD_SH) {
       const ViewParams& vp = views.v[v];
       float d0 = m[0] - vp.cam_center[0], d1 = m[1] - vp.cam_center[1],
@@ -666,11 +688,13 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
       sh_basis<DEG>(d0 * rn, d1 * rn, d2 * rn, Y);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        gsh[3 * k + 0] += r2.y * Y[k];
-        gsh[3 * k + 1] += r2.z * Y[k];
-        gsh[3 * k + 2] += r2.w * Y[k];
+        gsh[3 * k + 0] += cur.r2.y * Y[k];
+        gsh[3 * k + 1] += cur.r2.z * Y[k];
+        gsh[3 * k + 2] += cur.r2.w * Y[k];
       }
     }
+    v = v_next;
+    cur = nxt;
   }
   float gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
   // A Gaussian culled in every view gets zero gradients; its local quantities may be
@@ -807,7 +831,7 @@ int preprocess_backward_blocks(int64_t vn) {
 }
 
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
-                                       const rgs_gaussians& g, const uint32_t* ntiles,
+                                       const rgs_gaussians& g, unsigned long long* vis_mask,
                                        const uint32_t* order, const Counters* counters,
                                        int64_t vn, float* g2d, uint32_t grad_mask,
                                        float* d_means, float* d_log_scales, float* d_quats,
@@ -818,7 +842,7 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
 #define RGS_BWD_VIEW(D)                                                                      \
   backward_view_kernel<D><<<blocks1, kPreThreads, 0, stream>>>(                              \
       views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, order, counters, \
-      g2d, grad_mask, pose_partial)
+      g2d, vis_mask, grad_mask, pose_partial)
     switch (g.sh_degree) {
       case 0: RGS_BWD_VIEW(0); break;
       case 1: RGS_BWD_VIEW(1); break;
@@ -830,7 +854,7 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
     const int blocks2 = (g.n + kPreThreads - 1) / kPreThreads;
 #define RGS_BWD_GAUSS(D)                                                                      \
   backward_gaussian_kernel<D><<<blocks2, kPreThreads, 0, stream>>>(                           \
-      views, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, ntiles, g2d, grad_mask,   \
+      views, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, vis_mask, g2d, grad_mask, \
       d_means, d_log_scales, d_quats, d_logits, d_sh)
     switch (g.sh_degree) {
       case 0: RGS_BWD_GAUSS(0); break;

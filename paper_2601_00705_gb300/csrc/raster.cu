@@ -170,21 +170,50 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   }
 }
 
+// Keeps at most `capacity` visible entries (the sorted-list capacity under stream capture): the
+// entries beyond it are dropped from this forward and the overflow is recorded.
+__global__ void clamp_visible_kernel(Counters* counters, uint32_t capacity) {
+  if (counters->n_visible > capacity) {
+    counters->n_visible = capacity;
+    counters->status |= kStatusVisibleOverflow;
+  }
+}
+
 __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
   const uint32_t p = counters->n_pairs;
   counters->n_pairs_stored = p < capacity ? p : capacity;
 }
 
+// Thread t looks at the four sorted keys 4t .. 4t + 3 (one 16-byte load; the key arrays are
+// 256-byte aligned) and the key before them, and writes the run boundaries among them.
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys,
                                    const Counters* __restrict__ counters, uint32_t total_tiles,
                                    uint2* __restrict__ ranges) {
-  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t n = counters->n_pairs_stored;
-  if (p >= n) return;
-  const uint32_t key = keys[p];
-  if (key >= total_tiles) return;
-  if (p == 0 || keys[p - 1] != key) ranges[key].x = p;
-  if (p == n - 1 || keys[p + 1] != key) ranges[key].y = p + 1;
+  const uint32_t p0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (p0 >= n) return;
+  uint32_t k[5];  // k[0] = key before p0 (or none), k[1..4] = keys p0 .. p0 + 3
+  k[0] = p0 > 0 ? keys[p0 - 1] : 0xffffffffu;
+  if (p0 + 4 <= n) {
+    const uint4 q = *reinterpret_cast<const uint4*>(keys + p0);
+    k[1] = q.x;
+    k[2] = q.y;
+    k[3] = q.z;
+    k[4] = q.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j + 1] = p0 + j < n ? keys[p0 + j] : 0xffffffffu;
+  }
+  const uint32_t next = p0 + 4 < n ? keys[p0 + 4] : 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t p = p0 + j;
+    const uint32_t key = k[j + 1];
+    if (p >= n || key >= total_tiles) continue;
+    const uint32_t after = j < 3 ? k[j + 2] : next;
+    if (p == 0 || k[j] != key) ranges[key].x = p;
+    if (p == n - 1 || after != key) ranges[key].y = p + 1;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -546,13 +575,20 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
   return cudaGetLastError();
 }
 
+cudaError_t launch_clamp_visible(Counters* counters, uint32_t capacity, cudaStream_t stream) {
+  clamp_visible_kernel<<<1, 1, 0, stream>>>(counters, capacity);
+  RGS_LAUNCHED();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
                                int total_tiles, uint32_t capacity, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, stream);
   if (e != cudaSuccess) return e;
   if (capacity > 0) {
-    tile_ranges_kernel<<<(capacity + 255) / 256, 256, 0, stream>>>(keys, counters,
-                                                                   (uint32_t)total_tiles, ranges);
+    const uint32_t threads = (capacity + 3) / 4;
+    tile_ranges_kernel<<<(threads + 255) / 256, 256, 0, stream>>>(keys, counters,
+                                                                  (uint32_t)total_tiles, ranges);
     RGS_LAUNCHED();
   }
   return cudaGetLastError();

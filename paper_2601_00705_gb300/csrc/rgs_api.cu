@@ -29,7 +29,7 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       Counters* counters, cudaStream_t stream);
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
-                                       const rgs_gaussians& g, const uint32_t* ntiles,
+                                       const rgs_gaussians& g, unsigned long long* vis_mask,
                                        const uint32_t* order, const Counters* counters,
                                        int64_t vn, float* g2d, uint32_t grad_mask,
                                        float* d_means, float* d_log_scales, float* d_quats,
@@ -41,6 +41,7 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              int64_t visible_cap, uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream);
+cudaError_t launch_clamp_visible(Counters* counters, uint32_t capacity, cudaStream_t stream);
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
                                int total_tiles, uint32_t capacity, cudaStream_t stream);
 cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, const uint2* ranges,
@@ -76,8 +77,11 @@ struct State {
   bool has_forward = false;
 
   // Capacities and regions.
-  int64_t vn_cap = 0, pix_cap = 0, tile_cap = 0, pair_cap = 0, pose_cap = 0;
-  Region r_vn, r_pix, r_tile, r_pair, r_scratch, r_pose, r_counters;
+  int64_t vn_cap = 0, n_cap = 0, pix_cap = 0, tile_cap = 0, pair_cap = 0, pose_cap = 0;
+  // Sorted-list capacity for the visible entries (not an allocation: the buffers hold vn_cap
+  // entries); the depth sort, the offsets scan and the duplication are sized by it.
+  int64_t vis_cap = 0;
+  Region r_vn, r_n, r_pix, r_tile, r_pair, r_scratch, r_pose, r_counters;
 
   // Per (view, Gaussian).
   float4 *rec0 = nullptr, *rec1 = nullptr, *rec2 = nullptr;
@@ -85,6 +89,9 @@ struct State {
   uint32_t *vis_keys[2] = {nullptr, nullptr}, *vis_vals[2] = {nullptr, nullptr};
   uint32_t* offsets = nullptr;
   float* g2d = nullptr;
+  // Per Gaussian: bit v set by the backward's phase 1 for every view v that sees it, cleared by
+  // phase 2 (zero between backward calls).
+  unsigned long long* vis_mask = nullptr;
   const uint32_t* order = nullptr;  // depth-sorted visible entries (one of vis_vals)
   // Per pixel / tile / pair.
   float* t_final = nullptr;
@@ -190,8 +197,17 @@ rgs_status ensure_scratch(rgs_ctx* ctx, State& s, int64_t items, bool capturing)
   return RGS_OK;
 }
 
-rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t pose_entries, bool capturing,
-                     cudaStream_t stream) {
+rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t n, int64_t pose_entries,
+                     bool capturing, cudaStream_t stream) {
+  if (n > s.n_cap) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "per-Gaussian buffers grow during capture");
+    RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
+    RGS_CUDA(alloc_region(s.r_n, sizeof(unsigned long long) * n), "allocate visibility masks");
+    s.vis_mask = static_cast<unsigned long long*>(s.r_n.base);
+    RGS_CUDA(cudaMemsetAsync(s.vis_mask, 0, sizeof(unsigned long long) * n, stream),
+             "zero visibility masks");
+    s.n_cap = n;
+  }
   if (vn > s.vn_cap) {
     if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "per-Gaussian buffers grow during capture");
     RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
@@ -294,6 +310,7 @@ void destroy_state(State* s) {
   for (cudaEvent_t& e : s->ev)
     if (e) cudaEventDestroy(e);
   free_region(s->r_vn);
+  free_region(s->r_n);
   free_region(s->r_pix);
   free_region(s->r_tile);
   free_region(s->r_pair);
@@ -606,7 +623,7 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   if (st != RGS_OK) return st;
   s->has_forward = false;
   const int64_t pose_entries = (int64_t)preprocess_backward_blocks(vn) * n_views * 6;
-  st = ensure_vn(ctx, *s, vn, pose_entries, capturing, stream);
+  st = ensure_vn(ctx, *s, vn, g->n, pose_entries, capturing, stream);
   if (st != RGS_OK) return st;
   st = ensure_pix_tiles(ctx, *s, views.total_pixels, views.total_tiles, capturing);
   if (st != RGS_OK) return st;
@@ -639,16 +656,31 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
                                   &cnt->n_visible, s->block_sums, stream),
            "compact");
   RGS_CUDA(mark(ctx, *s, 2, stream, capturing), "event");
+  // Size the sorted list of visible entries (outside capture: read the count back; under
+  // capture the capacity of the last eager call holds, and a larger count is clamped to it and
+  // recorded in the status word).
+  if (!capturing) {
+    RGS_CUDA(cudaMemcpyAsync(ctx->host_counters, cnt, sizeof(Counters), cudaMemcpyDeviceToHost,
+                             stream),
+             "read counters");
+    RGS_CUDA(cudaStreamSynchronize(stream), "sync for visible count");
+    const int64_t nv = ctx->host_counters->n_visible;
+    if (nv > s->vis_cap) s->vis_cap = std::max<int64_t>(nv + nv / 4, 1024);
+  } else if (s->vis_cap == 0) {
+    s->vis_cap = vn;
+  }
+  const int64_t vis_cap = std::min<int64_t>(s->vis_cap, vn);
+  RGS_CUDA(launch_clamp_visible(cnt, (uint32_t)vis_cap, stream), "clamp visible");
   // 3. Stable sort by depth (positive float bits order like the values; the sign bit is 0).
   bool alt = false;
-  RGS_CUDA(launch_radix_sort(s->vis_keys[0], s->vis_vals[0], s->vis_keys[1], s->vis_vals[1], vn,
-                             &cnt->n_visible, 0, 31, s->hist, s->block_sums, &alt, stream,
-                             kSortItemsSmall),
+  RGS_CUDA(launch_radix_sort(s->vis_keys[0], s->vis_vals[0], s->vis_keys[1], s->vis_vals[1],
+                             vis_cap, &cnt->n_visible, 0, 31, s->hist, s->block_sums, &alt,
+                             stream, kSortItemsSmall),
            "depth sort");
   s->order = s->vis_vals[alt ? 1 : 0];
   RGS_CUDA(mark(ctx, *s, 3, stream, capturing), "event");
   // 4. Pair offsets in depth order.
-  RGS_CUDA(launch_gather_scan(s->ntiles, s->order, vn, &cnt->n_visible, s->offsets,
+  RGS_CUDA(launch_gather_scan(s->ntiles, s->order, vis_cap, &cnt->n_visible, s->offsets,
                               &cnt->n_pairs, s->block_sums, stream),
            "pair offsets");
   RGS_CUDA(mark(ctx, *s, 4, stream, capturing), "event");
@@ -671,7 +703,8 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   const uint32_t capacity = (uint32_t)s->pair_cap;
   // 5. Duplicate (tile, vi) pairs in depth order.
   RGS_CUDA(launch_duplicate(views, g->n, s->order, s->offsets, s->ntiles, s->rec0, s->rec1,
-                            s->rec2, consts.log2_alpha_min, vn, capacity, s->pair_keys[0], s->pair_vals[0], cnt, stream),
+                            s->rec2, consts.log2_alpha_min, vis_cap, capacity, s->pair_keys[0],
+                            s->pair_vals[0], cnt, stream),
            "duplicate");
   RGS_CUDA(mark(ctx, *s, 5, stream, capturing), "event");
   // 6. Stable sort by global tile id.
@@ -741,7 +774,7 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_gr
                         s->g2d, s->counters, stream),
            "blend backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 1, stream, capturing), "event");
-  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->ntiles, s->order,
+  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->vis_mask, s->order,
                                       s->counters, s->vn, s->g2d, grad_mask, d_means,
                                       d_log_scales, d_quats, d_opacity_logits, d_sh,
                                       s->pose_partial, d_pose, stream),
@@ -784,7 +817,7 @@ rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t handle, rgs_stats* out, void* 
   if (!s) return fail(ctx, RGS_ERR_STATE, "unknown state handle");
   std::memset(out, 0, sizeof(*out));
   out->pair_capacity = s->pair_cap;
-  out->state_bytes = (int64_t)(s->r_vn.bytes + s->r_pix.bytes + s->r_tile.bytes +
+  out->state_bytes = (int64_t)(s->r_vn.bytes + s->r_n.bytes + s->r_pix.bytes + s->r_tile.bytes +
                                s->r_pair.bytes + s->r_scratch.bytes + s->r_pose.bytes +
                                s->r_counters.bytes);
   if (!s->counters) return RGS_OK;

@@ -58,7 +58,10 @@ struct Consts {
 };
 
 // Device status bits.
-enum StatusBits : uint32_t { kStatusPairOverflow = 1u };
+enum StatusBits : uint32_t {
+  kStatusPairOverflow = 1u,     // the pair list outgrew its capacity
+  kStatusVisibleOverflow = 2u,  // the visible entries outgrew the sorted-list capacity
+};
 
 // Device counters of one forward.
 struct Counters {
@@ -341,7 +344,7 @@ cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, in
                                uint32_t* block_sums, cudaStream_t stream);
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;      // keys per thread for large sorts (4096 per block)
+constexpr int kSortItems = 8;       // keys per thread for large sorts (2048 per block)
 constexpr int kSortItemsSmall = 4;  // for sorts whose live count is far below the capacity
 constexpr int kRadixBins = 256;
 

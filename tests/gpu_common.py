@@ -81,6 +81,13 @@ def compare_forward(gpu, orc, mask=None):
     info = dict(color_max_abs=float(ec), alpha_max_abs=float(ea), depth_max_rel=float(ed),
                 ambiguous_fraction=float(1.0 - ok.mean()) if mask is None else
                 float(1.0 - ok[mask].mean()))
+    # Pixels whose propagated FP32 error bound is large (no discrete decision near a threshold):
+    # compared like the others above, and their largest errors reported separately.
+    cond = ok & ((orc["ambiguous"] & oracle.AMB_COND) != 0)
+    if cond.any():
+        info["cond_fraction"] = float(cond.mean() if mask is None else cond[mask].mean())
+        info["cond_color_max_abs"] = float(np.abs(gpu["color"] - orc["color"])[cond].max())
+        info["cond_alpha_max_abs"] = float(np.abs(gpu["alpha"] - orc["alpha"])[cond].max())
     assert ec <= COLOR_ATOL, info
     assert ea <= COLOR_ATOL, info
     assert ed <= DEPTH_RTOL, info

@@ -193,6 +193,49 @@ def test_pair_overflow_under_capture_is_reported_then_recovered():
     r.release(state)
 
 
+def test_visible_overflow_under_capture_is_reported_then_recovered():
+    wl = synthetic.tiny(n=20000, width=128, height=96)
+    g = wl.gaussians.as_dict()
+    P = wl.n_pixels
+    r = Renderer(0)
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    full = {k: to_dev(v) for k, v in g.items()}
+    few = dict(full)
+    means = g["means"].copy()
+    means[2000:, 0] += 100.0  # all but 2000 Gaussians far outside the view
+    few["means"] = to_dev(means)
+    imgs = (torch.empty((P, 3), device="cuda"), torch.empty(P, device="cuda"),
+            torch.empty(P, device="cuda"))
+    _, _, _, state = r.forward_raw(*[few[k] for k in keys], wl.cameras, out=imgs)
+    torch.cuda.synchronize()
+    seen = r.stats(state)["n_visible"]
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            r.forward_raw(*[full[k] for k in keys], wl.cameras, state=state, out=imgs)
+    torch.cuda.current_stream().wait_stream(s)
+    graph.replay()
+    torch.cuda.synchronize()
+    st = r.stats(state)
+    assert st["status"] & 2 and seen < st["n_visible"] < 5 * seen, (seen, st)
+    # Outside capture the same call sizes the list from the true count and renders completely,
+    # exactly as a fresh state does.
+    _, _, _, state = r.forward_raw(*[full[k] for k in keys], wl.cameras, state=state, out=imgs)
+    torch.cuda.synchronize()
+    st2 = r.stats(state)
+    assert st2["status"] == 0 and st2["n_visible"] > st["n_visible"], st2
+    got = [t.clone() for t in imgs]
+    r2 = Renderer(0)
+    ref = r2.forward_raw(*[full[k] for k in keys], wl.cameras)
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref[:3]):
+        assert torch.equal(a, b)
+    r.release(state)
+    r2.release(ref[3])
+
+
 def test_invalid_arguments_and_handles_return_error_codes():
     lib = binding.load()
     r = Renderer(0)
