@@ -93,8 +93,8 @@ typedef struct {
   float bg[3];      /* background colour, added as bg * T_final */
   int32_t tile_w;   /* tile shape of the binning and blend: 16x16 (default), 8x8 or 32x8 */
   int32_t tile_h;
-  int32_t pixels_per_thread; /* vertically adjacent pixels per blend thread: 1, 2 or 4
-                                (4 not with 8x8 tiles); 0 = default (4). Results do not depend
+  int32_t pixels_per_thread; /* vertically adjacent pixels per blend thread: 1, 2, 4 or 8
+                                (4 and 8 not with 8x8 tiles); 0 = default (4). Results do not depend
                                 on it or on the tile shape beyond atomics-order rounding of the
                                 gradients */
 } rgs_config;
@@ -185,7 +185,7 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t state, const rgs_image_gra
 
 /* Autotuner: picks the blend tile shape and pixels per thread (the per-thread batch depth of the
  * blends) that make one forward + backward of this exact workload fastest on this GPU. Every
- * supported combination (16x16, 8x8, 32x8 tiles; 1, 2 or 4 pixels per thread) is timed with
+ * supported combination (16x16, 8x8, 32x8 tiles; 1, 2, 4 or 8 pixels per thread) is timed with
  * CUDA events (one warm-up and three timed runs of forward + backward with a zero upstream
  * gradient, all gradients requested) in scratch buffers of its own. The fastest is written into
  * cfg->tile_w, cfg->tile_h and cfg->pixels_per_thread (other fields are kept) and cached in the

@@ -217,9 +217,38 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys,
 }
 
 // ------------------------------------------------------------------------------------------
+// Staging of a batch of Gaussians in shared memory. For an even number of pixels per thread every
+// per-Gaussian operand is stored twice, as (x, x) pairs, so the packed f32x2 arithmetic of two
+// pixels reads its broadcast operands straight from shared memory:
+//   [0] (mx hi, mx hi), (mx lo, mx lo)   [1] (my hi, my hi), (my lo, my lo)
+//   [2] (qa, qa), (qb, qb)               [3] (qc, qc), (log2 o, log2 o)
+//   [4] (r, r), (g, g)                   [5] (b, b), (z, z)
+// With one pixel per thread rows 0..2 hold rec0, rec1, rec2 as float4.
+// ------------------------------------------------------------------------------------------
+template <int R, int N>
+__device__ __forceinline__ void stage_gaussian(ulonglong2 (&sp)[R][N], int t, float4 r0,
+                                               float4 r1, float4 r2) {
+  if constexpr (R == 6) {
+    sp[0][t] = make_ulonglong2(f2_make(r0.x, r0.x), f2_make(r0.z, r0.z));
+    sp[1][t] = make_ulonglong2(f2_make(r0.y, r0.y), f2_make(r0.w, r0.w));
+    sp[2][t] = make_ulonglong2(f2_make(r1.x, r1.x), f2_make(r1.y, r1.y));
+    sp[3][t] = make_ulonglong2(f2_make(r1.z, r1.z), f2_make(r1.w, r1.w));
+    sp[4][t] = make_ulonglong2(f2_make(r2.x, r2.x), f2_make(r2.y, r2.y));
+    sp[5][t] = make_ulonglong2(f2_make(r2.z, r2.z), f2_make(r2.w, r2.w));
+  } else {
+    reinterpret_cast<float4*>(sp[0])[t] = r0;
+    reinterpret_cast<float4*>(sp[1])[t] = r1;
+    reinterpret_cast<float4*>(sp[2])[t] = r2;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Forward blend. A CTA covers one TW x TH tile with TW * TH / PPT threads; thread t owns the
 // PPT vertically adjacent pixels (x, y0 + k), k < PPT, of column x = t % TW, so every Gaussian
-// staged in shared memory is read once per thread and evaluated for PPT pixels.
+// staged in shared memory is read once per thread and evaluated for PPT pixels. With an even PPT
+// the pixels go in pairs through packed f32x2 arithmetic, branch-free: a pixel that does not
+// composite a Gaussian gets weight +0, which leaves its colour, depth and transmittance
+// bit-identical, so the result equals the one-pixel-per-thread kernel's.
 // ------------------------------------------------------------------------------------------
 template <int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
@@ -229,8 +258,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     float* __restrict__ depth, float* __restrict__ alpha_out, float* __restrict__ t_final,
     int32_t* __restrict__ last_index, Counters* __restrict__ counters) {
   constexpr int kThreads = TW * TH / PPT;
+  constexpr bool kPacked = PPT % 2 == 0;
+  constexpr int P2 = kPacked ? PPT / 2 : 1;
   static_assert(kThreads % 32 == 0, "whole warps only");
-  __shared__ float4 s0[kThreads], s1[kThreads], s2[kThreads];
+  __shared__ ulonglong2 sp[kPacked ? 6 : 3][kThreads];
   __shared__ unsigned long long s_eval[kThreads / 32], s_contrib[kThreads / 32];
   const int gtile = blockIdx.x;
   const int v = view_of_tile(views, gtile);
@@ -243,6 +274,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   const uint2 range = ranges[gtile];
 
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
+  f32x2 T2[P2], C02[P2], C12[P2], C22[P2], D2[P2], FY[P2];
   int32_t last[PPT];
   uint32_t visited_end[PPT];  // one past the last list position the pixel visited
   bool done[PPT];
@@ -256,50 +288,113 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     visited_end[k] = done[k] ? range.x : range.y;
     all_done = all_done && done[k];
   }
+#pragma unroll
+  for (int q = 0; q < P2; ++q) {
+    T2[q] = f2_make(1.0f, 1.0f);
+    C02[q] = C12[q] = C22[q] = D2[q] = f2_make(0.0f, 0.0f);
+    FY[q] = f2_make((float)(py0 + 2 * q), (float)(py0 + 2 * q + 1));
+  }
+  const f32x2 FX = f2_make(fx, fx);
   uint32_t contribs = 0;
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
     if (__syncthreads_count(all_done) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
     if (j < range.y) {
       const uint32_t vi = pair_vals[j];
-      s0[threadIdx.x] = rec0[vi];
-      s1[threadIdx.x] = rec1[vi];
-      s2[threadIdx.x] = rec2[vi];
+      stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi]);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kThreads, range.y - start);
     for (int g = 0; g < cnt && !all_done; ++g) {
-      const float4 g0 = s0[g];
-      const float4 g1 = s1[g];
-      const float4 g2 = s2[g];
-      const ColumnTerms ct = column_terms(__fsub_rn(__fsub_rn(fx, g0.x), g0.z), g1.x, g1.y, g1.w);
       const uint32_t pos = start + g;
-      all_done = true;
+      if constexpr (kPacked) {
+        const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
+        const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
+        // Column terms of Eq. alpha's exponent, computed as (x, x) pairs.
+        const f32x2 dx = f2_sub(f2_sub(FX, X.x), X.y);
+        const f32x2 AA = f2_fma(f2_mul(Q1.x, dx), dx, Q2.y);
+        const f32x2 BB = f2_mul(Q1.y, dx);
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (!done[k]) {
-          const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
-          const float a = fminf(c.alpha_max, opacity_times_gauss(ct, g1.z, dy));
-          if (a >= c.alpha_min) {
-            // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha).
-            const float w = __fmul_rn(a, T[k]);
-            const float Tn = __fsub_rn(T[k], w);
-            if (Tn < c.t_min) {
-              done[k] = true;
-              visited_end[k] = pos + 1;
-            } else {
-              C0[k] = fmaf(w, g2.x, C0[k]);
-              C1[k] = fmaf(w, g2.y, C1[k]);
-              C2[k] = fmaf(w, g2.z, C2[k]);
-              D[k] = fmaf(w, g2.w, D[k]);
-              T[k] = Tn;
-              ++contribs;
-              last[k] = (int32_t)pos;
+        for (int q = 0; q < P2; ++q) {
+          const int k0 = 2 * q, k1 = 2 * q + 1;
+          const f32x2 dy = f2_sub(f2_sub(FY[q], Y.x), Y.y);
+          const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
+          const float a0 = fminf(c.alpha_max, ex2_approx(f2_lo(pw)));
+          const float a1 = fminf(c.alpha_max, ex2_approx(f2_hi(pw)));
+          const bool cov0 = !done[k0] && a0 >= c.alpha_min;
+          const bool cov1 = !done[k1] && a1 >= c.alpha_min;
+          // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha).
+          const f32x2 w = f2_mul(f2_make(a0, a1), T2[q]);
+          const f32x2 Tn = f2_sub(T2[q], w);
+          const bool stop0 = cov0 && f2_lo(Tn) < c.t_min;
+          const bool stop1 = cov1 && f2_hi(Tn) < c.t_min;
+          const bool take0 = cov0 && !stop0, take1 = cov1 && !stop1;
+          const f32x2 wm = f2_make(take0 ? f2_lo(w) : 0.0f, take1 ? f2_hi(w) : 0.0f);
+          C02[q] = f2_fma(wm, CA.x, C02[q]);
+          C12[q] = f2_fma(wm, CA.y, C12[q]);
+          C22[q] = f2_fma(wm, CB.x, C22[q]);
+          D2[q] = f2_fma(wm, CB.y, D2[q]);
+          T2[q] = f2_sub(T2[q], wm);
+          if (stop0) {
+            done[k0] = true;
+            visited_end[k0] = pos + 1;
+          }
+          if (stop1) {
+            done[k1] = true;
+            visited_end[k1] = pos + 1;
+          }
+          if (take0) last[k0] = (int32_t)pos;
+          if (take1) last[k1] = (int32_t)pos;
+          contribs += (uint32_t)take0 + (uint32_t)take1;
+        }
+      } else {
+        const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
+        const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
+        const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
+        const ColumnTerms ct =
+            column_terms(__fsub_rn(__fsub_rn(fx, g0.x), g0.z), g1.x, g1.y, g1.w);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (!done[k]) {
+            const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
+            const float a = fminf(c.alpha_max, opacity_times_gauss(ct, g1.z, dy));
+            if (a >= c.alpha_min) {
+              const float w = __fmul_rn(a, T[k]);
+              const float Tn = __fsub_rn(T[k], w);
+              if (Tn < c.t_min) {
+                done[k] = true;
+                visited_end[k] = pos + 1;
+              } else {
+                C0[k] = fmaf(w, g2.x, C0[k]);
+                C1[k] = fmaf(w, g2.y, C1[k]);
+                C2[k] = fmaf(w, g2.z, C2[k]);
+                D[k] = fmaf(w, g2.w, D[k]);
+                T[k] = Tn;
+                ++contribs;
+                last[k] = (int32_t)pos;
+              }
             }
           }
         }
-        all_done = all_done && done[k];
       }
+      all_done = true;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) all_done = all_done && done[k];
+    }
+  }
+  if constexpr (kPacked) {
+#pragma unroll
+    for (int q = 0; q < P2; ++q) {
+      T[2 * q] = f2_lo(T2[q]);
+      T[2 * q + 1] = f2_hi(T2[q]);
+      C0[2 * q] = f2_lo(C02[q]);
+      C0[2 * q + 1] = f2_hi(C02[q]);
+      C1[2 * q] = f2_lo(C12[q]);
+      C1[2 * q + 1] = f2_hi(C12[q]);
+      C2[2 * q] = f2_lo(C22[q]);
+      C2[2 * q + 1] = f2_hi(C22[q]);
+      D[2 * q] = f2_lo(D2[q]);
+      D[2 * q + 1] = f2_hi(D2[q]);
     }
   }
   uint32_t evals = 0;
@@ -401,8 +496,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     const float* __restrict__ d_color, const float* __restrict__ d_depth,
     const float* __restrict__ d_alpha, float* __restrict__ g2d) {
   constexpr int kThreads = TW * TH / PPT;
+  constexpr bool kPacked = PPT % 2 == 0;
+  constexpr int P2 = kPacked ? PPT / 2 : 1;
   static_assert(kThreads % 32 == 0, "whole warps only");
-  __shared__ float4 s0[kThreads], s1[kThreads], s2[kThreads];
+  __shared__ ulonglong2 sp[kPacked ? 6 : 3][kThreads];
   __shared__ uint32_t s_vi[kThreads];
   __shared__ int s_max_last[kThreads / 32];
   const int gtile = blockIdx.x;
@@ -446,6 +543,21 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     U[k] = Tfin * (gC0[k] * c.bg[0] + gC1[k] * c.bg[1] + gC2[k] * c.bg[2]);
     thread_last = max(thread_last, last[k]);
   }
+  // The same state as (pixel 2q, pixel 2q + 1) pairs for the packed arithmetic.
+  f32x2 T2[P2], U2[P2], GC02[P2], GC12[P2], GC22[P2], GD2[P2], GAT2[P2], FY[P2];
+#pragma unroll
+  for (int q = 0; q < P2; ++q) {
+    const int k0 = kPacked ? 2 * q : 0, k1 = kPacked ? 2 * q + 1 : 0;
+    T2[q] = f2_make(T[k0], T[k1]);
+    U2[q] = f2_make(U[k0], U[k1]);
+    GC02[q] = f2_make(gC0[k0], gC0[k1]);
+    GC12[q] = f2_make(gC1[k0], gC1[k1]);
+    GC22[q] = f2_make(gC2[k0], gC2[k1]);
+    GD2[q] = f2_make(gD[k0], gD[k1]);
+    GAT2[q] = f2_make(gAT[k0], gAT[k1]);
+    FY[q] = f2_make((float)(py0 + k0), (float)(py0 + k1));
+  }
+  const f32x2 FX = f2_make(fx, fx), ONE2 = f2_make(1.0f, 1.0f), ZERO2 = f2_make(0.0f, 0.0f);
   // Only list positions up to the largest last-contributor index of the tile matter.
   int m = thread_last;
 #pragma unroll
@@ -465,56 +577,116 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     if (j < bend) {
       const uint32_t vi = pair_vals[j];
       s_vi[threadIdx.x] = vi;
-      s0[threadIdx.x] = rec0[vi];
-      s1[threadIdx.x] = rec1[vi];
-      s2[threadIdx.x] = rec2[vi];
+      stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi]);
     }
     __syncthreads();
     for (int jj = bend - 1; jj >= bstart; --jj) {
       const int g = jj - bstart;
       float acc[10];
 #pragma unroll
-      for (int s = 0; s < 10; ++s) acc[s] = 0.0f;
+      for (int s2 = 0; s2 < 10; ++s2) acc[s2] = 0.0f;
       bool contrib = false;
       if (jj <= thread_last) {
-        const float4 g0 = s0[g];
-        const float4 g1 = s1[g];
-        const float4 g2 = s2[g];
-        const float dx = __fsub_rn(__fsub_rn(fx, g0.x), g0.z);
-        const ColumnTerms ct = column_terms(dx, g1.x, g1.y, g1.w);
         // Per-thread moments of dL/dpower over the thread's pixels (all share dx):
         // sdp = sum dp, sdy = sum dp dy, sdy2 = sum dp dy^2.
-        float sdp = 0.0f, sdy = 0.0f, sdy2 = 0.0f;
+        float sdp = 0.0f, sdy = 0.0f, sdy2 = 0.0f, dx, qa, qb, qc, lo;
+        if constexpr (kPacked) {
+          const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
+          const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
+          const f32x2 dx2 = f2_sub(f2_sub(FX, X.x), X.y);
+          const f32x2 AA = f2_fma(f2_mul(Q1.x, dx2), dx2, Q2.y);
+          const f32x2 BB = f2_mul(Q1.y, dx2);
+          f32x2 aR = ZERO2, aG = ZERO2, aB = ZERO2, aZ = ZERO2, mP = ZERO2, mY = ZERO2,
+                mYY = ZERO2;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          if (jj > last[k]) continue;
-          const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
-          const float oG = opacity_times_gauss(ct, g1.z, dy);
-          const float a = fminf(c.alpha_max, oG);
-          if (a < c.alpha_min) continue;
-          contrib = true;
-          const float rom = rcp_approx(__fsub_rn(1.0f, a));
-          T[k] = T[k] * rom;  // transmittance in front of this Gaussian
-          const float w = a * T[k];
-          acc[kGR] = fmaf(gC0[k], w, acc[kGR]);
-          acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
-          acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
-          acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
-          const float q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g2.w)));
-          const float dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
-          U[k] = fmaf(w, q, U[k]);
-          if (oG < c.alpha_max) {
-            const float dp = dLda * a;  // dL/dpower: d alpha / d power = o G = alpha
-            sdp += dp;
-            const float t = dp * dy;
-            sdy += t;
-            sdy2 = fmaf(t, dy, sdy2);
+          for (int q = 0; q < P2; ++q) {
+            const int k0 = 2 * q, k1 = 2 * q + 1;
+            const f32x2 dy = f2_sub(f2_sub(FY[q], Y.x), Y.y);
+            const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
+            const float oG0 = ex2_approx(f2_lo(pw)), oG1 = ex2_approx(f2_hi(pw));
+            const float a0 = fminf(c.alpha_max, oG0), a1 = fminf(c.alpha_max, oG1);
+            const bool cov0 = jj <= last[k0] && a0 >= c.alpha_min;
+            const bool cov1 = jj <= last[k1] && a1 >= c.alpha_min;
+            contrib = contrib || cov0 || cov1;
+            // A pixel this Gaussian does not cover gets alpha 0 and 1 / (1 - alpha) = 1, so its
+            // transmittance, suffix sum and every accumulator stay bit-identical.
+            const f32x2 am = f2_make(cov0 ? a0 : 0.0f, cov1 ? a1 : 0.0f);
+            const f32x2 om = f2_sub(ONE2, am);
+            const f32x2 rom = f2_make(cov0 ? rcp_approx(f2_lo(om)) : 1.0f,
+                                      cov1 ? rcp_approx(f2_hi(om)) : 1.0f);
+            T2[q] = f2_mul(T2[q], rom);  // transmittance in front of this Gaussian
+            const f32x2 w = f2_mul(am, T2[q]);
+            aR = f2_fma(GC02[q], w, aR);
+            aG = f2_fma(GC12[q], w, aG);
+            aB = f2_fma(GC22[q], w, aB);
+            aZ = f2_fma(GD2[q], w, aZ);
+            const f32x2 qv =
+                f2_fma(GC02[q], CA.x, f2_fma(GC12[q], CA.y, f2_fma(GC22[q], CB.x, f2_mul(GD2[q], CB.y))));
+            const f32x2 dLda = f2_fma(T2[q], qv, f2_mul(rom, f2_sub(GAT2[q], U2[q])));
+            U2[q] = f2_fma(w, qv, U2[q]);
+            // dL/dpower = dL/dalpha * alpha (d alpha / d power = o G = alpha), unclamped only.
+            const f32x2 dpv = f2_mul(dLda, am);
+            const bool m0 = cov0 && oG0 < c.alpha_max, m1 = cov1 && oG1 < c.alpha_max;
+            const f32x2 dp = f2_make(m0 ? f2_lo(dpv) : 0.0f, m1 ? f2_hi(dpv) : 0.0f);
+            mP = f2_add(mP, dp);
+            const f32x2 t = f2_mul(dp, dy);
+            mY = f2_add(mY, t);
+            mYY = f2_fma(t, dy, mYY);
+          }
+          acc[kGR] = f2_lo(aR) + f2_hi(aR);
+          acc[kGG] = f2_lo(aG) + f2_hi(aG);
+          acc[kGB] = f2_lo(aB) + f2_hi(aB);
+          acc[kGZ] = f2_lo(aZ) + f2_hi(aZ);
+          sdp = f2_lo(mP) + f2_hi(mP);
+          sdy = f2_lo(mY) + f2_hi(mY);
+          sdy2 = f2_lo(mYY) + f2_hi(mYY);
+          dx = f2_lo(dx2);
+          qa = f2_lo(Q1.x);
+          qb = f2_lo(Q1.y);
+          qc = f2_lo(Q2.x);
+          lo = f2_lo(Q2.y);
+        } else {
+          const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
+          const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
+          const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
+          dx = __fsub_rn(__fsub_rn(fx, g0.x), g0.z);
+          qa = g1.x;
+          qb = g1.y;
+          qc = g1.z;
+          lo = g1.w;
+          const ColumnTerms ct = column_terms(dx, qa, qb, lo);
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (jj > last[k]) continue;
+            const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
+            const float oG = opacity_times_gauss(ct, qc, dy);
+            const float a = fminf(c.alpha_max, oG);
+            if (a < c.alpha_min) continue;
+            contrib = true;
+            const float rom = rcp_approx(__fsub_rn(1.0f, a));
+            T[k] = T[k] * rom;  // transmittance in front of this Gaussian
+            const float w = a * T[k];
+            acc[kGR] = fmaf(gC0[k], w, acc[kGR]);
+            acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
+            acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
+            acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
+            const float q =
+                fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g2.w)));
+            const float dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
+            U[k] = fmaf(w, q, U[k]);
+            if (oG < c.alpha_max) {
+              const float dp = dLda * a;  // dL/dpower: d alpha / d power = o G = alpha
+              sdp += dp;
+              const float t = dp * dy;
+              sdy += t;
+              sdy2 = fmaf(t, dy, sdy2);
+            }
           }
         }
         if (contrib) {
           // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = p - mu^I, alpha = o exp(power).
-          const float ca = g1.x * (-2.0f * kLn2), cb = g1.y * (-kLn2), cc = g1.z * (-2.0f * kLn2);
-          acc[kGOp] = sdp * ex2_approx(-g1.w);  // d alpha / d o = G = alpha / o, 1/o = 2^-log2 o
+          const float ca = qa * (-2.0f * kLn2), cb = qb * (-kLn2), cc = qc * (-2.0f * kLn2);
+          acc[kGOp] = sdp * ex2_approx(-lo);  // d alpha / d o = G = alpha / o, 1/o = 2^-log2 o
           acc[kGMx] = fmaf(ca * dx, sdp, cb * sdy);
           acc[kGMy] = fmaf(cb * dx, sdp, cc * sdy);
           acc[kGCa] = -0.5f * dx * dx * sdp;
@@ -609,11 +781,13 @@ cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, cons
   RGS_BLEND(16, 16, 1);
   RGS_BLEND(16, 16, 2);
   RGS_BLEND(16, 16, 4);
+  RGS_BLEND(16, 16, 8);
   RGS_BLEND(8, 8, 1);
   RGS_BLEND(8, 8, 2);
   RGS_BLEND(32, 8, 1);
   RGS_BLEND(32, 8, 2);
   RGS_BLEND(32, 8, 4);
+  RGS_BLEND(32, 8, 8);
 #undef RGS_BLEND
   return cudaErrorInvalidValue;
 }

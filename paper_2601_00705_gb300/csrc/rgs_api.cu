@@ -331,9 +331,9 @@ rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const 
   const int ppt = cfg.pixels_per_thread == 0 ? 4 : cfg.pixels_per_thread;
   if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8)))
     return fail(ctx, RGS_ERR_INVALID_ARG, "tile shape must be 16x16, 8x8 or 32x8");
-  if (!(ppt == 1 || ppt == 2 || ppt == 4) || (tw * th / ppt) % 32 != 0)
+  if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || (tw * th / ppt) % 32 != 0)
     return fail(ctx, RGS_ERR_INVALID_ARG,
-                "pixels_per_thread must be 1, 2 or 4 with whole warps per tile");
+                "pixels_per_thread must be 1, 2, 4 or 8 with whole warps per tile");
   std::memset(&views, 0, sizeof(views));
   views.n_views = n_views;
   views.tile_w = tw;
@@ -510,8 +510,8 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
     rgs_images out{img, img + 3 * pixels, img + 4 * pixels};
     rgs_image_grads up{upc, nullptr, nullptr};
     const uint32_t mask = RGS_GRAD_ALL;
-    const TuneChoice cands[] = {{16, 16, 4}, {16, 16, 2}, {16, 16, 1}, {8, 8, 2},
-                                {8, 8, 1},   {32, 8, 4},  {32, 8, 2},  {32, 8, 1}};
+    const TuneChoice cands[] = {{16, 16, 4}, {16, 16, 8}, {16, 16, 2}, {16, 16, 1}, {8, 8, 2},
+                                {8, 8, 1},   {32, 8, 8},  {32, 8, 4},  {32, 8, 2}, {32, 8, 1}};
     float best = 1e30f;
     TuneChoice choice = cands[0];
     for (const TuneChoice& c : cands) {
