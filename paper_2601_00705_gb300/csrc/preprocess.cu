@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ cand,
     Counters* __restrict__ counters, int views_per_chunk) {
+  chain_wait_release();
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   const bool in_range = i < n;
   const int lane = threadIdx.x & 31;
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const float* __restrict__ logits, const float* __restrict__ sh,
     const uint32_t* __restrict__ cand, float4* __restrict__ rec0, float4* __restrict__ rec1,
     float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, Counters* __restrict__ counters) {
+  chain_wait_release();
   constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t n_cand = counters->n_candidates;
   for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_cand;
@@ -457,6 +459,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const uint32_t* __restrict__ order, const Counters* __restrict__ counters,
     float* __restrict__ g2d, unsigned long long* __restrict__ vis_mask, uint32_t grad_mask,
     float* __restrict__ pose_partial) {
+  chain_wait_release();
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ float s_pose[kMaxViews * 6];
   const int nv = views.n_views;
@@ -620,6 +623,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ d_means,
     float* __restrict__ d_log_scales, float* __restrict__ d_quats, float* __restrict__ d_logits,
     float* __restrict__ d_sh) {
+  chain_wait_release();
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   if (i >= n) return;
@@ -774,6 +778,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
 // d_pose[v,k] = sum over blocks of the partials, in double precision.
 __global__ void pose_finalize_kernel(const float* __restrict__ partial, int n_blocks,
                                      int n_views, float* __restrict__ d_pose) {
+  chain_wait_release();
   const int vk = blockIdx.x;  // v * 6 + k
   double s = 0.0;
   for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += (double)partial[(size_t)b * n_views * 6 + vk];
@@ -801,17 +806,18 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   const int chunks = max(1, min(views.n_views, (target_blocks + blocks_x - 1) / blocks_x));
   const int per_chunk = (views.n_views + chunks - 1) / chunks;
   const dim3 grid((unsigned)blocks_x, (unsigned)((views.n_views + per_chunk - 1) / per_chunk));
-  cull_kernel<<<grid, kPreThreads, 0, stream>>>(views, c, g.n, g.means, g.log_scales, g.quats,
-                                                g.opacity_logits, ntiles, cand, counters,
-                                                per_chunk);
+  cudaError_t e = launch_chained(cull_kernel, grid, dim3(kPreThreads), stream, views, c, g.n,
+                                 g.means, g.log_scales, g.quats, g.opacity_logits, ntiles, cand,
+                                 counters, per_chunk);
   RGS_LAUNCHED();
+  if (e != cudaSuccess) return e;
   // Pass 2: grid-stride over the candidates.
   const int64_t vn = (int64_t)views.n_views * g.n;
   const int blocks2 = (int)std::min<int64_t>((vn + kPreThreads - 1) / kPreThreads, 16 * 152);
-#define RGS_PROJECT(D)                                                                        \
-  project_kernel<D><<<blocks2, kPreThreads, 0, stream>>>(views, c, g.n, g.means, g.log_scales, \
-                                                         g.quats, g.opacity_logits, g.sh, cand, \
-                                                         rec0, rec1, rec2, ntiles, counters)
+#define RGS_PROJECT(D)                                                                         \
+  e = launch_chained(project_kernel<D>, dim3(blocks2), dim3(kPreThreads), stream, views, c, g.n, \
+                     g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,                    \
+                     (const uint32_t*)cand, rec0, rec1, rec2, ntiles, counters)
   switch (g.sh_degree) {
     case 0: RGS_PROJECT(0); break;
     case 1: RGS_PROJECT(1); break;
@@ -820,7 +826,7 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   }
   RGS_LAUNCHED();
 #undef RGS_PROJECT
-  return cudaGetLastError();
+  return e;
 }
 
 // Phase-1 grid: a fixed number of blocks (grid-stride over the visible entries), so the
@@ -838,11 +844,12 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        float* d_logits, float* d_sh, float* pose_partial,
                                        float* d_pose, cudaStream_t stream) {
   const int blocks1 = preprocess_backward_blocks(vn);
+  cudaError_t e = cudaSuccess;
   if (g.n > 0) {
-#define RGS_BWD_VIEW(D)                                                                      \
-  backward_view_kernel<D><<<blocks1, kPreThreads, 0, stream>>>(                              \
-      views, c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, order, counters, \
-      g2d, vis_mask, grad_mask, pose_partial)
+#define RGS_BWD_VIEW(D)                                                                       \
+  e = launch_chained(backward_view_kernel<D>, dim3(blocks1), dim3(kPreThreads), stream, views, \
+                     c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, order,    \
+                     counters, g2d, vis_mask, grad_mask, pose_partial)
     switch (g.sh_degree) {
       case 0: RGS_BWD_VIEW(0); break;
       case 1: RGS_BWD_VIEW(1); break;
@@ -851,11 +858,12 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
     }
     RGS_LAUNCHED();
 #undef RGS_BWD_VIEW
+    if (e != cudaSuccess) return e;
     const int blocks2 = (g.n + kPreThreads - 1) / kPreThreads;
-#define RGS_BWD_GAUSS(D)                                                                      \
-  backward_gaussian_kernel<D><<<blocks2, kPreThreads, 0, stream>>>(                           \
-      views, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, vis_mask, g2d, grad_mask, \
-      d_means, d_log_scales, d_quats, d_logits, d_sh)
+#define RGS_BWD_GAUSS(D)                                                                          \
+  e = launch_chained(backward_gaussian_kernel<D>, dim3(blocks2), dim3(kPreThreads), stream, views, \
+                     g.n, g.means, g.log_scales, g.quats, g.opacity_logits, vis_mask, g2d,        \
+                     grad_mask, d_means, d_log_scales, d_quats, d_logits, d_sh)
     switch (g.sh_degree) {
       case 0: RGS_BWD_GAUSS(0); break;
       case 1: RGS_BWD_GAUSS(1); break;
@@ -864,18 +872,18 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
     }
     RGS_LAUNCHED();
 #undef RGS_BWD_GAUSS
+    if (e != cudaSuccess) return e;
   }
   if ((grad_mask & RGS_GRAD_POSE) && d_pose) {
     if (g.n > 0) {
-      pose_finalize_kernel<<<views.n_views * 6, 256, 0, stream>>>(pose_partial, blocks1,
-                                                                  views.n_views, d_pose);
+      e = launch_chained(pose_finalize_kernel, dim3(views.n_views * 6), dim3(256), stream,
+                         (const float*)pose_partial, blocks1, views.n_views, d_pose);
       RGS_LAUNCHED();
     } else {
-      cudaError_t e = cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * views.n_views, stream);
-      if (e != cudaSuccess) return e;
+      e = cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * views.n_views, stream);
     }
   }
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace rgs

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const float4* __restrict__ rec0, const float4* __restrict__ rec1, float log2_alpha_min,
     uint32_t capacity, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
     Counters* __restrict__ counters) {
+  chain_wait_release();
   __shared__ uint32_t s_stage[kDupWarps][kDupStage];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* stage = s_stage[warp];
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
 // Keeps at most `capacity` visible entries (the sorted-list capacity under stream capture): the
 // entries beyond it are dropped from this forward and the overflow is recorded.
 __global__ void clamp_visible_kernel(Counters* counters, uint32_t capacity) {
+  chain_wait_release();
   if (counters->n_visible > capacity) {
     counters->n_visible = capacity;
     counters->status |= kStatusVisibleOverflow;
@@ -180,6 +182,7 @@ __global__ void clamp_visible_kernel(Counters* counters, uint32_t capacity) {
 }
 
 __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
+  chain_wait_release();
   const uint32_t p = counters->n_pairs;
   counters->n_pairs_stored = p < capacity ? p : capacity;
 }
@@ -189,6 +192,7 @@ __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys,
                                    const Counters* __restrict__ counters, uint32_t total_tiles,
                                    uint2* __restrict__ ranges) {
+  chain_wait_release();
   const uint32_t n = counters->n_pairs_stored;
   const uint32_t p0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
   if (p0 >= n) return;
@@ -257,6 +261,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     const float4* __restrict__ rec1, const float4* __restrict__ rec2, float* __restrict__ color,
     float* __restrict__ depth, float* __restrict__ alpha_out, float* __restrict__ t_final,
     int32_t* __restrict__ last_index, Counters* __restrict__ counters) {
+  chain_wait_release();
   constexpr int kThreads = TW * TH / PPT;
   constexpr bool kPacked = PPT % 2 == 0;
   constexpr int P2 = kPacked ? PPT / 2 : 1;
@@ -495,6 +500,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     const float* __restrict__ t_final, const int32_t* __restrict__ last_index,
     const float* __restrict__ d_color, const float* __restrict__ d_depth,
     const float* __restrict__ d_alpha, float* __restrict__ g2d) {
+  chain_wait_release();
   constexpr int kThreads = TW * TH / PPT;
   constexpr bool kPacked = PPT % 2 == 0;
   constexpr int P2 = kPacked ? PPT / 2 : 1;
@@ -712,17 +718,19 @@ cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
                             float* g2d, Counters* counters, cudaStream_t stream) {
   if (views.total_tiles == 0) return cudaSuccess;
   constexpr int kThreads = TW * TH / PPT;
+  cudaError_t e;
   if (forward) {
-    blend_forward_kernel<TW, TH, PPT><<<views.total_tiles, kThreads, 0, stream>>>(
-        views, c, ranges, pair_vals, rec0, rec1, rec2, color, depth, alpha, t_final,
-        last_index, counters);
+    e = launch_chained(blend_forward_kernel<TW, TH, PPT>, dim3(views.total_tiles), dim3(kThreads),
+                       stream, views, c, ranges, pair_vals, rec0, rec1, rec2, color, depth, alpha,
+                       t_final, last_index, counters);
   } else {
-    blend_backward_kernel<TW, TH, PPT><<<views.total_tiles, kThreads, 0, stream>>>(
-        views, c, ranges, pair_vals, rec0, rec1, rec2, t_final, last_index, d_color, d_depth,
-        d_alpha, g2d);
+    e = launch_chained(blend_backward_kernel<TW, TH, PPT>, dim3(views.total_tiles),
+                       dim3(kThreads), stream, views, c, ranges, pair_vals, rec0, rec1, rec2,
+                       (const float*)t_final, (const int32_t*)last_index, d_color, d_depth,
+                       d_alpha, g2d);
   }
   RGS_LAUNCHED();
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace
@@ -737,33 +745,37 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
   if (visible_cap > 0) {
     const int64_t need = (visible_cap + kDupThreads - 1) / kDupThreads;
     const unsigned blocks = (unsigned)std::min<int64_t>(need, 8 * 152);
-    duplicate_kernel<<<blocks, kDupThreads, 0, stream>>>(views, n, order, offsets, ntiles, rec0,
-                                                         rec1, log2_alpha_min, capacity, keys,
-                                                         vals, counters);
+    const cudaError_t e =
+        launch_chained(duplicate_kernel, dim3(blocks), dim3(kDupThreads), stream, views, n, order,
+                       offsets, ntiles, rec0, rec1, log2_alpha_min, capacity, keys, vals,
+                       counters);
     RGS_LAUNCHED();
+    if (e != cudaSuccess) return e;
   }
-  store_pair_count_kernel<<<1, 1, 0, stream>>>(counters, capacity);
+  const cudaError_t e =
+      launch_chained(store_pair_count_kernel, dim3(1), dim3(1), stream, counters, capacity);
   RGS_LAUNCHED();
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_clamp_visible(Counters* counters, uint32_t capacity, cudaStream_t stream) {
-  clamp_visible_kernel<<<1, 1, 0, stream>>>(counters, capacity);
+  const cudaError_t e =
+      launch_chained(clamp_visible_kernel, dim3(1), dim3(1), stream, counters, capacity);
   RGS_LAUNCHED();
-  return cudaGetLastError();
+  return e;
 }
 
+// `ranges` must hold zeros on entry (tiles without pairs keep [0, 0)).
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
                                int total_tiles, uint32_t capacity, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, stream);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   if (capacity > 0) {
     const uint32_t threads = (capacity + 3) / 4;
-    tile_ranges_kernel<<<(threads + 255) / 256, 256, 0, stream>>>(keys, counters,
-                                                                  (uint32_t)total_tiles, ranges);
+    e = launch_chained(tile_ranges_kernel, dim3((threads + 255) / 256), dim3(256), stream, keys,
+                       counters, (uint32_t)total_tiles, ranges);
     RGS_LAUNCHED();
   }
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, const uint2* ranges,

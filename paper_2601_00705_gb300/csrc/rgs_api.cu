@@ -642,6 +642,9 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   const uint64_t launches0 = launch_counter();
   s->fwd_timed = ctx->timing;
   RGS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), stream), "reset counters");
+  // Tiles without pairs keep the empty range [0, 0); the range kernel writes the others.
+  RGS_CUDA(cudaMemsetAsync(s->ranges, 0, sizeof(uint2) * (size_t)views.total_tiles, stream),
+           "reset tile ranges");
   RGS_CUDA(mark(ctx, *s, 0, stream, capturing), "event");
 
   // 1. Projection.

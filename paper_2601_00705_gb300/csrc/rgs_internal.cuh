@@ -76,6 +76,39 @@ struct Counters {
   unsigned long long n_contrib;  // of which composited (covering, before the stop)
 };
 
+// Programmatic dependent launch. Every kernel of the library is launched with programmatic
+// stream serialization allowed (launch_chained below), so it can be scheduled before the
+// previous kernel of the stream has been retired. In every block, before any early return or
+// any access to data of earlier kernels, it waits for the previous kernel to complete with its
+// memory visible. Since each kernel completes only after that wait, the previous kernel's
+// completion implies the completion of all earlier ones. Inside a captured graph the stream
+// order becomes a programmatic edge.
+// chain_wait_release() also lets the successor be scheduled as soon as every block of this
+// kernel has started, so a chain of short kernels is resident and waiting, each starting the
+// moment its predecessor completes; chain_wait() leaves that to this kernel's exit. The radix
+// sort passes use the latter: there, successors resident that early slowed the sort.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_wait_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                  cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Host-side count of kernels the library has launched on the calling thread.
 inline uint64_t& launch_counter() {
   static thread_local uint64_t count = 0;

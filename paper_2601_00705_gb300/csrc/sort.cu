@@ -63,6 +63,7 @@ template <typename Load>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load load, int64_t n_cap,
                                                                    const uint32_t* n_dev,
                                                                    uint32_t* block_sums) {
+  chain_wait_release();
   const uint32_t n = read_count(n_dev, n_cap);
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   uint32_t s = 0;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load load, in
 __global__ void __launch_bounds__(1024) scan_block_sums_kernel(uint32_t* block_sums,
                                                                int64_t n_blocks,
                                                                uint32_t* total) {
+  chain_wait_release();
   uint32_t carry = 0;
   for (int64_t base = 0; base < n_blocks; base += 1024 * 4) {
     uint32_t v[4];
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_downsweep_kernel(Load load,
                                                                       int64_t n_cap,
                                                                       const uint32_t* n_dev,
                                                                       const uint32_t* block_sums) {
+  chain_wait_release();
   const uint32_t n = read_count(n_dev, n_cap);
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   if (base >= n) return;
@@ -159,14 +162,17 @@ cudaError_t run_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_de
     if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
     return cudaSuccess;
   }
-  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, n_cap, n_dev, block_sums);
+  cudaError_t e = launch_chained(scan_reduce_kernel<Load>, dim3((unsigned)nb), dim3(kScanThreads),
+                                 stream, load, n_cap, n_dev, block_sums);
   RGS_LAUNCHED();
-  scan_block_sums_kernel<<<1, 1024, 0, stream>>>(block_sums, nb, total);
+  if (e == cudaSuccess)
+    e = launch_chained(scan_block_sums_kernel, dim3(1), dim3(1024), stream, block_sums, nb, total);
   RGS_LAUNCHED();
-  scan_downsweep_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
-                                                                   block_sums);
+  if (e == cudaSuccess)
+    e = launch_chained(scan_downsweep_kernel<Load, Store>, dim3((unsigned)nb), dim3(kScanThreads),
+                       stream, load, store, n_cap, n_dev, (const uint32_t*)block_sums);
   RGS_LAUNCHED();
-  return cudaGetLastError();
+  return e;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -187,7 +193,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
                                                                      const uint32_t* n_dev,
                                                                      int shift, uint32_t mask,
                                                                      uint32_t* hist,
-                                                                     int64_t n_blocks) {
+                                                                     int64_t n_blocks, int early) {
+  if (early) chain_wait_release(); else chain_wait();
   __shared__ uint32_t counts[kRadixBins];
   const uint32_t n = read_count(n_dev, n_cap);
   for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) counts[d] = 0;
@@ -206,7 +213,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
 }
 
 __global__ void __launch_bounds__(kSortThreads) radix_row_scan_kernel(uint32_t* hist,
-                                                                      int64_t n_blocks) {
+                                                                      int64_t n_blocks,
+                                                                      int early) {
+  if (early) chain_wait_release(); else chain_wait();
   const int d = blockIdx.x;
   uint32_t* row = hist + (int64_t)d * n_blocks;
   uint32_t carry = 0;
@@ -235,7 +244,8 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
     int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* hist,
-    int64_t n_blocks) {
+    int64_t n_blocks, int early) {
+  if (early) chain_wait_release(); else chain_wait();
   static_assert(kSortThreads == kRadixBins, "one thread per digit in the digit scans");
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kTile = kSortThreads * ITEMS;
@@ -329,6 +339,8 @@ cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, in
                   stream);
 }
 
+constexpr int64_t kEarlyReleaseMaxKeys = 1 << 15;
+
 template <int ITEMS>
 cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                          int64_t n_cap, const uint32_t* n_dev, int begin_bit, int end_bit,
@@ -340,18 +352,27 @@ cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
   const int passes = (bits + 7) / 8;
   const int per_pass = (bits + passes - 1) / passes;
   uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals ? vals_alt : nullptr;
+  // Small sorts are launch-latency bound: let each pass kernel schedule its successor as soon as
+  // it has started (see chain_wait_release). Larger ones measured faster without.
+  const int early = n_cap <= kEarlyReleaseMaxKeys ? 1 : 0;
   for (int p = 0; p < passes; ++p) {
     const int shift = begin_bit + p * per_pass;
     const int w = (shift + per_pass <= end_bit) ? per_pass : end_bit - shift;
     const uint32_t mask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
-    radix_upsweep_kernel<ITEMS><<<(unsigned)nb, kSortThreads, 0, stream>>>(kin, n_cap, n_dev,
-                                                                           shift, mask, hist, nb);
+    cudaError_t e = launch_chained(radix_upsweep_kernel<ITEMS>, dim3((unsigned)nb),
+                                   dim3(kSortThreads), stream, (const uint32_t*)kin, n_cap, n_dev,
+                                   shift, mask, hist, nb, early);
     RGS_LAUNCHED();
-    radix_row_scan_kernel<<<kRadixBins, kSortThreads, 0, stream>>>(hist, nb);
+    if (e == cudaSuccess)
+      e = launch_chained(radix_row_scan_kernel, dim3(kRadixBins), dim3(kSortThreads), stream,
+                         hist, nb, early);
     RGS_LAUNCHED();
-    radix_downsweep_kernel<ITEMS><<<(unsigned)nb, kSortThreads, 0, stream>>>(
-        kin, vin, kout, vout, n_cap, n_dev, shift, mask, hist, nb);
+    if (e == cudaSuccess)
+      e = launch_chained(radix_downsweep_kernel<ITEMS>, dim3((unsigned)nb), dim3(kSortThreads),
+                         stream, (const uint32_t*)kin, (const uint32_t*)vin, kout, vout, n_cap,
+                         n_dev, shift, mask, (const uint32_t*)hist, nb, early);
     RGS_LAUNCHED();
+    if (e != cudaSuccess) return e;
     uint32_t* t = kin;
     kin = kout;
     kout = t;
