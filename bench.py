@@ -419,18 +419,38 @@ def run_ours(args, world, rank, local):
         means=1, log_scales=2, quats=4, opacity_logits=8, sh=16, pose=32)[k])
     d2h += sum(t.numel() * 4 for t in img_host)
 
+    # The copies that do not feed the next kernel overlap with compute, on streams of their own:
+    # the upstream gradients travel during the forward, the images come back during the backward.
+    s_params, s_upstream, s_images = (torch.cuda.Stream(dev) for _ in range(3))
+
     def step_e2e(st):
-        p = [pin[k].to(dev, non_blocking=True)
-             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
-        uc = up_pin[0].to(dev, non_blocking=True)
-        ud = up_pin[1].to(dev, non_blocking=True) if wl.depth_weight else None
+        cur = torch.cuda.current_stream(dev)
+        for s_ in (s_params, s_upstream, s_images):
+            s_.wait_stream(cur)
+        with torch.cuda.stream(s_params):
+            p = [pin[k].to(dev, non_blocking=True)
+                 for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+        with torch.cuda.stream(s_upstream):
+            uc = up_pin[0].to(dev, non_blocking=True)
+            ud = up_pin[1].to(dev, non_blocking=True) if wl.depth_weight else None
+        cur.wait_stream(s_params)
+        for t in p:
+            t.record_stream(cur)
         c, d, a, st = r.forward_raw(*p, cams, state=st)
+        s_images.wait_stream(cur)
+        with torch.cuda.stream(s_images):
+            for hbuf, dbuf in zip(img_host, (c, d, a)):
+                dbuf.record_stream(s_images)
+                hbuf.copy_(dbuf, non_blocking=True)
+        cur.wait_stream(s_upstream)
+        for t in (uc, ud):
+            if t is not None:
+                t.record_stream(cur)
         gr = r.backward_raw(st, n, K, V, uc, ud, None, mask)
         for k, t in gr.items():
             if t is not None:
                 out_host[k].copy_(t, non_blocking=True)
-        for hbuf, dbuf in zip(img_host, (c, d, a)):
-            hbuf.copy_(dbuf, non_blocking=True)
+        cur.wait_stream(s_images)
         return st
 
     e2e_state = step_e2e(0)
