@@ -16,6 +16,7 @@ namespace rgs {
 namespace {
 
 constexpr int kPreThreads = 128;
+constexpr int kCullMaxViewsPerThread = 8;  // views one cull thread takes (its candidate buffer)
 
 // Real spherical harmonics of a unit direction, degree <= DEG (basis index l*l + l + m).
 // Y_{l,m} = sqrt(2) Re / Im of the complex harmonic with the Condon-Shortley phase, as
@@ -282,15 +283,20 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, flo
 
 // Forward, pass 1 (cull): one thread per (Gaussian, chunk of views). Only the camera-space mean,
 // the projected centre and the footprint-radius bound of project_view are computed; every entry
-// gets ntiles = 0, and the entries that may touch the image are appended to `cand` (warp-
-// aggregated atomics; their order does not matter). Pass 2 then projects only those, so its
-// warps are not held up by the large majority of entries that fall outside the image.
+// gets ntiles = 0, and the entries that may touch the image are appended to `cand` (gathered in
+// shared memory, then one global atomic per block; their order does not matter). Pass 2 then
+// projects only those, so its warps are not held up by the large majority of entries that fall
+// outside the image.
 __global__ void __launch_bounds__(kPreThreads) cull_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ cand,
     Counters* __restrict__ counters, int views_per_chunk) {
   chain_wait_release();
+  __shared__ uint32_t s_cand[kPreThreads * kCullMaxViewsPerThread];
+  __shared__ uint32_t s_count, s_base;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   const bool in_range = i < n;
   const int lane = threadIdx.x & 31;
@@ -357,11 +363,15 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
     if (ballot) {
       const int leader = __ffs(ballot) - 1;
       uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(&counters->n_candidates, (uint32_t)__popc(ballot));
+      if (lane == leader) base = atomicAdd(&s_count, (uint32_t)__popc(ballot));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (keep) cand[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)vi;
+      if (keep) s_cand[base + __popc(ballot & ((1u << lane) - 1u))] = (uint32_t)vi;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) s_base = s_count ? atomicAdd(&counters->n_candidates, s_count) : 0u;
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < s_count; t += kPreThreads) cand[s_base + t] = s_cand[t];
 }
 
 // Forward, pass 2 (project): one thread per candidate entry (grid-stride). Full projection
@@ -803,7 +813,8 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   // times over.
   const int blocks_x = (g.n + kPreThreads - 1) / kPreThreads;
   const int target_blocks = 8 * 152;
-  const int chunks = max(1, min(views.n_views, (target_blocks + blocks_x - 1) / blocks_x));
+  const int chunks = max((views.n_views + kCullMaxViewsPerThread - 1) / kCullMaxViewsPerThread,
+                         min(views.n_views, (target_blocks + blocks_x - 1) / blocks_x));
   const int per_chunk = (views.n_views + chunks - 1) / chunks;
   const dim3 grid((unsigned)blocks_x, (unsigned)((views.n_views + per_chunk - 1) / per_chunk));
   cudaError_t e = launch_chained(cull_kernel, grid, dim3(kPreThreads), stream, views, c, g.n,
