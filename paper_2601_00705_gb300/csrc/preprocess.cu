@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ cand,
     Counters* __restrict__ counters, int views_per_chunk) {
-  chain_wait_release();
+  chain_wait();
   __shared__ uint32_t s_cand[kPreThreads * kCullMaxViewsPerThread];
   __shared__ uint32_t s_count, s_base;
   if (threadIdx.x == 0) s_count = 0;
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const float* __restrict__ logits, const float* __restrict__ sh,
     const uint32_t* __restrict__ cand, float4* __restrict__ rec0, float4* __restrict__ rec1,
     float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, Counters* __restrict__ counters) {
-  chain_wait_release();
+  chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t n_cand = counters->n_candidates;
   for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_cand;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const uint32_t* __restrict__ order, const Counters* __restrict__ counters,
     float* __restrict__ g2d, unsigned long long* __restrict__ vis_mask, uint32_t grad_mask,
     float* __restrict__ pose_partial) {
-  chain_wait_release();
+  chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ float s_pose[kMaxViews * 6];
   const int nv = views.n_views;
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ d_means,
     float* __restrict__ d_log_scales, float* __restrict__ d_quats, float* __restrict__ d_logits,
     float* __restrict__ d_sh) {
-  chain_wait_release();
+  chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   if (i >= n) return;
@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
 // d_pose[v,k] = sum over blocks of the partials, in double precision.
 __global__ void pose_finalize_kernel(const float* __restrict__ partial, int n_blocks,
                                      int n_views, float* __restrict__ d_pose) {
-  chain_wait_release();
+  chain_wait();
   const int vk = blockIdx.x;  // v * 6 + k
   double s = 0.0;
   for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += (double)partial[(size_t)b * n_views * 6 + vk];

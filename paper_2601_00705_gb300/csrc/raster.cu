@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const float4* __restrict__ rec0, const float4* __restrict__ rec1, float log2_alpha_min,
     uint32_t capacity, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
     Counters* __restrict__ counters) {
-  chain_wait_release();
+  chain_wait();
   __shared__ uint32_t s_stage[kDupWarps][kDupStage];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* stage = s_stage[warp];
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
 // Keeps at most `capacity` visible entries (the sorted-list capacity under stream capture): the
 // entries beyond it are dropped from this forward and the overflow is recorded.
 __global__ void clamp_visible_kernel(Counters* counters, uint32_t capacity) {
-  chain_wait_release();
+  chain_wait();
   if (counters->n_visible > capacity) {
     counters->n_visible = capacity;
     counters->status |= kStatusVisibleOverflow;
@@ -182,7 +182,7 @@ __global__ void clamp_visible_kernel(Counters* counters, uint32_t capacity) {
 }
 
 __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
-  chain_wait_release();
+  chain_wait();
   const uint32_t p = counters->n_pairs;
   counters->n_pairs_stored = p < capacity ? p : capacity;
 }
@@ -192,7 +192,7 @@ __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys,
                                    const Counters* __restrict__ counters, uint32_t total_tiles,
                                    uint2* __restrict__ ranges) {
-  chain_wait_release();
+  chain_wait();
   const uint32_t n = counters->n_pairs_stored;
   const uint32_t p0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
   if (p0 >= n) return;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     const float4* __restrict__ rec1, const float4* __restrict__ rec2, float* __restrict__ color,
     float* __restrict__ depth, float* __restrict__ alpha_out, float* __restrict__ t_final,
     int32_t* __restrict__ last_index, Counters* __restrict__ counters) {
-  chain_wait_release();
+  chain_wait();
   constexpr int kThreads = TW * TH / PPT;
   constexpr bool kPacked = PPT % 2 == 0;
   constexpr int P2 = kPacked ? PPT / 2 : 1;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     const float* __restrict__ t_final, const int32_t* __restrict__ last_index,
     const float* __restrict__ d_color, const float* __restrict__ d_depth,
     const float* __restrict__ d_alpha, float* __restrict__ g2d) {
-  chain_wait_release();
+  chain_wait();
   constexpr int kThreads = TW * TH / PPT;
   constexpr bool kPacked = PPT % 2 == 0;
   constexpr int P2 = kPacked ? PPT / 2 : 1;
@@ -614,12 +614,12 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
             const bool cov0 = jj <= last[k0] && a0 >= c.alpha_min;
             const bool cov1 = jj <= last[k1] && a1 >= c.alpha_min;
             contrib = contrib || cov0 || cov1;
-            // A pixel this Gaussian does not cover gets alpha 0 and 1 / (1 - alpha) = 1, so its
-            // transmittance, suffix sum and every accumulator stay bit-identical.
+            // A pixel this Gaussian does not cover gets alpha 0 and 1 / (1 - alpha) = 1 (the
+            // hardware reciprocal of 1 is exactly 1 on sm_103a, measured), so its transmittance,
+            // suffix sum and every accumulator stay bit-identical.
             const f32x2 am = f2_make(cov0 ? a0 : 0.0f, cov1 ? a1 : 0.0f);
             const f32x2 om = f2_sub(ONE2, am);
-            const f32x2 rom = f2_make(cov0 ? rcp_approx(f2_lo(om)) : 1.0f,
-                                      cov1 ? rcp_approx(f2_hi(om)) : 1.0f);
+            const f32x2 rom = f2_make(rcp_approx(f2_lo(om)), rcp_approx(f2_hi(om)));
             T2[q] = f2_mul(T2[q], rom);  // transmittance in front of this Gaussian
             const f32x2 w = f2_mul(am, T2[q]);
             aR = f2_fma(GC02[q], w, aR);

@@ -77,21 +77,15 @@ struct Counters {
 };
 
 // Programmatic dependent launch. Every kernel of the library is launched with programmatic
-// stream serialization allowed (launch_chained below), so it can be scheduled before the
-// previous kernel of the stream has been retired. In every block, before any early return or
-// any access to data of earlier kernels, it waits for the previous kernel to complete with its
-// memory visible. Since each kernel completes only after that wait, the previous kernel's
-// completion implies the completion of all earlier ones. Inside a captured graph the stream
-// order becomes a programmatic edge.
-// chain_wait_release() also lets the successor be scheduled as soon as every block of this
-// kernel has started, so a chain of short kernels is resident and waiting, each starting the
-// moment its predecessor completes; chain_wait() leaves that to this kernel's exit. The radix
-// sort passes use the latter: there, successors resident that early slowed the sort.
+// stream serialization allowed (launch_chained below): once every block of the previous kernel
+// of the stream has exited, the next kernel is scheduled without waiting for the previous grid
+// to be retired. In every block, before any early return or any access to data of earlier
+// kernels, it waits for the previous kernel to complete with its memory visible. Since each
+// kernel completes only after that wait, the previous kernel's completion implies the completion
+// of all earlier ones. No kernel lets its successor start before its own blocks have exited:
+// with successors scheduled as soon as their predecessor had started, a long chain of short
+// kernels captured in a graph replayed wrong results.
 __device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void chain_wait_release() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block,

@@ -63,7 +63,7 @@ template <typename Load>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load load, int64_t n_cap,
                                                                    const uint32_t* n_dev,
                                                                    uint32_t* block_sums) {
-  chain_wait_release();
+  chain_wait();
   const uint32_t n = read_count(n_dev, n_cap);
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   uint32_t s = 0;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load load, in
 __global__ void __launch_bounds__(1024) scan_block_sums_kernel(uint32_t* block_sums,
                                                                int64_t n_blocks,
                                                                uint32_t* total) {
-  chain_wait_release();
+  chain_wait();
   uint32_t carry = 0;
   for (int64_t base = 0; base < n_blocks; base += 1024 * 4) {
     uint32_t v[4];
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_downsweep_kernel(Load load,
                                                                       int64_t n_cap,
                                                                       const uint32_t* n_dev,
                                                                       const uint32_t* block_sums) {
-  chain_wait_release();
+  chain_wait();
   const uint32_t n = read_count(n_dev, n_cap);
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   if (base >= n) return;
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
                                                                      const uint32_t* n_dev,
                                                                      int shift, uint32_t mask,
                                                                      uint32_t* hist,
-                                                                     int64_t n_blocks, int early) {
-  if (early) chain_wait_release(); else chain_wait();
+                                                                     int64_t n_blocks) {
+  chain_wait();
   __shared__ uint32_t counts[kRadixBins];
   const uint32_t n = read_count(n_dev, n_cap);
   for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) counts[d] = 0;
@@ -213,9 +213,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint3
 }
 
 __global__ void __launch_bounds__(kSortThreads) radix_row_scan_kernel(uint32_t* hist,
-                                                                      int64_t n_blocks,
-                                                                      int early) {
-  if (early) chain_wait_release(); else chain_wait();
+                                                                      int64_t n_blocks) {
+  chain_wait();
   const int d = blockIdx.x;
   uint32_t* row = hist + (int64_t)d * n_blocks;
   uint32_t carry = 0;
@@ -244,8 +243,8 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
     int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* hist,
-    int64_t n_blocks, int early) {
-  if (early) chain_wait_release(); else chain_wait();
+    int64_t n_blocks) {
+  chain_wait();
   static_assert(kSortThreads == kRadixBins, "one thread per digit in the digit scans");
   constexpr int kWarps = kSortThreads / 32;
   constexpr int kTile = kSortThreads * ITEMS;
@@ -339,8 +338,6 @@ cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, in
                   stream);
 }
 
-constexpr int64_t kEarlyReleaseMaxKeys = 1 << 15;
-
 template <int ITEMS>
 cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                          int64_t n_cap, const uint32_t* n_dev, int begin_bit, int end_bit,
@@ -352,25 +349,22 @@ cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
   const int passes = (bits + 7) / 8;
   const int per_pass = (bits + passes - 1) / passes;
   uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals ? vals_alt : nullptr;
-  // Small sorts are launch-latency bound: let each pass kernel schedule its successor as soon as
-  // it has started (see chain_wait_release). Larger ones measured faster without.
-  const int early = n_cap <= kEarlyReleaseMaxKeys ? 1 : 0;
   for (int p = 0; p < passes; ++p) {
     const int shift = begin_bit + p * per_pass;
     const int w = (shift + per_pass <= end_bit) ? per_pass : end_bit - shift;
     const uint32_t mask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
     cudaError_t e = launch_chained(radix_upsweep_kernel<ITEMS>, dim3((unsigned)nb),
                                    dim3(kSortThreads), stream, (const uint32_t*)kin, n_cap, n_dev,
-                                   shift, mask, hist, nb, early);
+                                   shift, mask, hist, nb);
     RGS_LAUNCHED();
     if (e == cudaSuccess)
       e = launch_chained(radix_row_scan_kernel, dim3(kRadixBins), dim3(kSortThreads), stream,
-                         hist, nb, early);
+                         hist, nb);
     RGS_LAUNCHED();
     if (e == cudaSuccess)
       e = launch_chained(radix_downsweep_kernel<ITEMS>, dim3((unsigned)nb), dim3(kSortThreads),
                          stream, (const uint32_t*)kin, (const uint32_t*)vin, kout, vout, n_cap,
-                         n_dev, shift, mask, (const uint32_t*)hist, nb, early);
+                         n_dev, shift, mask, (const uint32_t*)hist, nb);
     RGS_LAUNCHED();
     if (e != cudaSuccess) return e;
     uint32_t* t = kin;
