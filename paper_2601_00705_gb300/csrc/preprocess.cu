@@ -500,14 +500,21 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const float4 ga = *reinterpret_cast<const float4*>(gp);
     const float4 gb = *reinterpret_cast<const float4*>(gp + 4);
     const float2 gc2 = *reinterpret_cast<const float2*>(gp + 8);
-    const float g_mx = ga.x, g_my = ga.y, g_ca = ga.z, g_cb = ga.w;
-    const float g_cc = gb.x, g_op = gb.y, g_r = gb.z, g_g = gb.w;
+    const float m0 = ga.x, mx = ga.y, mxx = ga.z, my = ga.w;
+    const float mxy = gb.x, myy = gb.y, g_r = gb.z, g_g = gb.w;
     const float g_b = gc2.x, g_zo = gc2.y;
     ViewProj p;
     project_view(g, vp, c, p);
     const float* R = vp.R;
-    // Conic -> Sigma^I: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]].
     const float a = p.conic[0], b = p.conic[1], cc = p.conic[2];
+    // Screen-space gradients from the blend's moments: power = -1/2 (a dx^2 + 2 b dx dy +
+    // c dy^2) with (dx, dy) = p - mu^I, alpha = o exp(power) (Section 3.1, Eq. alpha), so
+    // dpower/dmu^I = (a dx + b dy, b dx + c dy), dpower/d(a, b, c) = -(dx^2 / 2, dx dy, dy^2 / 2)
+    // and d alpha / d o = alpha / o.
+    const float g_mx = fmaf(a, mx, b * my), g_my = fmaf(b, mx, cc * my);
+    const float g_ca = -0.5f * mxx, g_cb = -mxy, g_cc = -0.5f * myy;
+    const float g_op = m0 / g.opacity;
+    // Conic -> Sigma^I: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]].
     const float hb = 0.5f * g_cb;
     const float P00 = a * g_ca + b * hb, P01 = a * hb + b * g_cc;
     const float P10 = b * g_ca + cc * hb, P11 = b * hb + cc * g_cc;

@@ -8,6 +8,7 @@
 // stored; per-Gaussian screen-space gradients are reduced across the warp before one atomic per
 // value and warp.
 #include <algorithm>
+#include <type_traits>
 
 #include "rgs_internal.cuh"
 
@@ -492,7 +493,10 @@ __device__ __forceinline__ int reduced_slot(int lane) {
 // ------------------------------------------------------------------------------------------
 // Backward blend (same pixel layout as the forward).
 // ------------------------------------------------------------------------------------------
-template <int TW, int TH, int PPT>
+// kAux: a depth or accumulated-opacity upstream gradient is present. Without one (a colour-only
+// loss) the per-pixel depth / opacity gradient state and its arithmetic drop out; the results
+// are those of the general kernel with those gradients zero.
+template <int TW, int TH, int PPT, bool kAux>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     const __grid_constant__ Views views, const Consts c, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ pair_vals, const float4* __restrict__ rec0,
@@ -542,8 +546,8 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
         gC1[k] = d_color[3 * pix + 1];
         gC2[k] = d_color[3 * pix + 2];
       }
-      if (d_depth) gD[k] = d_depth[pix];
-      if (d_alpha) gAT[k] = d_alpha[pix] * Tfin;
+      if (kAux && d_depth) gD[k] = d_depth[pix];
+      if (kAux && d_alpha) gAT[k] = d_alpha[pix] * Tfin;
     }
     T[k] = Tfin;
     U[k] = Tfin * (gC0[k] * c.bg[0] + gC1[k] * c.bg[1] + gC2[k] * c.bg[2]);
@@ -569,11 +573,143 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) s_max_last[threadIdx.x >> 5] = m;
+  // At or below the smallest last-contributor index of the warp every pixel of the warp is
+  // live, and the per-pixel test of the list position drops out (warp-uniform).
+  int thread_min_last = last[0];
+#pragma unroll
+  for (int k = 1; k < PPT; ++k) thread_min_last = min(thread_min_last, last[k]);
+  const int warp_min_last = __reduce_min_sync(0xffffffffu, thread_min_last);
   __syncthreads();
   int max_last = -1;
 #pragma unroll
   for (int w = 0; w < kThreads / 32; ++w) max_last = max(max_last, s_max_last[w]);
   if (max_last < (int)range.x) return;
+
+  // One Gaussian (list position jj, staged at g) against the thread's pixels; kCheckLast tests
+  // each pixel's last-contributor index.
+  auto visit = [&](int jj, int g, auto check_last) {
+    constexpr bool kCheckLast = decltype(check_last)::value;
+    float acc[10];
+#pragma unroll
+    for (int s2 = 0; s2 < 10; ++s2) acc[s2] = 0.0f;
+    bool contrib = false;
+    if (!kCheckLast || jj <= thread_last) {
+      // Per-thread moments of dL/dpower over the thread's pixels (all share dx):
+      // sdp = sum dp, sdy = sum dp dy, sdy2 = sum dp dy^2.
+      float sdp = 0.0f, sdy = 0.0f, sdy2 = 0.0f, dx;
+      if constexpr (kPacked) {
+        const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
+        const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
+        const f32x2 dx2 = f2_sub(f2_sub(FX, X.x), X.y);
+        const f32x2 AA = f2_fma(f2_mul(Q1.x, dx2), dx2, Q2.y);
+        const f32x2 BB = f2_mul(Q1.y, dx2);
+        f32x2 aR = ZERO2, aG = ZERO2, aB = ZERO2, aZ = ZERO2, mP = ZERO2, mY = ZERO2,
+              mYY = ZERO2;
+        (void)aZ;
+#pragma unroll
+        for (int q = 0; q < P2; ++q) {
+          const int k0 = 2 * q, k1 = 2 * q + 1;
+          const f32x2 dy = f2_sub(f2_sub(FY[q], Y.x), Y.y);
+          const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
+          const float oG0 = ex2_approx(f2_lo(pw)), oG1 = ex2_approx(f2_hi(pw));
+          const float a0 = fminf(c.alpha_max, oG0), a1 = fminf(c.alpha_max, oG1);
+          const bool cov0 = (!kCheckLast || jj <= last[k0]) && a0 >= c.alpha_min;
+          const bool cov1 = (!kCheckLast || jj <= last[k1]) && a1 >= c.alpha_min;
+          contrib = contrib || cov0 || cov1;
+          // A pixel this Gaussian does not cover gets alpha 0 and 1 / (1 - alpha) = 1 (the
+          // hardware reciprocal of 1 is exactly 1 on sm_103a, measured), so its transmittance,
+          // suffix sum and every accumulator stay bit-identical.
+          const f32x2 am = f2_make(cov0 ? a0 : 0.0f, cov1 ? a1 : 0.0f);
+          const f32x2 om = f2_sub(ONE2, am);
+          const f32x2 rom = f2_make(rcp_approx(f2_lo(om)), rcp_approx(f2_hi(om)));
+          T2[q] = f2_mul(T2[q], rom);  // transmittance in front of this Gaussian
+          const f32x2 w = f2_mul(am, T2[q]);
+          aR = f2_fma(GC02[q], w, aR);
+          aG = f2_fma(GC12[q], w, aG);
+          aB = f2_fma(GC22[q], w, aB);
+          f32x2 qv, dLda;
+          if constexpr (kAux) {
+            aZ = f2_fma(GD2[q], w, aZ);
+            qv = f2_fma(GC02[q], CA.x,
+                        f2_fma(GC12[q], CA.y, f2_fma(GC22[q], CB.x, f2_mul(GD2[q], CB.y))));
+            dLda = f2_fma(T2[q], qv, f2_mul(rom, f2_sub(GAT2[q], U2[q])));
+          } else {
+            qv = f2_fma(GC02[q], CA.x, f2_fma(GC12[q], CA.y, f2_mul(GC22[q], CB.x)));
+            dLda = f2_fma(T2[q], qv, f2_mul(rom, f2_sub(ZERO2, U2[q])));
+          }
+          U2[q] = f2_fma(w, qv, U2[q]);
+          // dL/dpower = dL/dalpha * alpha (d alpha / d power = o G = alpha), unclamped only.
+          const f32x2 dpv = f2_mul(dLda, am);
+          const bool m0 = cov0 && oG0 < c.alpha_max, m1 = cov1 && oG1 < c.alpha_max;
+          const f32x2 dp = f2_make(m0 ? f2_lo(dpv) : 0.0f, m1 ? f2_hi(dpv) : 0.0f);
+          mP = f2_add(mP, dp);
+          const f32x2 t = f2_mul(dp, dy);
+          mY = f2_add(mY, t);
+          mYY = f2_fma(t, dy, mYY);
+        }
+        acc[kGR] = f2_lo(aR) + f2_hi(aR);
+        acc[kGG] = f2_lo(aG) + f2_hi(aG);
+        acc[kGB] = f2_lo(aB) + f2_hi(aB);
+        if constexpr (kAux) acc[kGZ] = f2_lo(aZ) + f2_hi(aZ);
+        sdp = f2_lo(mP) + f2_hi(mP);
+        sdy = f2_lo(mY) + f2_hi(mY);
+        sdy2 = f2_lo(mYY) + f2_hi(mYY);
+        dx = f2_lo(dx2);
+      } else {
+        const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
+        const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
+        const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
+        dx = __fsub_rn(__fsub_rn(fx, g0.x), g0.z);
+        const float qc = g1.z;
+        const ColumnTerms ct = column_terms(dx, g1.x, g1.y, g1.w);
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (kCheckLast && jj > last[k]) continue;
+          const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
+          const float oG = opacity_times_gauss(ct, qc, dy);
+          const float a = fminf(c.alpha_max, oG);
+          if (a < c.alpha_min) continue;
+          contrib = true;
+          const float rom = rcp_approx(__fsub_rn(1.0f, a));
+          T[k] = T[k] * rom;  // transmittance in front of this Gaussian
+          const float w = a * T[k];
+          acc[kGR] = fmaf(gC0[k], w, acc[kGR]);
+          acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
+          acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
+          float q, dLda;
+          if constexpr (kAux) {
+            acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
+            q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g2.w)));
+            dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
+          } else {
+            q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, gC2[k] * g2.z));
+            dLda = fmaf(T[k], q, rom * (0.0f - U[k]));
+          }
+          U[k] = fmaf(w, q, U[k]);
+          if (oG < c.alpha_max) {
+            const float dp = dLda * a;  // dL/dpower: d alpha / d power = o G = alpha
+            sdp += dp;
+            const float t = dp * dy;
+            sdy += t;
+            sdy2 = fmaf(t, dy, sdy2);
+          }
+        }
+      }
+      // The thread's share of the moments (all its pixels have the same dx); zero when it
+      // covers nothing.
+      acc[kM0] = sdp;
+      acc[kMx] = dx * sdp;
+      acc[kMxx] = dx * acc[kMx];
+      acc[kMy] = sdy;
+      acc[kMxy] = dx * sdy;
+      acc[kMyy] = sdy2;
+    }
+    if (__any_sync(0xffffffffu, contrib)) {
+      const float total = transpose_reduce10(acc, lane);
+      if (slot >= 0 && (lane & 1) == 0)
+        atomicAdd(g2d + (size_t)s_vi[g] * kG2Stride + slot, total);
+    }
+  };
 
   const int first = (int)range.x;
   for (int bend = max_last + 1; bend > first; bend -= kThreads) {
@@ -586,126 +722,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
       stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi]);
     }
     __syncthreads();
-    for (int jj = bend - 1; jj >= bstart; --jj) {
-      const int g = jj - bstart;
-      float acc[10];
-#pragma unroll
-      for (int s2 = 0; s2 < 10; ++s2) acc[s2] = 0.0f;
-      bool contrib = false;
-      if (jj <= thread_last) {
-        // Per-thread moments of dL/dpower over the thread's pixels (all share dx):
-        // sdp = sum dp, sdy = sum dp dy, sdy2 = sum dp dy^2.
-        float sdp = 0.0f, sdy = 0.0f, sdy2 = 0.0f, dx, qa, qb, qc, lo;
-        if constexpr (kPacked) {
-          const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
-          const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
-          const f32x2 dx2 = f2_sub(f2_sub(FX, X.x), X.y);
-          const f32x2 AA = f2_fma(f2_mul(Q1.x, dx2), dx2, Q2.y);
-          const f32x2 BB = f2_mul(Q1.y, dx2);
-          f32x2 aR = ZERO2, aG = ZERO2, aB = ZERO2, aZ = ZERO2, mP = ZERO2, mY = ZERO2,
-                mYY = ZERO2;
-#pragma unroll
-          for (int q = 0; q < P2; ++q) {
-            const int k0 = 2 * q, k1 = 2 * q + 1;
-            const f32x2 dy = f2_sub(f2_sub(FY[q], Y.x), Y.y);
-            const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
-            const float oG0 = ex2_approx(f2_lo(pw)), oG1 = ex2_approx(f2_hi(pw));
-            const float a0 = fminf(c.alpha_max, oG0), a1 = fminf(c.alpha_max, oG1);
-            const bool cov0 = jj <= last[k0] && a0 >= c.alpha_min;
-            const bool cov1 = jj <= last[k1] && a1 >= c.alpha_min;
-            contrib = contrib || cov0 || cov1;
-            // A pixel this Gaussian does not cover gets alpha 0 and 1 / (1 - alpha) = 1 (the
-            // hardware reciprocal of 1 is exactly 1 on sm_103a, measured), so its transmittance,
-            // suffix sum and every accumulator stay bit-identical.
-            const f32x2 am = f2_make(cov0 ? a0 : 0.0f, cov1 ? a1 : 0.0f);
-            const f32x2 om = f2_sub(ONE2, am);
-            const f32x2 rom = f2_make(rcp_approx(f2_lo(om)), rcp_approx(f2_hi(om)));
-            T2[q] = f2_mul(T2[q], rom);  // transmittance in front of this Gaussian
-            const f32x2 w = f2_mul(am, T2[q]);
-            aR = f2_fma(GC02[q], w, aR);
-            aG = f2_fma(GC12[q], w, aG);
-            aB = f2_fma(GC22[q], w, aB);
-            aZ = f2_fma(GD2[q], w, aZ);
-            const f32x2 qv =
-                f2_fma(GC02[q], CA.x, f2_fma(GC12[q], CA.y, f2_fma(GC22[q], CB.x, f2_mul(GD2[q], CB.y))));
-            const f32x2 dLda = f2_fma(T2[q], qv, f2_mul(rom, f2_sub(GAT2[q], U2[q])));
-            U2[q] = f2_fma(w, qv, U2[q]);
-            // dL/dpower = dL/dalpha * alpha (d alpha / d power = o G = alpha), unclamped only.
-            const f32x2 dpv = f2_mul(dLda, am);
-            const bool m0 = cov0 && oG0 < c.alpha_max, m1 = cov1 && oG1 < c.alpha_max;
-            const f32x2 dp = f2_make(m0 ? f2_lo(dpv) : 0.0f, m1 ? f2_hi(dpv) : 0.0f);
-            mP = f2_add(mP, dp);
-            const f32x2 t = f2_mul(dp, dy);
-            mY = f2_add(mY, t);
-            mYY = f2_fma(t, dy, mYY);
-          }
-          acc[kGR] = f2_lo(aR) + f2_hi(aR);
-          acc[kGG] = f2_lo(aG) + f2_hi(aG);
-          acc[kGB] = f2_lo(aB) + f2_hi(aB);
-          acc[kGZ] = f2_lo(aZ) + f2_hi(aZ);
-          sdp = f2_lo(mP) + f2_hi(mP);
-          sdy = f2_lo(mY) + f2_hi(mY);
-          sdy2 = f2_lo(mYY) + f2_hi(mYY);
-          dx = f2_lo(dx2);
-          qa = f2_lo(Q1.x);
-          qb = f2_lo(Q1.y);
-          qc = f2_lo(Q2.x);
-          lo = f2_lo(Q2.y);
-        } else {
-          const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
-          const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
-          const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
-          dx = __fsub_rn(__fsub_rn(fx, g0.x), g0.z);
-          qa = g1.x;
-          qb = g1.y;
-          qc = g1.z;
-          lo = g1.w;
-          const ColumnTerms ct = column_terms(dx, qa, qb, lo);
-#pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            if (jj > last[k]) continue;
-            const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
-            const float oG = opacity_times_gauss(ct, qc, dy);
-            const float a = fminf(c.alpha_max, oG);
-            if (a < c.alpha_min) continue;
-            contrib = true;
-            const float rom = rcp_approx(__fsub_rn(1.0f, a));
-            T[k] = T[k] * rom;  // transmittance in front of this Gaussian
-            const float w = a * T[k];
-            acc[kGR] = fmaf(gC0[k], w, acc[kGR]);
-            acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
-            acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
-            acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
-            const float q =
-                fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g2.w)));
-            const float dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
-            U[k] = fmaf(w, q, U[k]);
-            if (oG < c.alpha_max) {
-              const float dp = dLda * a;  // dL/dpower: d alpha / d power = o G = alpha
-              sdp += dp;
-              const float t = dp * dy;
-              sdy += t;
-              sdy2 = fmaf(t, dy, sdy2);
-            }
-          }
-        }
-        if (contrib) {
-          // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), d = p - mu^I, alpha = o exp(power).
-          const float ca = qa * (-2.0f * kLn2), cb = qb * (-kLn2), cc = qc * (-2.0f * kLn2);
-          acc[kGOp] = sdp * ex2_approx(-lo);  // d alpha / d o = G = alpha / o, 1/o = 2^-log2 o
-          acc[kGMx] = fmaf(ca * dx, sdp, cb * sdy);
-          acc[kGMy] = fmaf(cb * dx, sdp, cc * sdy);
-          acc[kGCa] = -0.5f * dx * dx * sdp;
-          acc[kGCb] = -dx * sdy;
-          acc[kGCc] = -0.5f * sdy2;
-        }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-        const float total = transpose_reduce10(acc, lane);
-        if (slot >= 0 && (lane & 1) == 0)
-          atomicAdd(g2d + (size_t)s_vi[g] * kG2Stride + slot, total);
-      }
-    }
+    // Positions above the warp's smallest last index test each pixel; the rest do not.
+    const int split = max(bstart - 1, min(bend - 1, warp_min_last));
+    for (int jj = bend - 1; jj > split; --jj) visit(jj, jj - bstart, std::true_type{});
+    for (int jj = split; jj >= bstart; --jj) visit(jj, jj - bstart, std::false_type{});
   }
 }
 
@@ -724,10 +744,12 @@ cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
                        stream, views, c, ranges, pair_vals, rec0, rec1, rec2, color, depth, alpha,
                        t_final, last_index, counters);
   } else {
-    e = launch_chained(blend_backward_kernel<TW, TH, PPT>, dim3(views.total_tiles),
-                       dim3(kThreads), stream, views, c, ranges, pair_vals, rec0, rec1, rec2,
-                       (const float*)t_final, (const int32_t*)last_index, d_color, d_depth,
-                       d_alpha, g2d);
+    const bool aux = d_depth != nullptr || d_alpha != nullptr;
+    e = launch_chained(aux ? blend_backward_kernel<TW, TH, PPT, true>
+                           : blend_backward_kernel<TW, TH, PPT, false>,
+                       dim3(views.total_tiles), dim3(kThreads), stream, views, c, ranges,
+                       pair_vals, rec0, rec1, rec2, (const float*)t_final,
+                       (const int32_t*)last_index, d_color, d_depth, d_alpha, g2d);
   }
   RGS_LAUNCHED();
   return e;

@@ -7,8 +7,9 @@
 //   rec1[vi] = (qa, qb, qc, log2 o)                        float4, base-2 conic (see below)
 //   rec2[vi] = (r, g, b, depth z)                          float4
 //   ntiles[vi]: tiles touched (0 = culled / invisible)
-//   g2d[vi * 16 + s]: screen-space gradient slots (mean2d x/y, conic a/b/c, opacity, rgb, z),
-//              reused by the backward preprocess for its per-view intermediate results
+//   g2d[vi * 16 + s]: the backward blend's sums over the covered pixels of dL/dpower moments
+//              and of the colour / depth weights (see G2Slot), reused by the backward
+//              preprocess for its per-view intermediate results
 //   pair list: key = global tile id, value = vi; sorted so that each tile's run is in
 //              (depth, index) order; ranges[gtile] = [first, last + 1) of the run.
 #pragma once
@@ -23,8 +24,13 @@ namespace rgs {
 constexpr int kMaxViews = RGS_MAX_VIEWS;
 constexpr int kG2Stride = 16;  // floats per (view, Gaussian) gradient record (64 bytes)
 
-// Screen-space gradient slots.
-enum G2Slot { kGMx = 0, kGMy, kGCa, kGCb, kGCc, kGOp, kGR, kGG, kGB, kGZ };
+// Slots the backward blend accumulates per (view, Gaussian), with dp = dL/dpower of a covered,
+// unclamped pixel and (dx, dy) = p - mu^I:
+//   kM0 = sum dp, kMx = sum dp dx, kMxx = sum dp dx^2, kMy = sum dp dy, kMxy = sum dp dx dy,
+//   kMyy = sum dp dy^2; kGR/kGG/kGB/kGZ = dL/d(colour, depth) = sum dL/dC alpha T.
+// The screen-space gradients are linear in the moments (the conic and opacity are constant per
+// (view, Gaussian)), so the backward preprocess forms them once per record.
+enum G2Slot { kM0 = 0, kMx, kMxx, kMy, kMxy, kMyy, kGR, kGG, kGB, kGZ };
 
 struct ViewParams {
   int width, height;
@@ -206,13 +212,13 @@ __device__ __forceinline__ f32x2 f2_make(float lo, float hi) {
   return r;
 }
 __device__ __forceinline__ float f2_lo(f32x2 v) {
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  float lo;
+  asm("{\n\t.reg .f32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(lo) : "l"(v));
   return lo;
 }
 __device__ __forceinline__ float f2_hi(f32x2 v) {
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  float hi;
+  asm("{\n\t.reg .f32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(hi) : "l"(v));
   return hi;
 }
 __device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
