@@ -251,9 +251,11 @@ __device__ __forceinline__ void stage_gaussian(ulonglong2 (&sp)[R][N], int t, fl
 // Forward blend. A CTA covers one TW x TH tile with TW * TH / PPT threads; thread t owns the
 // PPT vertically adjacent pixels (x, y0 + k), k < PPT, of column x = t % TW, so every Gaussian
 // staged in shared memory is read once per thread and evaluated for PPT pixels. With an even PPT
-// the pixels go in pairs through packed f32x2 arithmetic, branch-free: a pixel that does not
-// composite a Gaussian gets weight +0, which leaves its colour, depth and transmittance
-// bit-identical, so the result equals the one-pixel-per-thread kernel's.
+// the pixels go in pairs through packed f32x2 arithmetic: a pixel that does not composite a
+// Gaussian gets weight +0, which leaves its colour, depth and transmittance bit-identical, so the
+// result equals the one-pixel-per-thread kernel's. A pixel that has stopped (its transmittance
+// would fall below t_min) keeps its transmittance negated: -T, so that every later Gaussian
+// fails the composite test without a per-pixel flag, and only the rare stop itself branches.
 // ------------------------------------------------------------------------------------------
 template <int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
@@ -283,27 +285,30 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   f32x2 T2[P2], C02[P2], C12[P2], C22[P2], D2[P2], FY[P2];
   int32_t last[PPT];
   uint32_t visited_end[PPT];  // one past the last list position the pixel visited
-  bool done[PPT];
-  bool all_done = true;
+  bool done[PPT];             // one-pixel path: the pixel has stopped (or is off the image)
+  int live = 0;               // pixels of the thread that have not stopped
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    T[k] = 1.0f;
+    done[k] = !(px < vp.width && py0 + k < vp.height);
+    T[k] = done[k] ? -1.0f : 1.0f;
     C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
     last[k] = -1;
-    done[k] = !(px < vp.width && py0 + k < vp.height);
     visited_end[k] = done[k] ? range.x : range.y;
-    all_done = all_done && done[k];
+    live += done[k] ? 0 : 1;
   }
 #pragma unroll
   for (int q = 0; q < P2; ++q) {
-    T2[q] = f2_make(1.0f, 1.0f);
+    const int k0 = kPacked ? 2 * q : 0, k1 = kPacked ? 2 * q + 1 : 0;
+    T2[q] = f2_make(T[k0], T[k1]);
     C02[q] = C12[q] = C22[q] = D2[q] = f2_make(0.0f, 0.0f);
-    FY[q] = f2_make((float)(py0 + 2 * q), (float)(py0 + 2 * q + 1));
+    FY[q] = f2_make((float)(py0 + k0), (float)(py0 + k1));
   }
   const f32x2 FX = f2_make(fx, fx);
+  // 0 <= x < t_min for a float x, as one unsigned compare of its bit pattern (t_min > 0).
+  const uint32_t t_min_bits = __float_as_uint(c.t_min);
   uint32_t contribs = 0;
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
-    if (__syncthreads_count(all_done) == kThreads) break;
+    if (__syncthreads_count(live == 0) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
     if (j < range.y) {
       const uint32_t vi = pair_vals[j];
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kThreads, range.y - start);
-    for (int g = 0; g < cnt && !all_done; ++g) {
+    for (int g = 0; g < cnt && live > 0; ++g) {
       const uint32_t pos = start + g;
       if constexpr (kPacked) {
         const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
@@ -327,31 +332,31 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
           const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
           const float a0 = fminf(c.alpha_max, ex2_approx(f2_lo(pw)));
           const float a1 = fminf(c.alpha_max, ex2_approx(f2_hi(pw)));
-          const bool cov0 = !done[k0] && a0 >= c.alpha_min;
-          const bool cov1 = !done[k1] && a1 >= c.alpha_min;
-          // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha).
+          const bool cov0 = a0 >= c.alpha_min, cov1 = a1 >= c.alpha_min;
+          // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha):
+          // positive while the pixel is live (alpha <= alpha_max < 1), negative once stopped.
           const f32x2 w = f2_mul(f2_make(a0, a1), T2[q]);
           const f32x2 Tn = f2_sub(T2[q], w);
-          const bool stop0 = cov0 && f2_lo(Tn) < c.t_min;
-          const bool stop1 = cov1 && f2_hi(Tn) < c.t_min;
-          const bool take0 = cov0 && !stop0, take1 = cov1 && !stop1;
+          const float tn0 = f2_lo(Tn), tn1 = f2_hi(Tn);
+          const bool take0 = cov0 && !(tn0 < c.t_min), take1 = cov1 && !(tn1 < c.t_min);
+          const bool stop0 = cov0 && __float_as_uint(tn0) < t_min_bits;
+          const bool stop1 = cov1 && __float_as_uint(tn1) < t_min_bits;
           const f32x2 wm = f2_make(take0 ? f2_lo(w) : 0.0f, take1 ? f2_hi(w) : 0.0f);
           C02[q] = f2_fma(wm, CA.x, C02[q]);
           C12[q] = f2_fma(wm, CA.y, C12[q]);
           C22[q] = f2_fma(wm, CB.x, C22[q]);
           D2[q] = f2_fma(wm, CB.y, D2[q]);
           T2[q] = f2_sub(T2[q], wm);
-          if (stop0) {
-            done[k0] = true;
-            visited_end[k0] = pos + 1;
-          }
-          if (stop1) {
-            done[k1] = true;
-            visited_end[k1] = pos + 1;
-          }
           if (take0) last[k0] = (int32_t)pos;
           if (take1) last[k1] = (int32_t)pos;
           contribs += (uint32_t)take0 + (uint32_t)take1;
+          if (stop0 || stop1) {  // once per pixel: keep -T from here on
+            const float t0 = f2_lo(T2[q]), t1 = f2_hi(T2[q]);
+            T2[q] = f2_make(stop0 ? -t0 : t0, stop1 ? -t1 : t1);
+            if (stop0) visited_end[k0] = pos + 1;
+            if (stop1) visited_end[k1] = pos + 1;
+            live -= (int)stop0 + (int)stop1;
+          }
         }
       } else {
         const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
@@ -370,6 +375,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
               if (Tn < c.t_min) {
                 done[k] = true;
                 visited_end[k] = pos + 1;
+                --live;
               } else {
                 C0[k] = fmaf(w, g2.x, C0[k]);
                 C1[k] = fmaf(w, g2.y, C1[k]);
@@ -383,16 +389,13 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
           }
         }
       }
-      all_done = true;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) all_done = all_done && done[k];
     }
   }
   if constexpr (kPacked) {
 #pragma unroll
     for (int q = 0; q < P2; ++q) {
-      T[2 * q] = f2_lo(T2[q]);
-      T[2 * q + 1] = f2_hi(T2[q]);
+      T[2 * q] = fabsf(f2_lo(T2[q]));
+      T[2 * q + 1] = fabsf(f2_hi(T2[q]));
       C0[2 * q] = f2_lo(C02[q]);
       C0[2 * q + 1] = f2_hi(C02[q]);
       C1[2 * q] = f2_lo(C12[q]);
