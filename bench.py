@@ -487,9 +487,10 @@ def run_ours(args, world, rank, local):
     dominant = max(phases, key=phases.get)
     if dominant in work:
         achieved = work[dominant] / (phases[dominant] / 1e3) / 1e12
+        ppt = tuned["pixels_per_thread" if dominant == "blend_forward"
+                    else "backward_pixels_per_thread"]
         traffic = MEASURED_TRAFFIC.get(
-            (args.workload, dominant,
-             f"{tuned['tile_w']}x{tuned['tile_h']}x{tuned['pixels_per_thread']}"))
+            (args.workload, dominant, f"{tuned['tile_w']}x{tuned['tile_h']}x{ppt}"))
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                     "peak_source": f"FP32 FMA pipe: 128 lanes x 2 FLOP x {props.multi_processor_count}"
@@ -508,7 +509,9 @@ def run_ours(args, world, rank, local):
                    "pixels_per_step": pixels, "sh_degree": int(round(K ** 0.5)) - 1,
                    "grad": wl.grad_mask, "cuda_graph": True,
                    "tile": f"{tuned['tile_w']}x{tuned['tile_h']}",
-                   "pixels_per_thread": tuned["pixels_per_thread"], "autotuned": True,
+                   "pixels_per_thread": tuned["pixels_per_thread"],
+                   "backward_pixels_per_thread": tuned["backward_pixels_per_thread"],
+                   "autotuned": True,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "clocks": clk,

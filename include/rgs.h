@@ -93,10 +93,14 @@ typedef struct {
   float bg[3];      /* background colour, added as bg * T_final */
   int32_t tile_w;   /* tile shape of the binning and blend: 16x16 (default), 8x8 or 32x8 */
   int32_t tile_h;
-  int32_t pixels_per_thread; /* vertically adjacent pixels per blend thread: 1, 2, 4 or 8
-                                (4 and 8 not with 8x8 tiles); 0 = default (4). Results do not depend
-                                on it or on the tile shape beyond atomics-order rounding of the
-                                gradients */
+  int32_t pixels_per_thread; /* vertically adjacent pixels per forward-blend thread: 1, 2, 4 or
+                                8 (4 and 8 not with 8x8 tiles); 0 = default (4). Results do not
+                                depend on it or on the tile shape beyond atomics-order rounding of
+                                the gradients */
+  int32_t backward_pixels_per_thread; /* the same for the backward blend (same rules); 0 = equal to
+                                         pixels_per_thread. The two blends share only the tile
+                                         shape: the per-pixel state between them is stored in
+                                         image order */
 } rgs_config;
 
 /* Forward outputs (device, caller-owned, P = sum_v W_v H_v): color [P,3], depth [P], alpha [P]. */
@@ -183,14 +187,16 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t state, const rgs_image_gra
                                float* d_quats, float* d_opacity_logits, float* d_sh,
                                float* d_pose, void* stream);
 
-/* Autotuner: picks the blend tile shape and pixels per thread (the per-thread batch depth of the
- * blends) that make one forward + backward of this exact workload fastest on this GPU. Every
- * supported combination (16x16, 8x8, 32x8 tiles; 1, 2, 4 or 8 pixels per thread) is timed with
- * CUDA events (one warm-up and three timed runs of forward + backward with a zero upstream
- * gradient, all gradients requested) in scratch buffers of its own. The fastest is written into
- * cfg->tile_w, cfg->tile_h and cfg->pixels_per_thread (other fields are kept) and cached in the
- * context under (n, sh_degree, the views' sizes); a later call with the same key returns the
- * cached choice without timing. Results do not depend on the choice beyond atomics-order
+/* Autotuner: picks the blend tile shape and the pixels per thread of each blend (the per-thread
+ * batch depth) that make one forward + backward of this exact workload fastest on this GPU. For
+ * every tile shape (16x16, 8x8, 32x8) and every pixels-per-thread value it admits (1, 2, 4, 8)
+ * the forward and the backward are timed separately with CUDA events (one warm-up and three
+ * timed runs, zero upstream colour gradient, all gradients requested) in scratch buffers of its
+ * own; per tile shape the fastest forward and the fastest backward setting are combined, and the
+ * tile shape with the smallest sum wins. The choice is written into cfg->tile_w, cfg->tile_h,
+ * cfg->pixels_per_thread and cfg->backward_pixels_per_thread (other fields are kept) and cached
+ * in the context under (n, sh_degree, the views' sizes); a later call with the same key returns
+ * the cached choice without timing. Results do not depend on the choice beyond atomics-order
  * rounding of the gradients. Synchronises `stream`; allocates and frees device memory. Under
  * stream capture it returns RGS_ERR_INVALID_ARG. ms_out (may be NULL) receives the winner's
  * forward + backward time in milliseconds (0 when served from the cache). */

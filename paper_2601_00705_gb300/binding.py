@@ -50,7 +50,8 @@ class Config(ctypes.Structure):
                 ("t_min", ctypes.c_float), ("znear", ctypes.c_float), ("eps2d", ctypes.c_float),
                 ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("pixels_per_thread", ctypes.c_int32)]
+                ("pixels_per_thread", ctypes.c_int32),
+                ("backward_pixels_per_thread", ctypes.c_int32)]
 
 
 class Images(ctypes.Structure):

@@ -809,7 +809,8 @@ cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, cons
                          float* t_final, int32_t* last_index, const float* d_color,
                          const float* d_depth, const float* d_alpha, float* g2d,
                          Counters* counters, cudaStream_t stream) {
-  const int tw = views.tile_w, th = views.tile_h, ppt = views.pixels_per_thread;
+  const int tw = views.tile_w, th = views.tile_h;
+  const int ppt = forward ? views.pixels_per_thread : views.bwd_pixels_per_thread;
 #define RGS_BLEND(W, H, P)                                                                        \
   if (tw == W && th == H && ppt == P)                                                             \
   return launch_blends_t<W, H, P>(forward, views, c, ranges, pair_vals, rec0, rec1, rec2, color, \

@@ -115,7 +115,7 @@ struct State {
 }  // namespace
 
 struct TuneChoice {
-  int tile_w, tile_h, ppt;
+  int tile_w, tile_h, ppt, bwd_ppt;
 };
 
 struct rgs_ctx {
@@ -329,16 +329,22 @@ rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const 
     return fail(ctx, RGS_ERR_INVALID_ARG, "n_views must be in 1..RGS_MAX_VIEWS");
   const int tw = cfg.tile_w, th = cfg.tile_h;
   const int ppt = cfg.pixels_per_thread == 0 ? 4 : cfg.pixels_per_thread;
+  const int bwd_ppt = cfg.backward_pixels_per_thread == 0 ? ppt : cfg.backward_pixels_per_thread;
   if (!((tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8)))
     return fail(ctx, RGS_ERR_INVALID_ARG, "tile shape must be 16x16, 8x8 or 32x8");
   if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || (tw * th / ppt) % 32 != 0)
     return fail(ctx, RGS_ERR_INVALID_ARG,
                 "pixels_per_thread must be 1, 2, 4 or 8 with whole warps per tile");
+  if (!(bwd_ppt == 1 || bwd_ppt == 2 || bwd_ppt == 4 || bwd_ppt == 8) ||
+      (tw * th / bwd_ppt) % 32 != 0)
+    return fail(ctx, RGS_ERR_INVALID_ARG,
+                "backward_pixels_per_thread must be 0, 1, 2, 4 or 8 with whole warps per tile");
   std::memset(&views, 0, sizeof(views));
   views.n_views = n_views;
   views.tile_w = tw;
   views.tile_h = th;
   views.pixels_per_thread = ppt;
+  views.bwd_pixels_per_thread = bwd_ppt;
   long long pix = 0;
   long long tiles = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -426,6 +432,7 @@ void rgs_config_default(rgs_config* cfg) {
   cfg->tile_w = 16;
   cfg->tile_h = 16;
   cfg->pixels_per_thread = 4;
+  cfg->backward_pixels_per_thread = 0;
 }
 
 rgs_status rgs_create(rgs_ctx** out, int device) {
@@ -477,6 +484,7 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
     cfg->tile_w = hit->second.tile_w;
     cfg->tile_h = hit->second.tile_h;
     cfg->pixels_per_thread = hit->second.ppt;
+    cfg->backward_pixels_per_thread = hit->second.bwd_ppt;
     return RGS_OK;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice");
@@ -499,48 +507,72 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
   float* d_sh = carve<float>(p, 3 * K * n1);
   float* dpose = carve<float>(p, 6 * n_views);
   rgs_status result = RGS_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   uint64_t state = 0;
   do {
     if (cudaMemsetAsync(upc, 0, sizeof(float) * 3 * pixels, stream) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaEventCreate(&e2) != cudaSuccess) {
       result = fail(ctx, RGS_ERR_CUDA, "autotune setup");
       break;
     }
     rgs_images out{img, img + 3 * pixels, img + 4 * pixels};
     rgs_image_grads up{upc, nullptr, nullptr};
     const uint32_t mask = RGS_GRAD_ALL;
-    const TuneChoice cands[] = {{16, 16, 4}, {16, 16, 8}, {16, 16, 2}, {16, 16, 1}, {8, 8, 2},
-                                {8, 8, 1},   {32, 8, 8},  {32, 8, 4},  {32, 8, 2}, {32, 8, 1}};
+    struct Shape {
+      int tile_w, tile_h;
+    };
+    const Shape shapes[] = {{16, 16}, {8, 8}, {32, 8}};
+    const int ppts[] = {4, 8, 2, 1};
     float best = 1e30f;
-    TuneChoice choice = cands[0];
-    for (const TuneChoice& c : cands) {
-      rgs_config trial = *cfg;
-      trial.tile_w = c.tile_w;
-      trial.tile_h = c.tile_h;
-      trial.pixels_per_thread = c.ppt;
-      float total = 0.0f;
-      rgs_status st = RGS_OK;
-      for (int it = 0; it < 4 && st == RGS_OK; ++it) {
-        if (it == 1) cudaEventRecord(e0, stream);
-        st = rgs_render_forward(ctx, g, cams, n_views, &trial, &out, &state, stream);
-        if (st == RGS_OK)
-          st = rgs_render_backward(ctx, state, &up, mask, d_means, d_ls, d_q, d_o, d_sh, dpose,
-                                   stream);
+    TuneChoice choice{16, 16, 4, 4};
+    for (const Shape& sh : shapes) {
+      // The blends share only the tile shape, so per shape the forward and the backward setting
+      // are chosen independently.
+      float best_f = 1e30f, best_b = 1e30f;
+      int ppt_f = 0, ppt_b = 0;
+      for (const int ppt : ppts) {
+        if ((sh.tile_w * sh.tile_h / ppt) % 32 != 0) continue;
+        rgs_config trial = *cfg;
+        trial.tile_w = sh.tile_w;
+        trial.tile_h = sh.tile_h;
+        trial.pixels_per_thread = ppt;
+        trial.backward_pixels_per_thread = ppt;
+        float t_f = 0.0f, t_b = 0.0f;
+        for (int it = 0; it < 4 && result == RGS_OK; ++it) {
+          cudaEventRecord(e0, stream);
+          rgs_status st = rgs_render_forward(ctx, g, cams, n_views, &trial, &out, &state, stream);
+          cudaEventRecord(e1, stream);
+          if (st == RGS_OK)
+            st = rgs_render_backward(ctx, state, &up, mask, d_means, d_ls, d_q, d_o, d_sh, dpose,
+                                     stream);
+          cudaEventRecord(e2, stream);
+          float ms_f = 0.0f, ms_b = 0.0f;
+          if (st != RGS_OK) {
+            result = st;
+          } else if (cudaEventSynchronize(e2) != cudaSuccess ||
+                     cudaEventElapsedTime(&ms_f, e0, e1) != cudaSuccess ||
+                     cudaEventElapsedTime(&ms_b, e1, e2) != cudaSuccess) {
+            result = fail(ctx, RGS_ERR_CUDA, "autotune timing");
+          } else if (it > 0) {  // the first run is the warm-up
+            t_f += ms_f;
+            t_b += ms_b;
+          }
+        }
+        if (result != RGS_OK) break;
+        if (t_f < best_f) {
+          best_f = t_f;
+          ppt_f = ppt;
+        }
+        if (t_b < best_b) {
+          best_b = t_b;
+          ppt_b = ppt;
+        }
       }
-      if (st != RGS_OK) {
-        result = st;
-        break;
-      }
-      cudaEventRecord(e1, stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&total, e0, e1) != cudaSuccess) {
-        result = fail(ctx, RGS_ERR_CUDA, "autotune timing");
-        break;
-      }
-      if (total < best) {
-        best = total;
-        choice = c;
+      if (result != RGS_OK) break;
+      if (ppt_f != 0 && best_f + best_b < best) {
+        best = best_f + best_b;
+        choice = TuneChoice{sh.tile_w, sh.tile_h, ppt_f, ppt_b};
       }
     }
     if (result != RGS_OK) break;
@@ -548,6 +580,7 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
     cfg->tile_w = choice.tile_w;
     cfg->tile_h = choice.tile_h;
     cfg->pixels_per_thread = choice.ppt;
+    cfg->backward_pixels_per_thread = choice.bwd_ppt;
     if (ms_out) *ms_out = best / 3.0f;
   } while (false);
   cudaStreamSynchronize(stream);
@@ -560,6 +593,7 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  if (e2) cudaEventDestroy(e2);
   cudaFree(base);
   return result;
 }

@@ -52,8 +52,8 @@ struct Views {
   int total_tiles;
   long long total_pixels;
   int tile_w, tile_h;
-  int pixels_per_thread;    // vertically adjacent pixels per blend thread
-  int pad1;
+  int pixels_per_thread;    // vertically adjacent pixels per forward-blend thread
+  int bwd_pixels_per_thread;  // the same for the backward blend
   ViewParams v[kMaxViews];
 };
 

@@ -127,7 +127,8 @@ class Renderer:
         g = binding.Gaussians(n, deg, *[x.data_ptr() for x in t])
         ms = self.ctx.autotune(g, cameras, self.config, self.stream_handle())
         return dict(tile_w=self.config.tile_w, tile_h=self.config.tile_h,
-                    pixels_per_thread=self.config.pixels_per_thread, ms=ms)
+                    pixels_per_thread=self.config.pixels_per_thread,
+                    backward_pixels_per_thread=self.config.backward_pixels_per_thread, ms=ms)
 
     def release(self, state: int):
         self.ctx.release(state)

@@ -277,6 +277,11 @@ def test_invalid_arguments_and_handles_return_error_codes():
     assert fwd(gauss(), cfg=bad) == binding.RGS_ERR_INVALID_ARG
     bad = binding.default_config(tile_w=8, tile_h=8, pixels_per_thread=4)
     assert fwd(gauss(), cfg=bad) == binding.RGS_ERR_INVALID_ARG
+    bad = binding.default_config(tile_w=8, tile_h=8, pixels_per_thread=2,
+                                 backward_pixels_per_thread=8)
+    assert fwd(gauss(), cfg=bad) == binding.RGS_ERR_INVALID_ARG
+    bad = binding.default_config(backward_pixels_per_thread=3)
+    assert fwd(gauss(), cfg=bad) == binding.RGS_ERR_INVALID_ARG
     bad = binding.default_config(znear=-1.0)
     assert fwd(gauss(), cfg=bad) == binding.RGS_ERR_INVALID_ARG
     grads = binding.ImageGrads(None, None, None)

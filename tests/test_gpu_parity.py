@@ -90,13 +90,16 @@ def test_tiny_forward_and_all_gradients():
 
 
 @pytest.mark.parametrize("tile", [(16, 16, 1), (16, 16, 2), (16, 16, 8), (8, 8, 1), (8, 8, 2),
-                                  (32, 8, 1), (32, 8, 2), (32, 8, 4), (32, 8, 8)])
+                                  (32, 8, 1), (32, 8, 2), (32, 8, 4), (32, 8, 8),
+                                  (16, 16, 8, 2), (16, 16, 1, 8), (32, 8, 2, 8), (8, 8, 2, 1)])
 def test_tile_shape_and_pixels_per_thread_do_not_change_results(tile):
+    """tile = (tile_w, tile_h, pixels per thread[, backward pixels per thread])."""
     wl = synthetic.tiny(seed=77)
     g, orc0, d_color, _ = _oracle_l1_case(wl)
     ref = gpu_render(g, wl.cameras, d_color=d_color)  # default: 16x16 tiles, 4 pixels per thread
     out = gpu_render(g, wl.cameras, d_color=d_color, tile_w=tile[0], tile_h=tile[1],
-                     pixels_per_thread=tile[2])
+                     pixels_per_thread=tile[2],
+                     backward_pixels_per_thread=tile[3] if len(tile) > 3 else 0)
     # Per-pixel compositing does not depend on the binning: the forward is bit-identical.
     for k in ("color", "depth", "alpha"):
         np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
@@ -187,11 +190,15 @@ def test_autotuner_choice_is_valid_cached_and_leaves_results_unchanged():
     first = r.autotune(*params, wl.cameras)
     assert (first["tile_w"], first["tile_h"]) in {(16, 16), (8, 8), (32, 8)}
     assert first["pixels_per_thread"] in (1, 2, 4, 8) and first["ms"] > 0
+    assert first["backward_pixels_per_thread"] in (1, 2, 4, 8)
+    for k in ("pixels_per_thread", "backward_pixels_per_thread"):
+        assert first["tile_w"] * first["tile_h"] // first[k] % 32 == 0
+    keys = ("tile_w", "tile_h", "pixels_per_thread", "backward_pixels_per_thread")
     second = r.autotune(*params, wl.cameras)
-    assert second["ms"] == 0 and {k: second[k] for k in ("tile_w", "tile_h", "pixels_per_thread")} \
-        == {k: first[k] for k in ("tile_w", "tile_h", "pixels_per_thread")}
+    assert second["ms"] == 0 and {k: second[k] for k in keys} == {k: first[k] for k in keys}
     tuned = gpu_render(g, wl.cameras, tile_w=first["tile_w"], tile_h=first["tile_h"],
-                       pixels_per_thread=first["pixels_per_thread"])
+                       pixels_per_thread=first["pixels_per_thread"],
+                       backward_pixels_per_thread=first["backward_pixels_per_thread"])
     ref = gpu_render(g, wl.cameras)
     for k in ("color", "depth", "alpha"):
         np.testing.assert_array_equal(tuned[k], ref[k], err_msg=k)
