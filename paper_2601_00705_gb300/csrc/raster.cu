@@ -307,6 +307,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   // 0 <= x < t_min for a float x, as one unsigned compare of its bit pattern (t_min > 0).
   const uint32_t t_min_bits = __float_as_uint(c.t_min);
   uint32_t contribs = 0;
+  // Packed path: Gaussians composited by the thread's even / odd pixels, counted in floats. The
+  // sums are exact: a pixel composites at most ln(t_min) / ln(1 - alpha_min) ~ 2.3e3 Gaussians
+  // before it stops, so they stay far below 2^24.
+  f32x2 cnt2 = f2_make(0.0f, 0.0f);
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
     if (__syncthreads_count(live == 0) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
           T2[q] = f2_sub(T2[q], wm);
           if (take0) last[k0] = (int32_t)pos;
           if (take1) last[k1] = (int32_t)pos;
-          contribs += (uint32_t)take0 + (uint32_t)take1;
+          cnt2 = f2_add(cnt2, f2_make(take0 ? 1.0f : 0.0f, take1 ? 1.0f : 0.0f));
           if (stop0 || stop1) {  // once per pixel: keep -T from here on
             const float t0 = f2_lo(T2[q]), t1 = f2_hi(T2[q]);
             T2[q] = f2_make(stop0 ? -t0 : t0, stop1 ? -t1 : t1);
@@ -392,6 +396,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     }
   }
   if constexpr (kPacked) {
+    contribs = (uint32_t)f2_lo(cnt2) + (uint32_t)f2_hi(cnt2);
 #pragma unroll
     for (int q = 0; q < P2; ++q) {
       T[2 * q] = fabsf(f2_lo(T2[q]));

@@ -23,6 +23,8 @@ def main(argv: list[str] | None = None) -> None:
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--workload", default="tum", choices=sorted(synthetic.WORKLOADS))
     p.add_argument("--tile", default="16x16x8", help="tile_w x tile_h x pixels per thread")
+    p.add_argument("--backward-ppt", type=int, default=0,
+                   help="pixels per thread of the backward blend (0: as the forward)")
     p.add_argument("--steps", type=int, default=2)
     args = p.parse_args(argv)
     tw, th, ppt = (int(x) for x in args.tile.split("x"))
@@ -40,14 +42,16 @@ def main(argv: list[str] | None = None) -> None:
     d_color = up(d_color)
     d_depth = up(d_depth) if wl.depth_weight else None
     mask = binding.GRAD_POSE if wl.grad_mask == "pose" else binding.GRAD_ALL
-    r = Renderer(dev, tile_w=tw, tile_h=th, pixels_per_thread=ppt)
+    r = Renderer(dev, tile_w=tw, tile_h=th, pixels_per_thread=ppt,
+                 backward_pixels_per_thread=args.backward_ppt)
     cams = binding.make_cameras(wl.cameras)
     state = 0
     for _ in range(args.steps):
         _, _, _, state = r.forward_raw(*params, cams, state=state)
         r.backward_raw(state, n, K, V, d_color, d_depth, None, mask)
     torch.cuda.synchronize(dev)
-    print(json.dumps({"workload": args.workload, "tile": args.tile, "steps": args.steps,
+    print(json.dumps({"workload": args.workload, "tile": args.tile,
+                      "backward_ppt": args.backward_ppt or ppt, "steps": args.steps,
                       "counters": r.stats(state)}))
 
 
