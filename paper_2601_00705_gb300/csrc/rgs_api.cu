@@ -444,6 +444,8 @@ rgs_status rgs_create(rgs_ctx** out, int device) {
   if (cudaSetDevice(device) != cudaSuccess) return RGS_ERR_CUDA;
   rgs_ctx* ctx = new rgs_ctx();
   ctx->device = device;
+  // Decide once, outside any stream capture, whether sorts can run as one cluster launch.
+  (void)cluster_sort_capacity(device);
   if (cudaMallocHost(&ctx->host_counters, sizeof(Counters)) != cudaSuccess) {
     delete ctx;
     return RGS_ERR_NOMEM;

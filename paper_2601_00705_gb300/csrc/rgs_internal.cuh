@@ -431,6 +431,10 @@ inline int64_t sort_hist_entries(int64_t n_cap, int items = kSortItems) {
   return (sort_blocks(n_cap, items) + 1) * kRadixBins;
 }
 
+// Largest n the single-cluster sort takes on `device` (0: cluster launches unavailable); sorts
+// with n_cap up to it run as one launch and always return their result in the alternate buffers.
+int64_t cluster_sort_capacity(int device);
+
 // Stable LSD radix sort of (keys, vals) by bits [begin_bit, end_bit); ping-pongs between the
 // (keys, vals) and (keys_alt, vals_alt) buffers and returns in *result_in_alt whether the
 // sorted data ended in the alternate buffers. vals may be null (keys only).

@@ -1,8 +1,17 @@
 // sort.cu -- prefix scans, visibility compaction and the stable LSD radix sort that build the
 // front-to-back ordered covering lists (Section 3.1: per pixel, the covering Gaussians near to
 // far). All scans are reduce-then-scan (three kernels, no inter-block waiting), so no kernel
-// here ever spins on another block.
+// here ever spins on another block. Sorts that fit in the shared memory of one thread-block
+// cluster run as a single launch whose blocks meet only at the hardware cluster barrier (the
+// blocks of a cluster are co-scheduled by construction).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "rgs_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rgs {
 namespace {
@@ -316,6 +325,157 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Single-cluster radix sort: the whole sort in one launch of one cluster of C blocks (C = 16,
+// else 8), for n <= C * kCsSlice; used for n_cap <= kCsMaxN, where it beats three launches per
+// pass. Block c owns the slice [c S, (c + 1) S) of the sequence,
+// S = ceil(n / C), held in its shared memory. Per 8-bit pass:
+//   (a) stable ranks inside the block (warp w owns a contiguous run of the slice and walks it
+//       in rounds of 32 elements, as in the multi-kernel downsweep);
+//   (b) per-digit counts of the block, published in its shared memory; local digit starts;
+//   (c) local sort of the slice into the second buffer;
+//   cluster barrier;
+//   (e) every block reads all blocks' digit counts (distributed shared memory): the global start
+//       of each digit plus the counts of that digit in the blocks before it;
+//   (f) each digit's run is stored, in order, at its global position: into the first buffer of
+//       the block that owns that position (distributed shared memory), or to the output array
+//       after the last pass;
+//   cluster barrier.
+// Every block executes every barrier, also when its slice is empty.
+// ------------------------------------------------------------------------------------------
+constexpr int kCsThreads = 1024;
+constexpr int kCsWarps = kCsThreads / 32;
+constexpr int kCsItems = 11;
+constexpr int kCsSlice = kCsThreads * kCsItems;  // elements per block at most
+// Dynamic shared memory: two (key, value) buffers of kCsSlice, the per-warp digit counts, the
+// block's digit counts, local digit starts and per-digit destination shifts.
+constexpr size_t kCsSmemWords = 4 * (size_t)kCsSlice + (size_t)kCsWarps * kRadixBins + 3 * kRadixBins;
+constexpr size_t kCsSmemBytes = kCsSmemWords * sizeof(uint32_t);
+// Largest n_cap routed to the single-cluster sort. Measured on GB300 with 16-block clusters, a
+// pass costs ~6.3 us plus ~0.09 us per 1k elements (latency of the in-block ranking and the
+// exchanges on 16 SMs), the three-kernel pass ~10.5 us at these sizes: the cluster wins below
+// ~48k elements (2k: 27 vs 39 us for a 31-bit sort; 36k: 39 vs 43 us; 115k: 71 vs 43 us).
+constexpr int64_t kCsMaxN = 56 * 1024;
+
+__global__ void __launch_bounds__(kCsThreads, 1) cluster_sort_kernel(
+    const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+    int64_t n_cap, const uint32_t* n_dev, int begin_bit, int end_bit) {
+  chain_wait();
+  extern __shared__ uint32_t cs_smem[];
+  uint32_t* a_keys = cs_smem;
+  uint32_t* a_vals = a_keys + kCsSlice;
+  uint32_t* b_keys = a_vals + kCsSlice;
+  uint32_t* b_vals = b_keys + kCsSlice;
+  uint32_t* warp_counts = b_vals + kCsSlice;  // [kCsWarps][kRadixBins]
+  uint32_t* cta_counts = warp_counts + kCsWarps * kRadixBins;
+  uint32_t* local_start = cta_counts + kRadixBins;
+  uint32_t* digit_shift = local_start + kRadixBins;
+  cg::cluster_group cluster = cg::this_cluster();
+  const uint32_t C = cluster.num_blocks(), me = cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t n = read_count(n_dev, n_cap);
+  const uint32_t S = (n + C - 1) / C;
+  const uint32_t lo = me * S;
+  const uint32_t cnt = n > lo ? min(S, n - lo) : 0u;
+  const bool has_vals = vals_in != nullptr;
+  for (uint32_t t = tid; t < cnt; t += kCsThreads) {
+    a_keys[t] = keys_in[lo + t];
+    if (has_vals) a_vals[t] = vals_in[lo + t];
+  }
+  __syncthreads();
+  const int bits = end_bit - begin_bit;
+  const int passes = (bits + 7) / 8;
+  const int per_pass = (bits + passes - 1) / passes;
+  const uint32_t rounds = (cnt + kCsThreads - 1) / kCsThreads;  // rounds of 32 per warp
+  const uint32_t wbase = (uint32_t)warp * 32u * rounds;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t* my_counts = warp_counts + warp * kRadixBins;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = begin_bit + p * per_pass;
+    const int w = (shift + per_pass <= end_bit) ? per_pass : end_bit - shift;
+    const uint32_t mask = (w >= 32) ? 0xffffffffu : ((1u << w) - 1u);
+    // (a) Stable ranks within the warp's run.
+    for (int d = lane; d < kRadixBins; d += 32) my_counts[d] = 0;
+    __syncwarp();
+    uint32_t key[kCsItems], val[kCsItems], rank[kCsItems];
+#pragma unroll
+    for (int r = 0; r < kCsItems; ++r) {
+      rank[r] = 0xffffffffu;
+      key[r] = val[r] = 0u;
+      if ((uint32_t)r < rounds) {  // warp-uniform
+        const uint32_t e = wbase + (uint32_t)r * 32u + lane;
+        const bool valid = e < cnt;
+        if (valid) {
+          key[r] = a_keys[e];
+          if (has_vals) val[r] = a_vals[e];
+        }
+        const uint32_t digit = valid ? ((key[r] >> shift) & mask) : (uint32_t)kRadixBins;
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t before = __popc(peers & lt_mask);
+        const uint32_t prior = valid ? my_counts[digit] : 0u;
+        __syncwarp();
+        if (valid && before == 0) my_counts[digit] = prior + __popc(peers);
+        __syncwarp();
+        if (valid) rank[r] = prior + before;
+      }
+    }
+    __syncthreads();
+    // (b) Digit d: exclusive prefix over the warps, block total, local start.
+    uint32_t total = 0;
+    if (tid < kRadixBins) {
+      for (int w2 = 0; w2 < kCsWarps; ++w2) {
+        const uint32_t c2 = warp_counts[w2 * kRadixBins + tid];
+        warp_counts[w2 * kRadixBins + tid] = total;
+        total += c2;
+      }
+    }
+    const uint32_t ls = block_exclusive_scan<kCsThreads>(tid < kRadixBins ? total : 0u, nullptr);
+    if (tid < kRadixBins) {
+      local_start[tid] = ls;
+      cta_counts[tid] = total;
+    }
+    __syncthreads();
+    // (c) Local sort into the second buffer.
+#pragma unroll
+    for (int r = 0; r < kCsItems; ++r) {
+      if (rank[r] == 0xffffffffu) continue;
+      const uint32_t d = (key[r] >> shift) & mask;
+      const uint32_t pos = local_start[d] + my_counts[d] + rank[r];
+      b_keys[pos] = key[r];
+      b_vals[pos] = val[r];
+    }
+    cluster.sync();
+    // (e) Global start of each digit's run of this block.
+    uint32_t all = 0, before_me = 0;
+    if (tid < kRadixBins) {
+      for (uint32_t r2 = 0; r2 < C; ++r2) {
+        const uint32_t v = cluster.map_shared_rank(cta_counts, r2)[tid];
+        all += v;
+        if (r2 < me) before_me += v;
+      }
+    }
+    const uint32_t gstart = block_exclusive_scan<kCsThreads>(tid < kRadixBins ? all : 0u, nullptr);
+    if (tid < kRadixBins) digit_shift[tid] = gstart + before_me - local_start[tid];  // mod 2^32
+    __syncthreads();
+    // (f) Runs to their global positions.
+    const bool last = p == passes - 1;
+    for (uint32_t t = tid; t < cnt; t += kCsThreads) {
+      const uint32_t k = b_keys[t];
+      const uint32_t dest = digit_shift[(k >> shift) & mask] + t;
+      if (last) {
+        keys_out[dest] = k;
+        if (has_vals) vals_out[dest] = b_vals[t];
+      } else {
+        const uint32_t owner = dest / S;
+        const uint32_t off = dest - owner * S;
+        cluster.map_shared_rank(a_keys, owner)[off] = k;
+        if (has_vals) cluster.map_shared_rank(a_vals, owner)[off] = b_vals[t];
+      }
+    }
+    cluster.sync();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_cap,
@@ -378,11 +538,85 @@ cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
   return cudaGetLastError();
 }
 
+int cluster_sort_blocks(int device) {
+  // Per device: 16 blocks per cluster if one such cluster fits on the GPU, else 8, else 0.
+  static std::mutex mu;
+  static int cached[64];
+  static bool known[64] = {};
+  if (device < 0 || device >= 64) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (known[device]) return cached[device];
+  int result = 0;
+  int prev = 0;
+  if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(device) == cudaSuccess &&
+      cudaFuncSetAttribute(cluster_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kCsSmemBytes) == cudaSuccess &&
+      cudaFuncSetAttribute(cluster_sort_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                           1) == cudaSuccess) {
+    for (const int c : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(c);
+      cfg.blockDim = dim3(kCsThreads);
+      cfg.dynamicSmemBytes = kCsSmemBytes;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = c;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, cluster_sort_kernel, &cfg) == cudaSuccess &&
+          clusters > 0) {
+        result = c;
+        break;
+      }
+    }
+  }
+  cudaGetLastError();  // a refused query leaves no sticky error: fall back to the multi-kernel sort
+  cudaSetDevice(prev);
+  cached[device] = result;
+  known[device] = true;
+  return result;
+}
+
+int64_t cluster_sort_capacity(int device) {
+  return std::min<int64_t>((int64_t)cluster_sort_blocks(device) * kCsSlice, kCsMaxN);
+}
+
 cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                               uint32_t* vals_alt, int64_t n_cap, const uint32_t* n_dev,
                               int begin_bit, int end_bit, uint32_t* hist, uint32_t* block_sums,
                               bool* result_in_alt, cudaStream_t stream, int items) {
   (void)block_sums;
+  int device = 0;
+  if (n_cap > 0 && end_bit > begin_bit && cudaGetDevice(&device) == cudaSuccess) {
+    const int blocks = cluster_sort_blocks(device);
+    if (blocks > 0 && n_cap <= std::min<int64_t>((int64_t)blocks * kCsSlice, kCsMaxN)) {
+      // One launch: (keys, vals) -> (keys_alt, vals_alt).
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(blocks);
+      cfg.blockDim = dim3(kCsThreads);
+      cfg.dynamicSmemBytes = kCsSmemBytes;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[2];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = blocks;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[1].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 2;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, cluster_sort_kernel, (const uint32_t*)keys,
+                                               (const uint32_t*)vals, keys_alt,
+                                               vals ? vals_alt : nullptr, n_cap, n_dev,
+                                               begin_bit, end_bit);
+      RGS_LAUNCHED();
+      *result_in_alt = true;
+      return e;
+    }
+  }
   if (items == kSortItemsSmall)
     return radix_sort_t<kSortItemsSmall>(keys, vals, keys_alt, vals_alt, n_cap, n_dev, begin_bit,
                                          end_bit, hist, result_in_alt, stream);

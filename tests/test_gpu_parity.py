@@ -34,9 +34,14 @@ def test_exclusive_scan_matches_cumsum(n):
     assert int(tot.item()) == int(x.astype(np.uint64).sum())
 
 
+# Sizes up to 56 * 1024 = 57344 run as one cluster launch (16- or 8-block clusters), larger ones
+# as three kernels per pass; both are covered, including the boundary and slices that leave the
+# last blocks of the cluster empty.
 @pytest.mark.parametrize("n,begin,end,distinct", [
-    (1, 0, 32, 10), (1000, 0, 8, 7), (4096, 0, 14, 300), (4097, 3, 17, 50),
-    (100_000, 0, 31, 1 << 30), (250_001, 0, 20, 5000), (1_000_000, 0, 32, 1 << 32)])
+    (1, 0, 32, 10), (17, 0, 31, 3), (1000, 0, 8, 7), (4096, 0, 14, 300), (4097, 3, 17, 50),
+    (30_000, 0, 31, 40), (57_344, 5, 29, 1 << 29), (57_345, 0, 24, 1 << 12),
+    (100_000, 0, 31, 1 << 30), (100_000, 0, 31, 50), (250_001, 0, 20, 5000),
+    (1_000_000, 0, 32, 1 << 32)])
 def test_radix_sort_is_stable_and_matches_numpy(n, begin, end, distinct):
     rng = np.random.default_rng(n + begin)
     keys = rng.integers(0, distinct, size=n, dtype=np.uint64).astype(np.uint32)
