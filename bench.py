@@ -50,7 +50,10 @@ BWD_FLOP_PER_EVAL = 40
 # DRAM bytes (read + written) per launch of a dominant kernel, from one ncu capture of exactly
 # this kernel build on exactly this workload and tile configuration; any other combination
 # reports null. Keyed by (workload, kernel, tile_w x tile_h x pixels per thread).
-MEASURED_TRAFFIC: dict[tuple[str, str, str], float] = {}
+MEASURED_TRAFFIC: dict[tuple[str, str, str], float] = {
+    ("tum", "blend_backward", "16x16x8"): 79.6e6,
+    ("tum", "blend_forward", "16x16x4"): 46.1e6,
+}
 
 
 def parse():
