@@ -265,6 +265,69 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------------------ GPU arm
 
+def measure_tracking(r, params, cameras, images, hbm_peak, steps, flush):
+    """Tracking iterations on the same workload: observations rendered at the true poses, the
+    iteration started from every view's pose moved by about 1 cm and 0.6 degrees. One iteration
+    (posed forward, exposure fit + weighted L1 + colour gradient, pose-only backward, Adam and
+    the left update) is captured once and replayed; the loss epilogue is also timed alone."""
+    import torch
+    from paper_2601_00705_gb300.track import Tracker, poses_of
+
+    dev = r.device
+    V = len(cameras)
+    P = images[0].shape[0]
+    poses = poses_of(cameras).reshape(V, 3, 4).astype(np.float64)
+    a = 0.01
+    Rz = np.array([[np.cos(a), -np.sin(a), 0.0], [np.sin(a), np.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    start = np.concatenate([Rz @ poses[:, :, :3], (Rz @ poses[:, :, 3:]) + 0.01], 2)
+    tr = Tracker(r, cameras, images[0].clone(), world_to_cam=start.astype(np.float32).reshape(V, 12),
+                 lr=1e-3, iterations=40)
+    tr.step(*params)
+    torch.cuda.synchronize()
+    first = tr.loss.sum().item()
+    graph = tr.capture(*params)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    last = tr.loss.sum().item()
+    # The loss epilogue alone (exposure sums + loss and gradient): algorithmic bytes per pixel
+    # 24 (sums: rendered and observed colour) + 44 (loss: rendered and observed colour, opacity,
+    # gradient weight; colour gradient written).
+    color, alpha = tr.images[0], tr.images[2]
+    stream = r.stream_handle()
+    loop = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r.ctx.track_loss(tr.cams, tr.track_cfg, color.data_ptr(), alpha.data_ptr(),
+                         tr.observed.data_ptr(), tr.w_grad.data_ptr(), tr.d_color.data_ptr(),
+                         tr.loss.data_ptr(), tr.gain_bias.data_ptr(), stream)
+        e1.record()
+        e1.synchronize()
+        loop.append(e0.elapsed_time(e1))
+    epi_ms = float(np.median(loop))
+    epi_bytes = 68.0 * P
+    r.release(tr.state)
+    return {"ms_per_iteration": float(np.median(ms)), "views": V, "pixels": int(P),
+            "mpix_per_s": P / (float(np.median(ms)) * 1e3), "cuda_graph": True,
+            "loss_first": first, "loss_after": last, "iterations": steps + 4,
+            "loss_epilogue": {"us": epi_ms * 1e3, "bound": "hbm",
+                              "achieved": epi_bytes / (epi_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                              "unit": "GB/s",
+                              "frac": epi_bytes / (epi_ms * 1e-3) / 1e9 / hbm_peak,
+                              "bytes_per_pixel": 68}}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2601_00705_gb300 import binding, synthetic
@@ -545,6 +608,8 @@ def run_ours(args, world, rank, local):
         "counts": {"visible": stats["n_visible"], "pairs": stats["n_pairs"],
                    "evaluated": n_eval, "composited": n_contrib},
     }
+    line["tracking"] = measure_tracking(r, params, wl.cameras, images,
+                                        float(peaks.get("hbm_gbs", 6800.0)), args.steps, flush)
     if world == 1 and rank == 0:
         px, dt, threads, frac = oracle_sample(wl, list(range(V)))
         line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": threads,

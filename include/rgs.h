@@ -213,6 +213,83 @@ rgs_status rgs_reserve(rgs_ctx* ctx, uint64_t* state, int64_t pair_capacity, voi
 /* Reads the counters of the last forward on `state` (synchronises `stream`). */
 rgs_status rgs_query_stats(rgs_ctx* ctx, uint64_t state, rgs_stats* out, void* stream);
 
+/* ---- Tracking step (Section 3.2 and its appendix: Eq. app-bright, app-ls, app-trackloss,
+ * app-weight; Eq. leftupdate). One tracking iteration on the device, with no host round trip:
+ *   rgs_render_forward_posed -> rgs_track_loss -> rgs_render_backward (RGS_GRAD_POSE)
+ *   -> rgs_pose_adam_step, which updates the device poses the next forward reads.
+ * With the observation's gradient weights from rgs_track_grad_weight (once per frame), the
+ * iteration can be captured in a CUDA graph and replayed. ---- */
+
+/* rgs_render_forward with the world-to-camera poses taken from DEVICE memory:
+ *   world_to_cam: device [n_views][12] floats, row-major [R|t] as in rgs_camera (4-byte
+ *     aligned); read by this call's first kernel, so it may be updated (e.g. by
+ *     rgs_pose_adam_step) as soon as the call's work is queued; the backward uses the poses of
+ *     this forward. The poses in cams are ignored (sizes and intrinsics are used). NULL is
+ *     RGS_ERR_INVALID_ARG.
+ * Given the same pose values, the result is bit-identical to rgs_render_forward's. */
+rgs_status rgs_render_forward_posed(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                                    int32_t n_views, const float* world_to_cam,
+                                    const rgs_config* cfg, rgs_images* out, uint64_t* state,
+                                    void* stream);
+
+/* Loss constants (HOST struct); rgs_track_config_default fills the defaults shown. The paper
+ * fixes neither threshold. */
+typedef struct {
+  float tau_alpha;      /* 0.5: w_alpha = clip(alpha / tau_alpha, 0, 1) */
+  float tau_grad;       /* 0.05: w_grad = clip(||grad I||_2 / tau_grad, 0, 1) (intensities in [0, 1]) */
+  int32_t fit_exposure; /* 1: fit (g, b) per view by least squares (Eq. app-ls); 0: g = 1, b = 0 */
+} rgs_track_config;
+void rgs_track_config_default(rgs_track_config* cfg);
+
+/* Gradient weights of observed frames (Eq. app-weight): w[p] = clip(||grad I(p)||_2 / tau_grad,
+ * 0, 1), with grad I from central differences per channel (one-sided on the image border, zero
+ * along an axis of extent 1) and the norm over both axes and the three channels.
+ *   observed: device [P,3] (views concatenated as in rgs_images); w: device [P] output.
+ *   cams: HOST array (sizes are used). tau_grad > 0. */
+rgs_status rgs_track_grad_weight(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
+                                 const float* observed, float tau_grad, float* w, void* stream);
+
+/* Exposure-compensated, weighted L1 tracking loss of each view and its gradient with respect to
+ * the rendered colour (Eq. app-bright, app-ls, app-trackloss, app-weight):
+ *   (g_v, b_v) = argmin_{g,b} sum_{p in v} ||I(p) - g C(p) - b||_2^2   (closed form, FP64;
+ *                a constant render gives g = 1 and b matching the means)
+ *   loss[v]    = sum_{p in v} w(p) ||I(p) - (g_v C(p) + b_v)||_1,
+ *   w(p)       = clip(alpha(p) / tau_alpha, 0, 1) * w_grad(p)   (w_grad NULL: 1)
+ *   d_color(p) = -w(p) g_v sign(I(p) - g_v C(p) - b_v)   per channel (sign(0) = 0).
+ * (g, b) and w are held fixed in the gradient: they are re-estimated from every render.
+ *   cams: HOST array (sizes are used); cfg: HOST or NULL (defaults).
+ *   color [P,3], alpha [P]: a forward's outputs; observed [P,3]; w_grad [P] or NULL (device).
+ *   d_color [P,3]: device output, the upstream colour gradient for rgs_render_backward.
+ *   loss: device double [n_views]; gain_bias: device float [n_views][2] = (g, b).
+ * Uses a fixed scratch of the context: calls on one context whose executions overlap on the
+ * GPU race on it. Never synchronises; may be captured. */
+rgs_status rgs_track_loss(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
+                          const rgs_track_config* cfg, const float* color, const float* alpha,
+                          const float* observed, const float* w_grad, float* d_color,
+                          double* loss, float* gain_bias, void* stream);
+
+/* Adam constants (HOST struct); rgs_adam_config_default fills the defaults shown. */
+typedef struct {
+  float lr;           /* 5e-3: base learning rate */
+  float beta1, beta2; /* 0.9, 0.999 */
+  float eps;          /* 1e-8 */
+  int32_t iterations; /* K > 0: cosine schedule lr_k = lr (1 + cos(pi min(k, K) / K)) / 2 for
+                         step k = 0, 1, ...; 0: constant lr. Default 0 */
+} rgs_adam_config;
+void rgs_adam_config_default(rgs_adam_config* cfg);
+
+/* One Adam step on the twist of every view and the left update T <- exp(xi^) T (Eq. leftupdate),
+ * with xi = -lr_k mhat / (sqrt(vhat) + eps) from d_pose = dL/dxi at xi = 0 (rgs_render_backward's
+ * (rho, omega)), and the closed-form SE(3) exponential (R <- R_d R, t <- R_d t + V rho). FP64
+ * arithmetic; all arrays are DEVICE memory:
+ *   d_pose [n_views][6]; adam_state [n_views][12] = (m[6], v[6]), zero before the first step;
+ *   step: one int32, the number of steps taken (0 before the first), incremented;
+ *   world_to_cam [n_views][12], row-major [R|t], updated in place.
+ * Never synchronises; may be captured. */
+rgs_status rgs_pose_adam_step(rgs_ctx* ctx, int32_t n_views, const rgs_adam_config* cfg,
+                              const float* d_pose, float* adam_state, int32_t* step,
+                              float* world_to_cam, void* stream);
+
 /* Phases timed by rgs_phase_times, in this order. */
 #define RGS_PHASE_PREPROCESS 0     /* projection, SH colour, tile counts (Eq. proj, Eq. app-sh) */
 #define RGS_PHASE_COMPACT 1        /* visible (view, Gaussian) entries with depth keys */

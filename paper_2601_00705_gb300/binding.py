@@ -26,7 +26,9 @@ EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_render_forward", "rgs_render_backward", "rgs_release_state", "rgs_reserve",
             "rgs_query_stats", "rgs_set_phase_timing", "rgs_phase_times", "rgs_radix_sort_u32",
             "rgs_exclusive_scan_u32", "rgs_exclusive_scan_u32_static", "rgs_copy_tile_lists",
-            "rgs_copy_records", "rgs_autotune")
+            "rgs_copy_records", "rgs_autotune", "rgs_render_forward_posed",
+            "rgs_track_config_default", "rgs_adam_config_default", "rgs_track_grad_weight",
+            "rgs_track_loss", "rgs_pose_adam_step")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -61,6 +63,16 @@ class Images(ctypes.Structure):
 class ImageGrads(ctypes.Structure):
     _fields_ = [("d_color", ctypes.c_void_p), ("d_depth", ctypes.c_void_p),
                 ("d_alpha", ctypes.c_void_p)]
+
+
+class TrackConfig(ctypes.Structure):
+    _fields_ = [("tau_alpha", ctypes.c_float), ("tau_grad", ctypes.c_float),
+                ("fit_exposure", ctypes.c_int32)]
+
+
+class AdamConfig(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("iterations", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -113,6 +125,16 @@ def load(build_if_needed: bool = True):
             "rgs_copy_records": (S, [P, U64, P, P, P]),
             "rgs_autotune": (S, [P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), I32,
                                  ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float), P]),
+            "rgs_render_forward_posed": (S, [P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera),
+                                             I32, P, ctypes.POINTER(Config),
+                                             ctypes.POINTER(Images), ctypes.POINTER(U64), P]),
+            "rgs_track_config_default": (None, [ctypes.POINTER(TrackConfig)]),
+            "rgs_adam_config_default": (None, [ctypes.POINTER(AdamConfig)]),
+            "rgs_track_grad_weight": (S, [P, ctypes.POINTER(Camera), I32, P, ctypes.c_float, P,
+                                          P]),
+            "rgs_track_loss": (S, [P, ctypes.POINTER(Camera), I32, ctypes.POINTER(TrackConfig),
+                                   P, P, P, P, P, P, P, P]),
+            "rgs_pose_adam_step": (S, [P, I32, ctypes.POINTER(AdamConfig), P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -136,6 +158,22 @@ def default_config(**overrides) -> Config:
             cfg.bg = (ctypes.c_float * 3)(*[float(x) for x in v])
         else:
             setattr(cfg, k, v)
+    return cfg
+
+
+def default_track_config(**overrides) -> TrackConfig:
+    cfg = TrackConfig()
+    load().rgs_track_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def default_adam_config(**overrides) -> AdamConfig:
+    cfg = AdamConfig()
+    load().rgs_adam_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
     return cfg
 
 
@@ -192,6 +230,36 @@ class Context:
                                                 ctypes.byref(images), ctypes.byref(h),
                                                 ctypes.c_void_p(stream)))
         return h.value
+
+    def forward_posed(self, g: Gaussians, cams, world_to_cam: int, cfg: Config, images: Images,
+                      state: int, stream: int) -> int:
+        h = ctypes.c_uint64(state)
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        self._check(self.lib.rgs_render_forward_posed(
+            self.handle, ctypes.byref(g), cam_arr, len(cam_arr), ctypes.c_void_p(world_to_cam),
+            ctypes.byref(cfg), ctypes.byref(images), ctypes.byref(h), ctypes.c_void_p(stream)))
+        return h.value
+
+    def track_grad_weight(self, cams, observed: int, tau_grad: float, w: int, stream: int):
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        self._check(self.lib.rgs_track_grad_weight(self.handle, cam_arr, len(cam_arr),
+                                                   ctypes.c_void_p(observed), float(tau_grad),
+                                                   ctypes.c_void_p(w), ctypes.c_void_p(stream)))
+
+    def track_loss(self, cams, cfg: TrackConfig, color: int, alpha: int, observed: int,
+                   w_grad: int, d_color: int, loss: int, gain_bias: int, stream: int):
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_track_loss(self.handle, cam_arr, len(cam_arr), ctypes.byref(cfg),
+                                            P(color), P(alpha), P(observed), P(w_grad or None),
+                                            P(d_color), P(loss), P(gain_bias), P(stream)))
+
+    def pose_adam_step(self, n_views: int, cfg: AdamConfig, d_pose: int, adam_state: int,
+                       step: int, world_to_cam: int, stream: int):
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_pose_adam_step(self.handle, int(n_views), ctypes.byref(cfg),
+                                                P(d_pose), P(adam_state), P(step),
+                                                P(world_to_cam), P(stream)))
 
     def backward(self, state: int, grads: ImageGrads, grad_mask: int, d_means: int,
                  d_log_scales: int, d_quats: int, d_opacity_logits: int, d_sh: int, d_pose: int,

@@ -176,12 +176,12 @@ struct ViewProj {
 
 // Returns false if the Gaussian is culled in this view (behind znear or degenerate).
 __device__ __forceinline__ bool project_view(const GaussianLocal& g, const ViewParams& vp,
-                                             const Consts& c, ViewProj& p) {
-  const float* R = vp.R;
+                                             const PoseRef& ps, const Consts& c, ViewProj& p) {
+  const float* R = ps.R;
   float lo[3];
-  p.mc[0] = dot3_plus_dd(R[0], R[1], R[2], g.m[0], g.m[1], g.m[2], vp.t[0], lo[0]);
-  p.mc[1] = dot3_plus_dd(R[3], R[4], R[5], g.m[0], g.m[1], g.m[2], vp.t[1], lo[1]);
-  p.mc[2] = dot3_plus_dd(R[6], R[7], R[8], g.m[0], g.m[1], g.m[2], vp.t[2], lo[2]);
+  p.mc[0] = dot3_plus_dd(R[0], R[1], R[2], g.m[0], g.m[1], g.m[2], ps.t[0], lo[0]);
+  p.mc[1] = dot3_plus_dd(R[3], R[4], R[5], g.m[0], g.m[1], g.m[2], ps.t[1], lo[1]);
+  p.mc[2] = dot3_plus_dd(R[6], R[7], R[8], g.m[0], g.m[1], g.m[2], ps.t[2], lo[2]);
   const float z = p.mc[2];
   if (!(z > c.znear)) return false;
   const float rz = 1.0f / z;
@@ -330,15 +330,16 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
   const float kappa = finite ? 2.0f * logf(opacity / c.alpha_min) : -1.0f;
   for (int v = v_begin; v < v_end; ++v) {
     const ViewParams& vp = views.v[v];
+    const PoseRef ps = view_pose(views, v);
     const size_t vi = (size_t)v * n + i;
     bool keep = false;
     if (finite && kappa >= 0.0f) {
-      const float* R = vp.R;
+      const float* R = ps.R;
       float lo;
-      const float z = dot3_plus_dd(R[6], R[7], R[8], m[0], m[1], m[2], vp.t[2], lo);
+      const float z = dot3_plus_dd(R[6], R[7], R[8], m[0], m[1], m[2], ps.t[2], lo);
       if (z > c.znear) {
-        const float x = dot3_plus_dd(R[0], R[1], R[2], m[0], m[1], m[2], vp.t[0], lo);
-        const float y = dot3_plus_dd(R[3], R[4], R[5], m[0], m[1], m[2], vp.t[1], lo);
+        const float x = dot3_plus_dd(R[0], R[1], R[2], m[0], m[1], m[2], ps.t[0], lo);
+        const float y = dot3_plus_dd(R[3], R[4], R[5], m[0], m[1], m[2], ps.t[1], lo);
         const float rz = 1.0f / z;
         const float u = x * rz, w = y * rz;
         float uc = u, wc = w;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
 // Forward, pass 2 (project): one thread per candidate entry (grid-stride). Full projection
 // (Eq. proj), colour (Eq. app-sh) and tile count; writes the entry's records and tile count.
 // Entries that are not candidates keep ntiles = 0 and unwritten records.
-template <int DEG>
+template <int DEG, bool kDevPose>
 __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
@@ -414,15 +415,16 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     GaussianLocal g;
     gaussian_local(m, ls, q, __ldg(logits + i), g);
     const ViewParams& vp = views.v[v];
+    const PoseRef ps = view_pose<kDevPose>(views, v);
     ViewProj p;
-    if (!project_view(g, vp, c, p)) continue;
+    if (!project_view(g, vp, ps, c, p)) continue;
     const float4 r0 = make_float4(p.mean2d[0], p.mean2d[1], p.mean2d_lo[0], p.mean2d_lo[1]);
     const float4 r1 =
         make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
                     __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
     // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
-    float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
-          d2 = g.m[2] - vp.cam_center[2];
+    float d0 = g.m[0] - ps.c[0], d1 = g.m[1] - ps.c[1],
+          d2 = g.m[2] - ps.c[2];
     const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     d0 *= rn;
     d1 *= rn;
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
 // ------------------------------------------------------------------------------------------
 enum ViewSlot { kVMean = 0, kVSigma = 3, kVRgb = 9, kVOpacity = 12 };
 
-template <int DEG>
+template <int DEG, bool kDevPose>
 __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
@@ -496,6 +498,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     GaussianLocal g;
     gaussian_local(m, ls, q, __ldg(logits + i), g);
     const ViewParams& vp = views.v[v];
+    const PoseRef ps = view_pose<kDevPose>(views, v);
     float* gp = g2d + (size_t)vi * kG2Stride;
     const float4 ga = *reinterpret_cast<const float4*>(gp);
     const float4 gb = *reinterpret_cast<const float4*>(gp + 4);
@@ -504,8 +507,8 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const float mxy = gb.x, myy = gb.y, g_r = gb.z, g_g = gb.w;
     const float g_b = gc2.x, g_zo = gc2.y;
     ViewProj p;
-    project_view(g, vp, c, p);
-    const float* R = vp.R;
+    project_view(g, vp, ps, c, p);
+    const float* R = ps.R;
     const float a = p.conic[0], b = p.conic[1], cc = p.conic[2];
     // Screen-space gradients from the blend's moments: power = -1/2 (a dx^2 + 2 b dx dy +
     // c dy^2) with (dx, dy) = p - mu^I, alpha = o exp(power) (Section 3.1, Eq. alpha), so
@@ -563,8 +566,8 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     for (int a2 = 0; a2 < 3; ++a2)
       out[kVMean + a2] = R[a2] * gmc[0] + R[3 + a2] * gmc[1] + R[6 + a2] * gmc[2];
     // Colour: rgb = max(sum_k sh_k Y_k(dir) + 0.5, 0), dir = normalize(mu^W - c_W).
-    float d0 = g.m[0] - vp.cam_center[0], d1 = g.m[1] - vp.cam_center[1],
-          d2 = g.m[2] - vp.cam_center[2];
+    float d0 = g.m[0] - ps.c[0], d1 = g.m[1] - ps.c[1],
+          d2 = g.m[2] - ps.c[2];
     const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     d0 *= rn;
     d1 *= rn;
@@ -701,9 +704,9 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     gSw[5] += cur.r2.x;
     gop += cur.r3;
     if (grad_mask & RGS_GRAD_SH) {
-      const ViewParams& vp = views.v[v];
-      float d0 = m[0] - vp.cam_center[0], d1 = m[1] - vp.cam_center[1],
-            d2 = m[2] - vp.cam_center[2];
+      const PoseRef ps = view_pose(views, v);
+      float d0 = m[0] - ps.c[0], d1 = m[1] - ps.c[1],
+            d2 = m[2] - ps.c[2];
       const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
       float Y[16];
       sh_basis<DEG>(d0 * rn, d1 * rn, d2 * rn, Y);
@@ -832,10 +835,11 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   // Pass 2: grid-stride over the candidates.
   const int64_t vn = (int64_t)views.n_views * g.n;
   const int blocks2 = (int)std::min<int64_t>((vn + kPreThreads - 1) / kPreThreads, 16 * 152);
-#define RGS_PROJECT(D)                                                                         \
-  e = launch_chained(project_kernel<D>, dim3(blocks2), dim3(kPreThreads), stream, views, c, g.n, \
-                     g.means, g.log_scales, g.quats, g.opacity_logits, g.sh,                    \
-                     (const uint32_t*)cand, rec0, rec1, rec2, ntiles, counters)
+#define RGS_PROJECT(D)                                                                          \
+  e = launch_chained(views.pose_dev ? project_kernel<D, true> : project_kernel<D, false>,         \
+                     dim3(blocks2), dim3(kPreThreads), stream, views, c, g.n, g.means,            \
+                     g.log_scales, g.quats, g.opacity_logits, g.sh, (const uint32_t*)cand, rec0, \
+                     rec1, rec2, ntiles, counters)
   switch (g.sh_degree) {
     case 0: RGS_PROJECT(0); break;
     case 1: RGS_PROJECT(1); break;
@@ -864,10 +868,12 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
   const int blocks1 = preprocess_backward_blocks(vn);
   cudaError_t e = cudaSuccess;
   if (g.n > 0) {
-#define RGS_BWD_VIEW(D)                                                                       \
-  e = launch_chained(backward_view_kernel<D>, dim3(blocks1), dim3(kPreThreads), stream, views, \
-                     c, g.n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, order,    \
-                     counters, g2d, vis_mask, grad_mask, pose_partial)
+#define RGS_BWD_VIEW(D)                                                                          \
+  e = launch_chained(views.pose_dev ? backward_view_kernel<D, true>                               \
+                                    : backward_view_kernel<D, false>,                             \
+                     dim3(blocks1), dim3(kPreThreads), stream, views, c, g.n, g.means,            \
+                     g.log_scales, g.quats, g.opacity_logits, g.sh, order, counters, g2d,         \
+                     vis_mask, grad_mask, pose_partial)
     switch (g.sh_degree) {
       case 0: RGS_BWD_VIEW(0); break;
       case 1: RGS_BWD_VIEW(1); break;

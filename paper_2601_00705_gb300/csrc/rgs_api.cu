@@ -105,6 +105,7 @@ struct State {
   int64_t hist_cap = 0, sums_cap = 0;
   float* pose_partial = nullptr;
   Counters* counters = nullptr;
+  float* pose_records = nullptr;  // [kMaxViews][16] device poses of a posed forward
   // Phase timing: event k is recorded at the start (k = 0) / end of each forward phase, and
   // kEvBwd0 .. at the start / end of each backward phase.
   cudaEvent_t ev[kNumEvents] = {};
@@ -113,6 +114,20 @@ struct State {
 };
 
 }  // namespace
+
+namespace rgs {
+cudaError_t launch_pose_prepare(const float* world_to_cam, int n_views, float* records,
+                                cudaStream_t stream);
+cudaError_t launch_grad_weight(const Views& views, const float* obs, float tau_grad, float* w_out,
+                               cudaStream_t stream);
+cudaError_t launch_track_loss(const Views& views, const float* color, const float* alpha,
+                              const float* obs, const float* w_grad, float tau_alpha,
+                              bool fit_exposure, double* sums, float* d_color, double* loss,
+                              float* gain_bias, cudaStream_t stream);
+cudaError_t launch_pose_adam(int n_views, float lr, float beta1, float beta2, float eps,
+                             int iterations, const float* d_pose, float* adam_state,
+                             int32_t* step, float* world_to_cam, cudaStream_t stream);
+}  // namespace rgs
 
 struct TuneChoice {
   int tile_w, tile_h, ppt, bwd_ppt;
@@ -126,6 +141,7 @@ struct rgs_ctx {
   std::map<uint64_t, State*> states;
   uint64_t next_id = 1;
   Counters* host_counters = nullptr;  // pinned
+  double* track_sums = nullptr;       // device [kMaxViews][4]: exposure-fit sums
 };
 
 namespace {
@@ -450,6 +466,11 @@ rgs_status rgs_create(rgs_ctx** out, int device) {
     delete ctx;
     return RGS_ERR_NOMEM;
   }
+  if (cudaMalloc(&ctx->track_sums, sizeof(double) * 4 * kMaxViews) != cudaSuccess) {
+    cudaFreeHost(ctx->host_counters);
+    delete ctx;
+    return RGS_ERR_NOMEM;
+  }
   *out = ctx;
   return RGS_OK;
 }
@@ -461,6 +482,7 @@ void rgs_destroy(rgs_ctx* ctx) {
   for (auto& kv : ctx->states) destroy_state(kv.second);
   ctx->states.clear();
   if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
+  if (ctx->track_sums) cudaFree(ctx->track_sums);
   delete ctx;
 }
 
@@ -627,9 +649,34 @@ rgs_status rgs_reserve(rgs_ctx* ctx, uint64_t* handle, int64_t pair_capacity, vo
   return RGS_OK;
 }
 
+namespace {
+rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                          int32_t n_views, const float* world_to_cam, const rgs_config* cfg_in,
+                          rgs_images* out, uint64_t* handle, void* stream_ptr);
+}  // namespace
+
 rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
                               int32_t n_views, const rgs_config* cfg_in, rgs_images* out,
                               uint64_t* handle, void* stream_ptr) {
+  return render_forward(ctx, g, cams, n_views, nullptr, cfg_in, out, handle, stream_ptr);
+}
+
+rgs_status rgs_render_forward_posed(rgs_ctx* ctx, const rgs_gaussians* g,
+                                    const rgs_camera* cams, int32_t n_views,
+                                    const float* world_to_cam, const rgs_config* cfg_in,
+                                    rgs_images* out, uint64_t* handle, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  if (!world_to_cam) {
+    ctx->last_error = "world_to_cam is null";
+    return RGS_ERR_INVALID_ARG;
+  }
+  return render_forward(ctx, g, cams, n_views, world_to_cam, cfg_in, out, handle, stream_ptr);
+}
+
+namespace {
+rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* cams,
+                          int32_t n_views, const float* world_to_cam, const rgs_config* cfg_in,
+                          rgs_images* out, uint64_t* handle, void* stream_ptr) {
   if (!ctx) return RGS_ERR_INVALID_ARG;
   ctx->last_error.clear();
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
@@ -667,9 +714,14 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   if (st != RGS_OK) return st;
   if (!s->r_counters.base) {
     if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "state must be created outside capture");
-    RGS_CUDA(alloc_region(s->r_counters, sizeof(Counters)), "allocate counters");
+    RGS_CUDA(alloc_region(s->r_counters,
+                          align_up(sizeof(Counters)) + sizeof(float) * 16 * kMaxViews),
+             "allocate counters");
     s->counters = static_cast<Counters*>(s->r_counters.base);
+    s->pose_records = reinterpret_cast<float*>(static_cast<char*>(s->r_counters.base) +
+                                               align_up(sizeof(Counters)));
   }
+  if (world_to_cam) views.pose_dev = s->pose_records;
   s->g = *g;
   s->views = views;
   s->consts = consts;
@@ -682,6 +734,9 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   RGS_CUDA(cudaMemsetAsync(s->ranges, 0, sizeof(uint2) * (size_t)views.total_tiles, stream),
            "reset tile ranges");
   RGS_CUDA(mark(ctx, *s, 0, stream, capturing), "event");
+  // Device poses: records (R, t, camera centre) for the projection kernels and the backward.
+  if (world_to_cam)
+    RGS_CUDA(launch_pose_prepare(world_to_cam, n_views, s->pose_records, stream), "pose records");
 
   // 1. Projection.
   // The cull pass's candidate list lives in the depth sort's second key buffer, which is free
@@ -772,6 +827,7 @@ rgs_status rgs_render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_ca
   s->has_forward = true;
   return RGS_OK;
 }
+}  // namespace
 
 rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads* grads,
                                uint32_t grad_mask, float* d_means, float* d_log_scales,
@@ -982,3 +1038,91 @@ rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* ou
 }
 
 }  // extern "C"
+
+// ---- Tracking step ----
+
+void rgs_track_config_default(rgs_track_config* cfg) {
+  if (!cfg) return;
+  cfg->tau_alpha = 0.5f;
+  cfg->tau_grad = 0.05f;
+  cfg->fit_exposure = 1;
+}
+
+void rgs_adam_config_default(rgs_adam_config* cfg) {
+  if (!cfg) return;
+  cfg->lr = 5e-3f;
+  cfg->beta1 = 0.9f;
+  cfg->beta2 = 0.999f;
+  cfg->eps = 1e-8f;
+  cfg->iterations = 0;
+}
+
+rgs_status rgs_track_grad_weight(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
+                                 const float* observed, float tau_grad, float* w,
+                                 void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (!observed || !w) return fail(ctx, RGS_ERR_INVALID_ARG, "null image pointer");
+  if (!(tau_grad > 0.0f) || !std::isfinite(tau_grad))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "tau_grad must be positive");
+  rgs_config cfg;
+  rgs_config_default(&cfg);
+  Views views;
+  Consts consts;
+  rgs_status st = build_views(ctx, cams, n_views, cfg, views, consts);
+  if (st != RGS_OK) return st;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_grad_weight(views, observed, tau_grad, w, static_cast<cudaStream_t>(stream_ptr)),
+           "gradient weights");
+  return RGS_OK;
+}
+
+rgs_status rgs_track_loss(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
+                          const rgs_track_config* tcfg_in, const float* color,
+                          const float* alpha, const float* observed, const float* w_grad,
+                          float* d_color, double* loss, float* gain_bias, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (!color || !alpha || !observed || !d_color || !loss || !gain_bias)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null pointer");
+  rgs_track_config tcfg;
+  if (tcfg_in) tcfg = *tcfg_in; else rgs_track_config_default(&tcfg);
+  if (!(tcfg.tau_alpha > 0.0f) || !std::isfinite(tcfg.tau_alpha))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "tau_alpha must be positive");
+  rgs_config cfg;
+  rgs_config_default(&cfg);
+  Views views;
+  Consts consts;
+  rgs_status st = build_views(ctx, cams, n_views, cfg, views, consts);
+  if (st != RGS_OK) return st;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_track_loss(views, color, alpha, observed, w_grad, tcfg.tau_alpha,
+                             tcfg.fit_exposure != 0, ctx->track_sums, d_color, loss, gain_bias,
+                             static_cast<cudaStream_t>(stream_ptr)),
+           "tracking loss");
+  return RGS_OK;
+}
+
+rgs_status rgs_pose_adam_step(rgs_ctx* ctx, int32_t n_views, const rgs_adam_config* acfg_in,
+                              const float* d_pose, float* adam_state, int32_t* step,
+                              float* world_to_cam, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n_views < 1 || n_views > kMaxViews)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n_views must be in 1..RGS_MAX_VIEWS");
+  if (!d_pose || !adam_state || !step || !world_to_cam)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null pointer");
+  rgs_adam_config a;
+  if (acfg_in) a = *acfg_in; else rgs_adam_config_default(&a);
+  if (!(a.lr >= 0.0f) || !std::isfinite(a.lr) || !(a.beta1 >= 0.0f && a.beta1 < 1.0f) ||
+      !(a.beta2 >= 0.0f && a.beta2 < 1.0f) || !(a.eps > 0.0f) || a.iterations < 0)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "Adam constants out of range");
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_pose_adam(n_views, a.lr, a.beta1, a.beta2, a.eps, a.iterations, d_pose,
+                            adam_state, step, world_to_cam, static_cast<cudaStream_t>(stream_ptr)),
+           "pose update");
+  return RGS_OK;
+}

@@ -54,8 +54,39 @@ struct Views {
   int tile_w, tile_h;
   int pixels_per_thread;    // vertically adjacent pixels per forward-blend thread
   int bwd_pixels_per_thread;  // the same for the backward blend
+  // Device pose records [n_views][16] = R (9, row-major), t (3), c = -R^T t (3), pad; when set,
+  // they replace the poses in v[] (a pose that lives on the device, e.g. one a tracking loop
+  // updates without the host). Null: the poses in v[].
+  const float* pose_dev;
   ViewParams v[kMaxViews];
 };
+
+// The pose of view v that the launch uses: R (row-major), t and the camera centre.
+struct PoseRef {
+  const float* R;
+  const float* t;
+  const float* c;
+};
+__device__ __forceinline__ PoseRef view_pose(const Views& views, int v) {
+  if (views.pose_dev) {
+    const float* p = views.pose_dev + 16 * v;
+    return PoseRef{p, p + 9, p + 12};
+  }
+  const ViewParams& vp = views.v[v];
+  return PoseRef{vp.R, vp.t, vp.cam_center};
+}
+// The same with the pose's location fixed at compile time (kDevice: the device records), for
+// kernels whose host-pose variant should read the parameter block directly.
+template <bool kDevice>
+__device__ __forceinline__ PoseRef view_pose(const Views& views, int v) {
+  if constexpr (kDevice) {
+    const float* p = views.pose_dev + 16 * v;
+    return PoseRef{p, p + 9, p + 12};
+  } else {
+    const ViewParams& vp = views.v[v];
+    return PoseRef{vp.R, vp.t, vp.cam_center};
+  }
+}
 
 struct Consts {
   float alpha_min, alpha_max, t_min, znear, eps2d;
