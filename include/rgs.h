@@ -343,6 +343,72 @@ rgs_status rgs_radix_sort_u32(rgs_ctx* ctx, uint32_t* keys, uint32_t* vals, int6
 rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                                   uint32_t* total_out, void* stream);
 
+/* ---- Dense initialisation (Section 3.3 "Multi-view Triangulation" and "Gaussian Parameter
+ * Initialization"; appendix "Gaussian Initialization and Joint Mapping", Eq. app-sigma-init,
+ * Eq. app-alpha-init). Matched pixels of a keyframe window become Gaussian seeds: a two-view
+ * DLT in double precision per (reference pixel, neighbour), the best hypothesis per pixel, then
+ * one seed per accepted point. The paper fixes none of the constants below. ---- */
+typedef struct {
+  float min_parallax; /* radians: smallest baseline angle of an accepted hypothesis; 1 degree */
+  float max_reproj;   /* pixels: largest RMS reprojection error over the two views; 2 */
+  float tie_eps;      /* pixels: errors within this of the lowest are ties (larger angle wins); 1e-3 */
+  float plane_radius; /* world units: neighbourhood of the plane fit for the normal; 0.05 */
+  float s_par_cap;    /* s_par <= s_par_cap * s_perp; 10 */
+  float alpha_lo;     /* opacity = alpha_lo + (alpha_hi - alpha_lo) * kappa_bar; 0.1 */
+  float alpha_hi;     /* 0.9 */
+  float voxel;        /* world units: keep one seed per cube of this edge; 0 = keep all (default) */
+} rgs_seed_config;
+void rgs_seed_config_default(rgs_seed_config* cfg);
+
+/* Two-view linear triangulation of m reference pixels against up to k (1..8) neighbours each:
+ *   A = [x_r P_r^3 - P_r^1; y_r P_r^3 - P_r^2; x_n P_n^3 - P_n^1; y_n P_n^3 - P_n^2],
+ *   X~ = argmin_{|X~| = 1} |A X~| (smallest right singular vector, one-sided Jacobi in FP64),
+ *   X = X~[0:3] / X~[3], P = K [R | t] of each view.
+ * A hypothesis is accepted if X is in front of both cameras, the angle between the two rays at X
+ * is at least min_parallax and the RMS reprojection error over the two views is at most
+ * max_reproj; the lowest error wins, errors within tie_eps of it are ties decided by the larger
+ * angle, then the lower neighbour slot.
+ *   cams: HOST array of n_views cameras (intrinsics and poses); cfg: HOST or NULL (defaults).
+ *   DEVICE arrays: ref_view [m] int32, ref_xy [m][2] double (pixel (x, y) at (x, y)),
+ *     nb_view [m][k] int32 (-1 or out of range: no match), nb_xy [m][k][2] double,
+ *     nb_conf [m][k] float (per-match confidence in [0, 1]);
+ *   outputs: valid [m] u32 (1 accepted), X [m][3] double, best [m] int32 (slot, -1),
+ *     err [m] double (pixels), angle [m] double (radians), kappa [m] float (mean confidence of
+ *     the matches, Eq. conf).
+ * Never synchronises; may be captured. */
+rgs_status rgs_triangulate(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views, int64_t m,
+                           int32_t k, const int32_t* ref_view, const double* ref_xy,
+                           const int32_t* nb_view, const double* nb_xy, const float* nb_conf,
+                           const rgs_seed_config* cfg, uint32_t* valid, double* X, int32_t* best,
+                           double* err, double* angle, float* kappa, void* stream);
+
+/* Gaussian seeds of the accepted points of rgs_triangulate (same m, k, views and arrays):
+ *   mean = X; normal v = eigenvector of the smallest eigenvalue of the covariance of the
+ *   accepted points within plane_radius of X (FP64 Jacobi), turned towards the reference camera
+ *   (fewer than 3 points: the direction to the reference camera); rotation [t1, t2, v] (the
+ *   tangent frame of Duff et al. 2017) as a quaternion (w, x, y, z), w >= 0; scales
+ *   (s_perp, s_perp, s_par) with s_perp = det(J J^T)^(-1/4) for the projection Jacobian J at X
+ *   in the reference view and s_par = min(s_perp (1 + err / 1 px) / sin(angle), s_par_cap s_perp)
+ *   (Eq. app-sigma-init); opacity alpha_lo + (alpha_hi - alpha_lo) kappa as a logit
+ *   (Eq. app-alpha-init); colour = per-channel median of the exposure-corrected bilinear samples
+ *   (I - b) / g over the reference and matched views where X projects inside (SH DC
+ *   (c - 0.5) / Y_0, higher orders 0); then, if voxel > 0, one seed per cube of edge voxel
+ *   (highest kappa, then lowest index).
+ *   observed: DEVICE [P][3] frames (views concatenated as in rgs_images); gain_bias: DEVICE
+ *     [n_views][2] exposure (g, b) of each view; sh_degree 0..3.
+ *   outputs (DEVICE, capacity m seeds, in increasing reference-pixel order): index [m] int32
+ *     (the reference pixel of each seed), means [m][3], log_scales [m][3], quats [m][4],
+ *     opacity_logits [m], sh [m][K][3], normals [m][3]; n_seeds: HOST, the number written.
+ * Allocates and frees device scratch and synchronises `stream`; not for stream capture. */
+rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views, int64_t m,
+                          int32_t k, const int32_t* ref_view, const int32_t* nb_view,
+                          const uint32_t* valid, const double* X, const double* err,
+                          const double* angle, const float* kappa, const float* observed,
+                          const float* gain_bias, int32_t sh_degree, const rgs_seed_config* cfg,
+                          int32_t* index, float* means, float* log_scales, float* quats,
+                          float* opacity_logits, float* sh, float* normals, int64_t* n_seeds,
+                          void* stream);
+
 /* ---- Allocation-free variant (the paper has no counterpart: this serves library users). ----
  *
  * rgs_exclusive_scan_u32_static computes exactly what rgs_exclusive_scan_u32 computes, but

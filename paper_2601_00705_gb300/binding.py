@@ -28,7 +28,8 @@ EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_exclusive_scan_u32", "rgs_exclusive_scan_u32_static", "rgs_copy_tile_lists",
             "rgs_copy_records", "rgs_autotune", "rgs_render_forward_posed",
             "rgs_track_config_default", "rgs_adam_config_default", "rgs_track_grad_weight",
-            "rgs_track_loss", "rgs_pose_adam_step")
+            "rgs_track_loss", "rgs_pose_adam_step", "rgs_seed_config_default", "rgs_triangulate",
+            "rgs_init_seeds")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -73,6 +74,13 @@ class TrackConfig(ctypes.Structure):
 class AdamConfig(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("iterations", ctypes.c_int32)]
+
+
+class SeedConfig(ctypes.Structure):
+    _fields_ = [("min_parallax", ctypes.c_float), ("max_reproj", ctypes.c_float),
+                ("tie_eps", ctypes.c_float), ("plane_radius", ctypes.c_float),
+                ("s_par_cap", ctypes.c_float), ("alpha_lo", ctypes.c_float),
+                ("alpha_hi", ctypes.c_float), ("voxel", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):
@@ -135,6 +143,12 @@ def load(build_if_needed: bool = True):
             "rgs_track_loss": (S, [P, ctypes.POINTER(Camera), I32, ctypes.POINTER(TrackConfig),
                                    P, P, P, P, P, P, P, P]),
             "rgs_pose_adam_step": (S, [P, I32, ctypes.POINTER(AdamConfig), P, P, P, P, P]),
+            "rgs_seed_config_default": (None, [ctypes.POINTER(SeedConfig)]),
+            "rgs_triangulate": (S, [P, ctypes.POINTER(Camera), I32, I64, I32, P, P, P, P, P,
+                                    ctypes.POINTER(SeedConfig), P, P, P, P, P, P, P]),
+            "rgs_init_seeds": (S, [P, ctypes.POINTER(Camera), I32, I64, I32, P, P, P, P, P, P, P,
+                                   P, P, I32, ctypes.POINTER(SeedConfig), P, P, P, P, P, P, P,
+                                   ctypes.POINTER(I64), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -172,6 +186,14 @@ def default_track_config(**overrides) -> TrackConfig:
 def default_adam_config(**overrides) -> AdamConfig:
     cfg = AdamConfig()
     load().rgs_adam_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def default_seed_config(**overrides) -> SeedConfig:
+    cfg = SeedConfig()
+    load().rgs_seed_config_default(ctypes.byref(cfg))
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg
@@ -260,6 +282,34 @@ class Context:
         self._check(self.lib.rgs_pose_adam_step(self.handle, int(n_views), ctypes.byref(cfg),
                                                 P(d_pose), P(adam_state), P(step),
                                                 P(world_to_cam), P(stream)))
+
+    def triangulate(self, cams, m: int, k: int, ptrs: dict, cfg: SeedConfig, stream: int):
+        """ptrs: device pointers ref_view, ref_xy, nb_view, nb_xy, nb_conf (inputs) and valid, X,
+        best, err, angle, kappa (outputs)."""
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_triangulate(
+            self.handle, cam_arr, len(cam_arr), int(m), int(k), P(ptrs["ref_view"]),
+            P(ptrs["ref_xy"]), P(ptrs["nb_view"]), P(ptrs["nb_xy"]), P(ptrs["nb_conf"]),
+            ctypes.byref(cfg), P(ptrs["valid"]), P(ptrs["X"]), P(ptrs["best"]), P(ptrs["err"]),
+            P(ptrs["angle"]), P(ptrs["kappa"]), P(stream)))
+
+    def init_seeds(self, cams, m: int, k: int, ptrs: dict, sh_degree: int, cfg: SeedConfig,
+                   stream: int) -> int:
+        """ptrs: device pointers ref_view, nb_view, valid, X, err, angle, kappa, observed,
+        gain_bias (inputs) and index, means, log_scales, quats, opacity_logits, sh, normals
+        (outputs, capacity m). Returns the number of seeds written."""
+        cam_arr = cams if isinstance(cams, ctypes.Array) else make_cameras(cams)
+        P = ctypes.c_void_p
+        n = ctypes.c_int64(0)
+        self._check(self.lib.rgs_init_seeds(
+            self.handle, cam_arr, len(cam_arr), int(m), int(k), P(ptrs["ref_view"]),
+            P(ptrs["nb_view"]), P(ptrs["valid"]), P(ptrs["X"]), P(ptrs["err"]), P(ptrs["angle"]),
+            P(ptrs["kappa"]), P(ptrs["observed"]), P(ptrs["gain_bias"]), int(sh_degree),
+            ctypes.byref(cfg), P(ptrs["index"]), P(ptrs["means"]), P(ptrs["log_scales"]),
+            P(ptrs["quats"]), P(ptrs["opacity_logits"]), P(ptrs["sh"]), P(ptrs["normals"]),
+            ctypes.byref(n), P(stream)))
+        return int(n.value)
 
     def backward(self, state: int, grads: ImageGrads, grad_mask: int, d_means: int,
                  d_log_scales: int, d_quats: int, d_opacity_logits: int, d_sh: int, d_pose: int,

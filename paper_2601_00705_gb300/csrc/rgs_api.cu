@@ -1126,3 +1126,193 @@ rgs_status rgs_pose_adam_step(rgs_ctx* ctx, int32_t n_views, const rgs_adam_conf
            "pose update");
   return RGS_OK;
 }
+
+// ---- Dense initialisation ----
+
+void rgs_seed_config_default(rgs_seed_config* cfg) {
+  if (!cfg) return;
+  cfg->min_parallax = (float)(M_PI / 180.0);
+  cfg->max_reproj = 2.0f;
+  cfg->tie_eps = 1e-3f;
+  cfg->plane_radius = 0.05f;
+  cfg->s_par_cap = 10.0f;
+  cfg->alpha_lo = 0.1f;
+  cfg->alpha_hi = 0.9f;
+  cfg->voxel = 0.0f;
+}
+
+namespace {
+
+rgs_status seed_setup(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
+                      const rgs_seed_config* cfg_in, SeedCams& sc, SeedConsts& c) {
+  if (!cams) return fail(ctx, RGS_ERR_INVALID_ARG, "cams is null");
+  if (n_views < 1 || n_views > kMaxViews)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n_views must be in 1..RGS_MAX_VIEWS");
+  rgs_seed_config cfg;
+  if (cfg_in) cfg = *cfg_in; else rgs_seed_config_default(&cfg);
+  if (!(cfg.min_parallax >= 0.0f) || !(cfg.max_reproj > 0.0f) || !(cfg.tie_eps >= 0.0f) ||
+      !(cfg.plane_radius > 0.0f) || !(cfg.s_par_cap >= 1.0f) || !(cfg.alpha_lo > 0.0f) ||
+      !(cfg.alpha_hi < 1.0f) || !(cfg.alpha_lo <= cfg.alpha_hi) || !(cfg.voxel >= 0.0f) ||
+      !std::isfinite(cfg.plane_radius) || !std::isfinite(cfg.voxel))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "seed config values out of range");
+  std::memset(&sc, 0, sizeof(sc));
+  sc.n_views = n_views;
+  long long pix = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const rgs_camera& cm = cams[v];
+    if (cm.width < 1 || cm.height < 1 || cm.width > 16384 || cm.height > 16384 ||
+        !(cm.fx > 0.0f) || !(cm.fy > 0.0f))
+      return fail(ctx, RGS_ERR_INVALID_ARG, "camera size or intrinsics invalid");
+    sc.pixel_offset[v] = pix;
+    sc.width[v] = cm.width;
+    sc.height[v] = cm.height;
+    sc.fx[v] = cm.fx;
+    sc.fy[v] = cm.fy;
+    sc.cx[v] = cm.cx;
+    sc.cy[v] = cm.cy;
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) sc.R[v][3 * a + b] = cm.world_to_cam[4 * a + b];
+      sc.t[v][a] = cm.world_to_cam[4 * a + 3];
+    }
+    for (int j = 0; j < 4; ++j) {
+      const double r0 = j < 3 ? sc.R[v][j] : sc.t[v][0];
+      const double r1 = j < 3 ? sc.R[v][3 + j] : sc.t[v][1];
+      const double r2 = j < 3 ? sc.R[v][6 + j] : sc.t[v][2];
+      sc.P[v][j] = sc.fx[v] * r0 + sc.cx[v] * r2;
+      sc.P[v][4 + j] = sc.fy[v] * r1 + sc.cy[v] * r2;
+      sc.P[v][8 + j] = r2;
+    }
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < 3; ++b) s -= sc.R[v][3 * b + a] * sc.t[v][b];
+      sc.c[v][a] = s;
+    }
+    pix += (long long)cm.width * cm.height;
+  }
+  c.min_parallax = cfg.min_parallax;
+  c.max_reproj = cfg.max_reproj;
+  c.tie_eps = cfg.tie_eps;
+  c.plane_radius = cfg.plane_radius;
+  c.s_par_cap = cfg.s_par_cap;
+  c.alpha_lo = cfg.alpha_lo;
+  c.alpha_hi = cfg.alpha_hi;
+  c.voxel = cfg.voxel;
+  return RGS_OK;
+}
+
+}  // namespace
+
+rgs_status rgs_triangulate(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views, int64_t m,
+                           int32_t k, const int32_t* ref_view, const double* ref_xy,
+                           const int32_t* nb_view, const double* nb_xy, const float* nb_conf,
+                           const rgs_seed_config* cfg, uint32_t* valid, double* X, int32_t* best,
+                           double* err, double* angle, float* kappa, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (m < 0 || m >= (1ll << 31) || k < 1 || k > 8)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "m must be in 0..2^31-1 and k in 1..8");
+  if (m > 0 && (!ref_view || !ref_xy || !nb_view || !nb_xy || !nb_conf || !valid || !X || !best ||
+                !err || !angle || !kappa))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null array");
+  SeedCams sc;
+  SeedConsts c;
+  rgs_status st = seed_setup(ctx, cams, n_views, cfg, sc, c);
+  if (st != RGS_OK) return st;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_triangulate(sc, c, m, k, ref_view, ref_xy, nb_view, nb_xy, nb_conf, valid, X,
+                              best, err, angle, kappa, static_cast<cudaStream_t>(stream_ptr)),
+           "triangulate");
+  return RGS_OK;
+}
+
+rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views, int64_t m,
+                          int32_t k, const int32_t* ref_view, const int32_t* nb_view,
+                          const uint32_t* valid, const double* X, const double* err,
+                          const double* angle, const float* kappa, const float* observed,
+                          const float* gain_bias, int32_t sh_degree, const rgs_seed_config* cfg,
+                          int32_t* index, float* means, float* log_scales, float* quats,
+                          float* opacity_logits, float* sh, float* normals, int64_t* n_seeds,
+                          void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (!n_seeds) return fail(ctx, RGS_ERR_INVALID_ARG, "n_seeds is null");
+  *n_seeds = 0;
+  if (m < 0 || m >= (1ll << 31) || k < 1 || k > 8 || sh_degree < 0 || sh_degree > 3)
+    return fail(ctx, RGS_ERR_INVALID_ARG, "m, k or sh_degree out of range");
+  if (m > 0 && (!ref_view || !nb_view || !valid || !X || !err || !angle || !kappa || !observed ||
+                !gain_bias || !index || !means || !log_scales || !quats || !opacity_logits ||
+                !sh || !normals))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null array");
+  SeedCams sc;
+  SeedConsts c;
+  rgs_status st = seed_setup(ctx, cams, n_views, cfg, sc, c);
+  if (st != RGS_OK) return st;
+  if (m == 0) return RGS_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  const int sh_k = (sh_degree + 1) * (sh_degree + 1);
+  const int64_t hist = sort_hist_entries(m);
+  const int64_t sums = std::max(scan_blocks(hist), scan_blocks(m)) + 1;
+  const size_t bytes = 12 * align_up(sizeof(uint32_t) * m) + align_up(sizeof(uint32_t) * hist) +
+                       align_up(sizeof(uint32_t) * sums) + align_up(sizeof(uint64_t) * m) +
+                       align_up(sizeof(double) * 3 * m) +
+                       align_up(sizeof(float) * (size_t)m * (3 + 3 + 4 + 1 + 3 + 3 * sh_k));
+  char* base = nullptr;
+  RGS_CUDA(cudaMalloc(&base, bytes), "allocate seeding scratch");
+  char* p = base;
+  uint32_t* flags = carve<uint32_t>(p, m);
+  uint32_t* pos = carve<uint32_t>(p, m);
+  uint32_t* vidx = carve<uint32_t>(p, m);
+  uint32_t* lo = carve<uint32_t>(p, m);
+  uint32_t* hi = carve<uint32_t>(p, m);
+  uint32_t* slot = carve<uint32_t>(p, m);
+  uint32_t* t0 = carve<uint32_t>(p, m);
+  uint32_t* t1 = carve<uint32_t>(p, m);
+  uint32_t* keep = carve<uint32_t>(p, m);
+  uint32_t* kpos = carve<uint32_t>(p, m);
+  uint32_t* totals = carve<uint32_t>(p, m);  // [0]: accepted points, [1]: kept seeds
+  carve<uint32_t>(p, m);                     // spare
+  uint32_t* h = carve<uint32_t>(p, hist);
+  uint32_t* bs = carve<uint32_t>(p, sums);
+  unsigned long long* skey = carve<unsigned long long>(p, m);
+  double* sX = carve<double>(p, 3 * m);
+  float* f_means = carve<float>(p, 3 * m);
+  float* f_ls = carve<float>(p, 3 * m);
+  float* f_q = carve<float>(p, 4 * m);
+  float* f_o = carve<float>(p, m);
+  float* f_n = carve<float>(p, 3 * m);
+  float* f_sh = carve<float>(p, 3 * sh_k * m);
+  rgs_status result = RGS_OK;
+  uint32_t host_tot[2] = {0, 0};
+  do {
+    cudaError_t e = launch_seed_flags(m, n_views, valid, ref_view, flags, stream);
+    if (e == cudaSuccess) e = launch_exclusive_scan(flags, pos, m, nullptr, totals, bs, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_tot, totals, sizeof(uint32_t),
+                                              cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) { result = cuda_fail(ctx, e, "seed compaction"); break; }
+    const int s = (int)host_tot[0];
+    e = launch_compact_points(m, flags, pos, vidx, stream);
+    if (e == cudaSuccess)
+      e = launch_seed_points(sc, c, s, k, sh_k, vidx, ref_view, nb_view, X, err, angle, kappa,
+                             observed, gain_bias, lo, hi, slot, t0, t1, h, bs, skey, sX, f_means,
+                             f_ls, f_q, f_o, f_sh, f_n, keep, stream);
+    if (e == cudaSuccess && s > 0)
+      e = launch_exclusive_scan(keep, kpos, s, nullptr, totals + 1, bs, stream);
+    if (e == cudaSuccess && s > 0)
+      e = cudaMemcpyAsync(host_tot + 1, totals + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                          stream);
+    if (e == cudaSuccess)
+      e = launch_scatter_seeds(s, sh_k, keep, kpos, vidx, f_means, f_ls, f_q, f_o, f_sh, f_n,
+                               index, means, log_scales, quats, opacity_logits, sh, normals,
+                               stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) { result = cuda_fail(ctx, e, "seed initialisation"); break; }
+    *n_seeds = s > 0 ? (int64_t)host_tot[1] : 0;
+  } while (false);
+  cudaStreamSynchronize(stream);
+  cudaFree(base);
+  return result;
+}

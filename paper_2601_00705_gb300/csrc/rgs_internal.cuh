@@ -462,6 +462,49 @@ inline int64_t sort_hist_entries(int64_t n_cap, int items = kSortItems) {
   return (sort_blocks(n_cap, items) + 1) * kRadixBins;
 }
 
+// Per-view camera data in double precision (built on the host from the float cameras).
+struct SeedCams {
+  int n_views;
+  int pad;
+  long long pixel_offset[kMaxViews];
+  int width[kMaxViews], height[kMaxViews];
+  double P[kMaxViews][12];   // K [R | t], row-major 3x4
+  double R[kMaxViews][9];
+  double t[kMaxViews][3];
+  double c[kMaxViews][3];    // camera centre -R^T t
+  double fx[kMaxViews], fy[kMaxViews], cx[kMaxViews], cy[kMaxViews];
+};
+
+struct SeedConsts {
+  double min_parallax, max_reproj, tie_eps, plane_radius, s_par_cap, alpha_lo, alpha_hi, voxel;
+};
+
+cudaError_t launch_triangulate(const SeedCams& cams, const SeedConsts& c, int64_t m, int k,
+                               const int32_t* ref_view, const double* ref_xy,
+                               const int32_t* nb_view, const double* nb_xy, const float* nb_conf,
+                               uint32_t* valid, double* X, int32_t* best, double* err,
+                               double* angle, float* kappa, cudaStream_t stream);
+cudaError_t launch_seed_flags(int64_t m, int n_views, const uint32_t* valid,
+                              const int32_t* ref_view, uint32_t* flags, cudaStream_t stream);
+cudaError_t launch_compact_points(int64_t m, const uint32_t* valid, const uint32_t* pos,
+                                  uint32_t* vidx, cudaStream_t stream);
+cudaError_t launch_seed_points(const SeedCams& cams, const SeedConsts& c, int s, int k, int sh_k,
+                               const uint32_t* vidx, const int32_t* ref_view,
+                               const int32_t* nb_view, const double* X, const double* err,
+                               const double* angle, const float* kappa, const float* obs,
+                               const float* gain_bias, uint32_t* lo, uint32_t* hi,
+                               uint32_t* slot, uint32_t* t0, uint32_t* t1, uint32_t* hist,
+                               uint32_t* block_sums, unsigned long long* skey, double* sX,
+                               float* means, float* log_scales, float* quats, float* logits,
+                               float* sh, float* normals, uint32_t* keep, cudaStream_t stream);
+cudaError_t launch_scatter_seeds(int s, int sh_k, const uint32_t* keep, const uint32_t* pos,
+                                 const uint32_t* vidx, const float* means,
+                                 const float* log_scales, const float* quats,
+                                 const float* logits, const float* sh, const float* normals,
+                                 int32_t* o_index, float* o_means, float* o_log_scales,
+                                 float* o_quats, float* o_logits, float* o_sh, float* o_normals,
+                                 cudaStream_t stream);
+
 // Largest n the single-cluster sort takes on `device` (0: cluster launches unavailable); sorts
 // with n_cap up to it run as one launch and always return their result in the alternate buffers.
 int64_t cluster_sort_capacity(int device);

@@ -31,7 +31,8 @@ import numpy as np
 ROOM = np.array([6.0, 5.0, 3.0])
 
 WORKLOADS = ("tiny", "replica", "tum", "uneven", "large")
-SEEDS = dict(tiny=1001, replica=1002, tum=1003, uneven=1004, large=1005, crowded=1006)
+SEEDS = dict(tiny=1001, replica=1002, tum=1003, uneven=1004, large=1005, crowded=1006,
+             seeding=1007)
 
 # Intrinsics per resolution: TUM RGB-D (640x480) and half of it, Replica (1200x680), 1080p.
 INTRINSICS = {
@@ -309,3 +310,96 @@ def patch_mask(cameras, fraction=0.1, patch=16, seed=3001) -> np.ndarray:
         m = np.kron(sel, np.ones((patch, patch), dtype=bool))[:H, :W]
         masks.append(m.reshape(-1))
     return np.concatenate(masks)
+
+
+# ------------------------------------------------------------------------------------------
+# Correspondences for the dense initialisation (the stand-in for matched keyframes): ground-truth
+# surface points of the TUM-shaped room seen from a window of keyframes, their pixels in a
+# reference view and in up to K neighbour views with Gaussian pixel noise, a share of outlier
+# matches at random pixels, per-match confidences (inliers high, outliers low), observed frames
+# with a smooth colour pattern per view and a per-view exposure (gain, bias).
+# ------------------------------------------------------------------------------------------
+@dataclass
+class Correspondences:
+    cameras: list
+    ref_view: np.ndarray      # [M] int32
+    ref_xy: np.ndarray        # [M,2] float64
+    nb_view: np.ndarray       # [M,K] int32, -1: no match
+    nb_xy: np.ndarray         # [M,K,2] float64
+    nb_conf: np.ndarray       # [M,K] float32
+    observed: np.ndarray      # [P,3] float32
+    gain_bias: np.ndarray     # [V,2] float32
+    points: np.ndarray        # [M,3] ground truth
+
+
+def correspondences(seed=SEEDS["seeding"], m=2048, k=4, n_views=10, noise_px=0.3,
+                    outlier_frac=0.05, width=640, height=480) -> Correspondences:
+    rng = np.random.default_rng(seed)
+    cams = tum(seed=SEEDS["tum"], n=16, n_views=n_views).cameras
+    cams = [camera(width, height, *INTRINSICS[(640, 480)][:2],
+                   (width - 1) / 2.0, (height - 1) / 2.0, c["R"], c["t"]) for c in cams]
+    centres, radii = _sample_spheres(np.random.default_rng(SEEDS["tum"]), 20, 0.2, 0.6)
+
+    def pix(v, X):  # pixels of points X [N,3] in view v and whether they are usable
+        cam = cams[v]
+        xc = X @ cam["R"].astype(np.float64).T + cam["t"].astype(np.float64)
+        z = np.where(xc[:, 2] > 0.05, xc[:, 2], 1.0)
+        uv = np.stack([cam["fx"] * xc[:, 0] / z + cam["cx"], cam["fy"] * xc[:, 1] / z + cam["cy"]], 1)
+        ok = ((xc[:, 2] > 0.05) & (uv[:, 0] >= 1.0) & (uv[:, 0] <= width - 2.0)
+              & (uv[:, 1] >= 1.0) & (uv[:, 1] <= height - 2.0))
+        return uv, ok
+
+    chunks = []
+    have = 0
+    while have < m:
+        N = 4 * (m - have) + 64
+        X = _surface_points(rng, N, centres, radii, jitter=0.0)[0].astype(np.float64)
+        r = rng.integers(n_views, size=N)
+        xr = np.zeros((N, 2))
+        okr = np.zeros(N, bool)
+        for v in range(n_views):
+            sel = r == v
+            uv, ok = pix(v, X[sel])
+            xr[sel], okr[sel] = uv, ok
+        nbv = np.full((N, k), -1, np.int64)
+        nbx = np.zeros((N, k, 2))
+        nbc = np.zeros((N, k))
+        fill = np.zeros(N, np.int64)
+        for j in range(k):  # the j-th nearest other view by index distance
+            for v in range(n_views):
+                sel = np.nonzero((r == v) & okr)[0]
+                order = sorted([u for u in range(n_views) if u != v], key=lambda u: (abs(u - v), u))
+                if j >= len(order) or sel.size == 0:
+                    continue
+                n = order[j]
+                uv, ok = pix(n, X[sel])
+                sel, uv = sel[ok], uv[ok]
+                out = rng.random(sel.size) < outlier_frac
+                noisy = uv + rng.normal(0.0, noise_px, uv.shape)
+                rand = np.stack([rng.uniform(1, width - 2, sel.size), rng.uniform(1, height - 2, sel.size)], 1)
+                slot = fill[sel]
+                nbv[sel, slot] = n
+                nbx[sel, slot] = np.where(out[:, None], rand, noisy)
+                nbc[sel, slot] = np.where(out, rng.uniform(0.0, 0.4, sel.size), rng.uniform(0.6, 1.0, sel.size))
+                fill[sel] += 1
+        keep = np.nonzero(okr & (fill > 0))[0][:m - have]
+        xr_noisy = xr[keep] + rng.normal(0.0, noise_px, (keep.size, 2))
+        chunks.append((r[keep], xr_noisy, nbv[keep], nbx[keep], nbc[keep], X[keep]))
+        have += keep.size
+    ref_view = np.concatenate([c[0] for c in chunks]).astype(np.int32)
+    ref_xy = np.concatenate([c[1] for c in chunks])
+    nb_view = np.concatenate([c[2] for c in chunks]).astype(np.int32)
+    nb_xy = np.concatenate([c[3] for c in chunks])
+    nb_conf = np.concatenate([c[4] for c in chunks]).astype(np.float32)
+    points = np.concatenate([c[5] for c in chunks])
+    P = width * height
+    obs = np.zeros((n_views * P, 3), np.float32)
+    yy, xx = np.mgrid[0:height, 0:width].astype(np.float32)
+    for v in range(n_views):
+        f = rng.uniform(0.01, 0.05, size=(3, 2)).astype(np.float32)
+        ph = rng.uniform(0, 2 * math.pi, size=3).astype(np.float32)
+        for c in range(3):
+            obs[v * P:(v + 1) * P, c] = (0.5 + 0.4 * np.sin(f[c, 0] * xx + f[c, 1] * yy + ph[c])).ravel()
+    gain_bias = np.stack([rng.uniform(0.8, 1.2, n_views), rng.uniform(-0.05, 0.05, n_views)],
+                         1).astype(np.float32)
+    return Correspondences(cams, ref_view, ref_xy, nb_view, nb_xy, nb_conf, obs, gain_bias, points)
