@@ -328,6 +328,64 @@ def measure_tracking(r, params, cameras, images, hbm_peak, steps, flush):
                               "bytes_per_pixel": 68}}
 
 
+# FP64 operations of one two-view hypothesis of the triangulation (4x4 system, one-sided Jacobi,
+# reprojection error and angle), counted from the kernel's double-precision instructions under
+# ncu on the seeding workload (FMA as 2; the division and square-root sequences included):
+# 1.772e9 over 409957 hypotheses.
+TRI_FP64_FLOP_PER_HYP = 4323
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured figure exists for it)
+
+
+def measure_seeding(r, steps):
+    """Dense initialisation on a TUM-shaped keyframe window (10 views, 640x480): 131072 matched
+    reference pixels with up to 4 neighbours each (0.3 px noise, 5 % outliers)."""
+    import torch
+    from paper_2601_00705_gb300 import binding, seeding, synthetic
+
+    c = synthetic.correspondences(m=131072, k=4)
+    dev = r.device
+    tri = seeding.triangulate(r.ctx, c.cameras, c.ref_view, c.ref_xy, c.nb_view, c.nb_xy,
+                              c.nb_conf, dev, r.stream_handle())
+    torch.cuda.synchronize()
+    inp = tri["inputs"]
+    hyp = int((c.nb_view >= 0).sum())
+    ptrs = {k: v.data_ptr() for k, v in {**inp, **{k: tri[k] for k in (
+        "valid", "X", "best", "err", "angle", "kappa")}}.items()}
+    cams = binding.make_cameras(c.cameras)
+    cfg = binding.default_seed_config()
+    M, K = inp["nb_view"].shape
+    tms = []
+    for _ in range(max(steps, 5)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r.ctx.triangulate(cams, M, K, ptrs, cfg, r.stream_handle())
+        e1.record()
+        e1.synchronize()
+        tms.append(e0.elapsed_time(e1))
+    tri_ms = float(np.median(tms))
+    seeds = seeding.init_seeds(r.ctx, c.cameras, tri, c.observed, c.gain_bias, dev)
+    torch.cuda.synchronize()
+    sms = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        seeds = seeding.init_seeds(r.ctx, c.cameras, tri, c.observed, c.gain_bias, dev)
+        torch.cuda.synchronize()
+        sms.append((time.perf_counter() - t0) * 1e3)
+    flops = TRI_FP64_FLOP_PER_HYP * hyp / (tri_ms * 1e-3) / 1e12
+    return {"workload": "10 x 640x480 keyframes, 131072 reference pixels, <= 4 neighbours",
+            "hypotheses": hyp, "accepted": int(tri["valid"].sum().item()),
+            "seeds": int(seeds["index"].numel()),
+            "triangulate_us": tri_ms * 1e3, "hypotheses_per_s": hyp / (tri_ms * 1e-3),
+            "triangulate_roofline": {"bound": "fp64", "achieved": flops,
+                                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": flops / FP64_NOMINAL_TFLOPS,
+                                     "peak_source": "nominal GB300 dense FP64",
+                                     "flop_per_hypothesis": TRI_FP64_FLOP_PER_HYP},
+            "init_seeds_ms": float(np.median(sms)),
+            "init_seeds_note": "host wall clock of the synchronous call (scratch allocation, "
+                               "two count read-backs, ~15 kernels)"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2601_00705_gb300 import binding, synthetic
@@ -610,6 +668,7 @@ def run_ours(args, world, rank, local):
     }
     line["tracking"] = measure_tracking(r, params, wl.cameras, images,
                                         float(peaks.get("hbm_gbs", 6800.0)), args.steps, flush)
+    line["seeding"] = measure_seeding(r, args.steps)
     if world == 1 and rank == 0:
         px, dt, threads, frac = oracle_sample(wl, list(range(V)))
         line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": threads,

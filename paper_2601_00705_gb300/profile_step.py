@@ -1,11 +1,15 @@
-"""Eager forward + backward steps of a synthetic workload in a fixed tile configuration.
+"""Eager forward + backward steps of a synthetic workload in a fixed tile configuration, or
+eager runs of the dense initialisation.
 
 A driver for kernel profilers: it runs ``--steps`` batched steps through ``Renderer`` (the
 library's public path) with no autotuning, no CUDA graph and no timing, so that a profiler's
 launch filter (``-k`` / ``-s`` / ``-c``) sees exactly ``--steps`` launches of each kernel in
-the order forward, backward. Prints the counters of the last forward.
+the order forward, backward. Prints the counters of the last forward. With ``--seeding M`` it
+instead runs ``--steps`` triangulations and seed initialisations of M synthetic matched pixels
+(up to 4 neighbours each, ten 640x480 keyframes).
 
     python -m paper_2601_00705_gb300.profile_step --workload tum --tile 16x16x8 --steps 2
+    python -m paper_2601_00705_gb300.profile_step --seeding 131072 --steps 2
 """
 from __future__ import annotations
 
@@ -26,7 +30,23 @@ def main(argv: list[str] | None = None) -> None:
     p.add_argument("--backward-ppt", type=int, default=0,
                    help="pixels per thread of the backward blend (0: as the forward)")
     p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--seeding", type=int, default=0,
+                   help="run the dense initialisation on this many matched pixels instead")
     args = p.parse_args(argv)
+    if args.seeding:
+        from . import seeding
+        r = Renderer(torch.device("cuda", 0))
+        c = synthetic.correspondences(m=args.seeding, k=4)
+        for _ in range(args.steps):
+            tri = seeding.triangulate(r.ctx, c.cameras, c.ref_view, c.ref_xy, c.nb_view, c.nb_xy,
+                                      c.nb_conf, r.device, r.stream_handle())
+            seeds = seeding.init_seeds(r.ctx, c.cameras, tri, c.observed, c.gain_bias, r.device)
+        torch.cuda.synchronize()
+        print(json.dumps({"seeding": args.seeding, "steps": args.steps,
+                          "hypotheses": int((c.nb_view >= 0).sum()),
+                          "accepted": int(tri["valid"].sum().item()),
+                          "seeds": int(seeds["index"].numel())}))
+        return
     tw, th, ppt = (int(x) for x in args.tile.split("x"))
 
     wl = synthetic.make(args.workload)
