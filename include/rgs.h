@@ -343,6 +343,66 @@ rgs_status rgs_radix_sort_u32(rgs_ctx* ctx, uint32_t* keys, uint32_t* vals, int6
 rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                                   uint32_t* total_out, void* stream);
 
+/* ---- Mapping (Section 3.5 Eq. map-loss and Eq. reg; appendix Eq. app-ema and the maintenance
+ * of observation counts, visibility scores and pruning). ---- */
+typedef struct {
+  float lambda_iso;        /* weight of sum_i |Sigma_i - tr(Sigma_i) / 3 I|_F */
+  float lambda_alpha;      /* weight of sum_i psi(alpha_i), psi = -log(alpha) - log(1 - alpha) */
+  float lambda_mu;         /* weight of sum_i |mu_i - mu_bar_i|^2 */
+  const float* ema_means;  /* DEVICE [n][3] anchor mu_bar, or NULL: no position term */
+  uint32_t* obs_count;     /* DEVICE [n] or NULL: += number of views of the forward that see i */
+  float* vis_score;        /* DEVICE [n] or NULL: += that number times alpha_i */
+  double* value;           /* DEVICE [1] or NULL: R summed over all Gaussians */
+} rgs_map_reg;
+
+/* rgs_render_backward plus the mapping regulariser R of Eq. reg over all n Gaussians (seen or
+ * not): its gradients are added to the requested parameter gradients (isotropy: log-scales
+ * only, since the Frobenius norm is invariant under the rotation, zero at the isotropic kink;
+ * psi: opacity logits, d psi / d logit = 2 alpha - 1; position: means, the anchor held
+ * fixed), its value is written to reg->value, and the counters are advanced. Parameters with
+ * non-finite values contribute nothing. The first call with reg->value set on a state allocates
+ * a per-Gaussian scratch and must be made outside stream capture. reg NULL: rgs_render_backward. */
+rgs_status rgs_render_backward_mapping(rgs_ctx* ctx, uint64_t state, const rgs_image_grads* grads,
+                                       uint32_t grad_mask, float* d_means, float* d_log_scales,
+                                       float* d_quats, float* d_opacity_logits, float* d_sh,
+                                       float* d_pose, const rgs_map_reg* reg, void* stream);
+
+/* Anchor update after a mapping step (Eq. app-ema): ema = (1 - eta) ema + eta means, over n
+ * Gaussians (DEVICE [n][3] each); 0 < eta < 1. Never synchronises. */
+rgs_status rgs_map_ema(rgs_ctx* ctx, int64_t n, const float* means, float* ema_means, float eta,
+                       void* stream);
+
+/* Pruning bounds (HOST struct; the paper gives no values): a Gaussian is kept iff
+ *   alpha >= min_opacity, tr(Sigma^W) = sum_k exp(2 log_scale_k) <= max_trace, and not
+ *   (obs_count >= min_observations and vis_score < min_visibility).
+ * Defaults: 0.005, 1.0, 5, 1.0 (observed five times with a summed opacity below one). */
+typedef struct {
+  float min_opacity;
+  float max_trace;
+  uint32_t min_observations;
+  float min_visibility;
+} rgs_prune_config;
+void rgs_prune_config_default(rgs_prune_config* cfg);
+
+/* keep[i] = 1 or 0 by the bounds above (DEVICE u8 [n]); n_keep: DEVICE u32 [1], the number
+ * kept. Inputs DEVICE [n][3] log-scales, [n] logits, [n] counts, [n] scores. Never
+ * synchronises. */
+rgs_status rgs_prune_mask(rgs_ctx* ctx, int64_t n, const float* log_scales,
+                          const float* opacity_logits, const uint32_t* obs_count,
+                          const float* vis_score, const rgs_prune_config* cfg, uint8_t* keep,
+                          uint32_t* n_keep, void* stream);
+
+/* Co-visibility of frame pairs for keyframe scheduling (Eq. iou, with the per-pixel visibility
+ * masks of the appendix "Keyframe Scheduling by Co-Visibility"): for pair j,
+ *   V_a = {p : alpha_a[j n + p] > tau},  V_b = {p : alpha_b[j n + p] > tau},
+ *   counts[j] = (|V_a n V_b|, |V_a u V_b|),  iou[j] = |V_a n V_b| / |V_a u V_b| (0 if empty).
+ *   alpha_a, alpha_b: DEVICE [n_pairs][n] accumulated opacities (e.g. rgs_images.alpha of two
+ *     renders of the same size); counts: DEVICE u64 [n_pairs][2]; iou: DEVICE float [n_pairs].
+ * Never synchronises; may be captured. */
+rgs_status rgs_covisibility(rgs_ctx* ctx, const float* alpha_a, const float* alpha_b, int64_t n,
+                            int32_t n_pairs, float tau, uint64_t* counts, float* iou,
+                            void* stream);
+
 /* ---- Dense initialisation (Section 3.3 "Multi-view Triangulation" and "Gaussian Parameter
  * Initialization"; appendix "Gaussian Initialization and Joint Mapping", Eq. app-sigma-init,
  * Eq. app-alpha-init). Matched pixels of a keyframe window become Gaussian seeds: a two-view

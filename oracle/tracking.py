@@ -1,6 +1,6 @@
 """FP64 CPU oracle of the tracking step around the renderer (Section 3.2 and its appendix: Eq.
 app-bright, app-ls, app-trackloss, app-weight; Eq. leftupdate; the Adam optimiser with a cosine
-learning-rate schedule).
+learning-rate schedule) and of the co-visibility measure of keyframe scheduling (Eq. iou).
 
 TEST INFRASTRUCTURE ONLY. Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import this module. The product path never imports it, and it imports
@@ -22,6 +22,9 @@ Readings where the paper is silent (the same readings the CUDA path takes):
     lr (1 + cos(pi min(k, K) / K)) / 2 for a schedule of K steps, or lr when K = 0.
   * The twist xi = (rho, omega) acts on the left: T <- exp(xi^) T, with the SE(3) exponential
     of the 4x4 matrix [[omega]_x, rho; 0, 0].
+  * Co-visibility (Eq. iou): the main text counts visible Gaussians, the appendix visible
+    pixels; the pixel form is used, V = {p : accumulated opacity > tau}, compared pixel by
+    pixel between the two frames, and IoU = 0 when both masks are empty.
 """
 from __future__ import annotations
 
@@ -154,3 +157,14 @@ def adam_pose_step(world_to_cam, d_pose, m, v, k, lr=5e-3, beta1=0.9, beta2=0.99
         T[:3] = T0[i]
         out[i] = (se3_exp(xi[i]) @ T)[:3]
     return out, m, v, xi
+
+
+def covisibility(alpha_a, alpha_b, tau):
+    """Eq. iou with the per-pixel visibility masks: V = {p : alpha(p) > tau} for each image of a
+    pair; returns (intersection, union, IoU), IoU = 0 for an empty union. alpha_* [n_pairs, n]."""
+    va = np.asarray(alpha_a, dtype=np.float64) > tau
+    vb = np.asarray(alpha_b, dtype=np.float64) > tau
+    inter = (va & vb).sum(-1)
+    union = (va | vb).sum(-1)
+    iou = np.where(union > 0, inter / np.maximum(union, 1), 0.0)
+    return inter, union, iou

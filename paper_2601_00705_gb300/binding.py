@@ -29,7 +29,8 @@ EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_copy_records", "rgs_autotune", "rgs_render_forward_posed",
             "rgs_track_config_default", "rgs_adam_config_default", "rgs_track_grad_weight",
             "rgs_track_loss", "rgs_pose_adam_step", "rgs_seed_config_default", "rgs_triangulate",
-            "rgs_init_seeds")
+            "rgs_init_seeds", "rgs_covisibility", "rgs_render_backward_mapping", "rgs_map_ema",
+            "rgs_prune_config_default", "rgs_prune_mask")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -81,6 +82,18 @@ class SeedConfig(ctypes.Structure):
                 ("tie_eps", ctypes.c_float), ("plane_radius", ctypes.c_float),
                 ("s_par_cap", ctypes.c_float), ("alpha_lo", ctypes.c_float),
                 ("alpha_hi", ctypes.c_float), ("voxel", ctypes.c_float)]
+
+
+class MapReg(ctypes.Structure):
+    _fields_ = [("lambda_iso", ctypes.c_float), ("lambda_alpha", ctypes.c_float),
+                ("lambda_mu", ctypes.c_float), ("ema_means", ctypes.c_void_p),
+                ("obs_count", ctypes.c_void_p), ("vis_score", ctypes.c_void_p),
+                ("value", ctypes.c_void_p)]
+
+
+class PruneConfig(ctypes.Structure):
+    _fields_ = [("min_opacity", ctypes.c_float), ("max_trace", ctypes.c_float),
+                ("min_observations", ctypes.c_uint32), ("min_visibility", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):
@@ -144,6 +157,12 @@ def load(build_if_needed: bool = True):
                                    P, P, P, P, P, P, P, P]),
             "rgs_pose_adam_step": (S, [P, I32, ctypes.POINTER(AdamConfig), P, P, P, P, P]),
             "rgs_seed_config_default": (None, [ctypes.POINTER(SeedConfig)]),
+            "rgs_covisibility": (S, [P, P, P, I64, I32, ctypes.c_float, P, P, P]),
+            "rgs_render_backward_mapping": (S, [P, U64, ctypes.POINTER(ImageGrads), U32, P, P, P,
+                                                P, P, P, ctypes.POINTER(MapReg), P]),
+            "rgs_map_ema": (S, [P, I64, P, P, ctypes.c_float, P]),
+            "rgs_prune_config_default": (None, [ctypes.POINTER(PruneConfig)]),
+            "rgs_prune_mask": (S, [P, I64, P, P, P, P, ctypes.POINTER(PruneConfig), P, P, P]),
             "rgs_triangulate": (S, [P, ctypes.POINTER(Camera), I32, I64, I32, P, P, P, P, P,
                                     ctypes.POINTER(SeedConfig), P, P, P, P, P, P, P]),
             "rgs_init_seeds": (S, [P, ctypes.POINTER(Camera), I32, I64, I32, P, P, P, P, P, P, P,
@@ -186,6 +205,14 @@ def default_track_config(**overrides) -> TrackConfig:
 def default_adam_config(**overrides) -> AdamConfig:
     cfg = AdamConfig()
     load().rgs_adam_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def default_prune_config(**overrides) -> PruneConfig:
+    cfg = PruneConfig()
+    load().rgs_prune_config_default(ctypes.byref(cfg))
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg
@@ -283,6 +310,13 @@ class Context:
                                                 P(d_pose), P(adam_state), P(step),
                                                 P(world_to_cam), P(stream)))
 
+    def covisibility(self, alpha_a: int, alpha_b: int, n: int, n_pairs: int, tau: float,
+                     counts: int, iou: int, stream: int):
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_covisibility(self.handle, P(alpha_a), P(alpha_b), int(n),
+                                              int(n_pairs), float(tau), P(counts), P(iou),
+                                              P(stream)))
+
     def triangulate(self, cams, m: int, k: int, ptrs: dict, cfg: SeedConfig, stream: int):
         """ptrs: device pointers ref_view, ref_xy, nb_view, nb_xy, nb_conf (inputs) and valid, X,
         best, err, angle, kappa (outputs)."""
@@ -310,6 +344,26 @@ class Context:
             P(ptrs["quats"]), P(ptrs["opacity_logits"]), P(ptrs["sh"]), P(ptrs["normals"]),
             ctypes.byref(n), P(stream)))
         return int(n.value)
+
+    def backward_mapping(self, state: int, grads: ImageGrads, grad_mask: int, ptrs: list,
+                         reg: MapReg, stream: int):
+        """ptrs: d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_pose (0 = none)."""
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_render_backward_mapping(
+            self.handle, ctypes.c_uint64(state), ctypes.byref(grads), grad_mask,
+            *[P(p or None) for p in ptrs], ctypes.byref(reg), P(stream)))
+
+    def map_ema(self, n: int, means: int, ema: int, eta: float, stream: int):
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_map_ema(self.handle, int(n), P(means), P(ema), float(eta),
+                                         P(stream)))
+
+    def prune_mask(self, n: int, log_scales: int, logits: int, obs_count: int, vis_score: int,
+                   cfg: "PruneConfig", keep: int, n_keep: int, stream: int):
+        P = ctypes.c_void_p
+        self._check(self.lib.rgs_prune_mask(self.handle, int(n), P(log_scales), P(logits),
+                                            P(obs_count), P(vis_score), ctypes.byref(cfg),
+                                            P(keep), P(n_keep), P(stream)))
 
     def backward(self, state: int, grads: ImageGrads, grad_mask: int, d_means: int,
                  d_log_scales: int, d_quats: int, d_opacity_logits: int, d_sh: int, d_pose: int,

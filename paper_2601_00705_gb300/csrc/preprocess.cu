@@ -635,14 +635,14 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
 // dL/dSigma^W to the log-scales and the quaternion once. Every parameter gradient is written
 // exactly once.
 // ------------------------------------------------------------------------------------------
-template <int DEG>
+template <int DEG, bool kReg>
 __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     const __grid_constant__ Views views, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, unsigned long long* __restrict__ vis_mask,
     float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ d_means,
     float* __restrict__ d_log_scales, float* __restrict__ d_quats, float* __restrict__ d_logits,
-    float* __restrict__ d_sh) {
+    float* __restrict__ d_sh, const MapReg reg) {
   chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
@@ -658,6 +658,8 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
   uint64_t vis = vis_mask[i];
   if (vis) vis_mask[i] = 0ull;
   const bool any_visible = vis != 0;
+  const int n_seen = __popcll(vis);
+  (void)n_seen;
   // The records are gathered one view ahead: the next view's loads are issued before the
   // current record is cleared and accumulated.
   struct Rec {
@@ -772,6 +774,57 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
       gq[3] = (gz - z * dot) * iq;
     }
   }
+  if constexpr (kReg) {
+    // Eq. reg for this Gaussian, with its gradients added to the rendering ones:
+    //   lambda_iso |Sigma - tr(Sigma) / 3 I|_F = lambda_iso sqrt(sum_k (s_k^2 - mean s^2)^2)
+    //     (the Frobenius norm is invariant under the rotation, so only the scales enter;
+    //     d/d log s_k = 2 s_k^2 (s_k^2 - mean s^2) / norm, 0 at the isotropic kink),
+    //   lambda_alpha psi(alpha), psi = -log(alpha) - log(1 - alpha) = |l| + 2 log(1 + e^-|l|)
+    //     for the logit l (d psi / d l = 2 alpha - 1),
+    //   lambda_mu |mu - mu_bar|^2 (d / d mu = 2 lambda_mu (mu - mu_bar)).
+    // Non-finite parameters contribute nothing. The counters add the views that see it.
+    float ls[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
+    const float l = __ldg(logits + i);
+    float val = 0.0f;
+    const bool finite = isfinite(ls[0]) && isfinite(ls[1]) && isfinite(ls[2]) && isfinite(l) &&
+                        isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]);
+    const float alpha = 1.0f / (1.0f + expf(-l));
+    if (finite) {
+      float s2[3], mean = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        s2[a] = expf(2.0f * ls[a]);
+        mean += s2[a];
+      }
+      mean *= (1.0f / 3.0f);
+      float nrm2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) nrm2 = fmaf(s2[a] - mean, s2[a] - mean, nrm2);
+      const float nrm = sqrtf(nrm2);
+      val = reg.lambda_iso * nrm;
+      if (nrm > 0.0f)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gls[a] += reg.lambda_iso * 2.0f * s2[a] * (s2[a] - mean) / nrm;
+      const float al = fabsf(l);
+      val += reg.lambda_alpha * (al + 2.0f * log1pf(expf(-al)));
+      glogit += reg.lambda_alpha * (2.0f * alpha - 1.0f);
+      if (reg.ema_means) {
+        float d2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float d = m[a] - __ldg(reg.ema_means + 3 * (size_t)i + a);
+          d2 = fmaf(d, d, d2);
+          gm[a] += 2.0f * reg.lambda_mu * d;
+        }
+        val += reg.lambda_mu * d2;
+      }
+    }
+    if (reg.values) reg.values[i] = val;
+    if (reg.obs_count) reg.obs_count[i] += (uint32_t)n_seen;
+    if (reg.vis_score) reg.vis_score[i] += (float)n_seen * (finite ? alpha : 0.0f);
+  }
   if ((grad_mask & RGS_GRAD_MEANS) && d_means)
 #pragma unroll
     for (int k = 0; k < 3; ++k) d_means[3 * (size_t)i + k] = gm[k];
@@ -793,6 +846,22 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
       for (int k = 0; k < 3 * K; ++k) p[k] = gsh[k];
     }
   }
+}
+
+// R = sum of the per-Gaussian values, in double precision (grid-stride, one atomic per block).
+__global__ void __launch_bounds__(256) reg_sum_kernel(int n, const float* __restrict__ values,
+                                                      double* __restrict__ value) {
+  chain_wait();
+  double s = 0.0;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) s += (double)values[i];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(value, red[0]);
 }
 
 // d_pose[v,k] = sum over blocks of the partials, in double precision.
@@ -864,7 +933,7 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        int64_t vn, float* g2d, uint32_t grad_mask,
                                        float* d_means, float* d_log_scales, float* d_quats,
                                        float* d_logits, float* d_sh, float* pose_partial,
-                                       float* d_pose, cudaStream_t stream) {
+                                       float* d_pose, const MapReg* reg, cudaStream_t stream) {
   const int blocks1 = preprocess_backward_blocks(vn);
   cudaError_t e = cudaSuccess;
   if (g.n > 0) {
@@ -884,10 +953,12 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
 #undef RGS_BWD_VIEW
     if (e != cudaSuccess) return e;
     const int blocks2 = (g.n + kPreThreads - 1) / kPreThreads;
+    const MapReg no_reg{};
 #define RGS_BWD_GAUSS(D)                                                                          \
-  e = launch_chained(backward_gaussian_kernel<D>, dim3(blocks2), dim3(kPreThreads), stream, views, \
-                     g.n, g.means, g.log_scales, g.quats, g.opacity_logits, vis_mask, g2d,        \
-                     grad_mask, d_means, d_log_scales, d_quats, d_logits, d_sh)
+  e = launch_chained(reg ? backward_gaussian_kernel<D, true> : backward_gaussian_kernel<D, false>, \
+                     dim3(blocks2), dim3(kPreThreads), stream, views, g.n, g.means, g.log_scales, \
+                     g.quats, g.opacity_logits, vis_mask, g2d, grad_mask, d_means, d_log_scales,  \
+                     d_quats, d_logits, d_sh, reg ? *reg : no_reg)
     switch (g.sh_degree) {
       case 0: RGS_BWD_GAUSS(0); break;
       case 1: RGS_BWD_GAUSS(1); break;
@@ -896,6 +967,16 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
     }
     RGS_LAUNCHED();
 #undef RGS_BWD_GAUSS
+    if (e != cudaSuccess) return e;
+  }
+  if (reg && reg->value) {
+    e = cudaMemsetAsync(reg->value, 0, sizeof(double), stream);
+    if (e == cudaSuccess && g.n > 0 && reg->values) {
+      const int blocks = std::min((g.n + 255) / 256, 4 * 152);
+      e = launch_chained(reg_sum_kernel, dim3(blocks), dim3(256), stream, g.n,
+                         (const float*)reg->values, reg->value);
+      RGS_LAUNCHED();
+    }
     if (e != cudaSuccess) return e;
   }
   if ((grad_mask & RGS_GRAD_POSE) && d_pose) {

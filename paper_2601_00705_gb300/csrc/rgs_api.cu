@@ -34,7 +34,7 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        int64_t vn, float* g2d, uint32_t grad_mask,
                                        float* d_means, float* d_log_scales, float* d_quats,
                                        float* d_logits, float* d_sh, float* pose_partial,
-                                       float* d_pose, cudaStream_t stream);
+                                       float* d_pose, const MapReg* reg, cudaStream_t stream);
 cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              const uint32_t* offsets, const uint32_t* ntiles, const float4* rec0,
                              const float4* rec1, const float4* rec2, float log2_alpha_min,
@@ -106,6 +106,9 @@ struct State {
   float* pose_partial = nullptr;
   Counters* counters = nullptr;
   float* pose_records = nullptr;  // [kMaxViews][16] device poses of a posed forward
+  Region r_reg;                   // per-Gaussian regulariser values (first mapping backward)
+  float* reg_vals = nullptr;
+  int64_t reg_cap = 0;
   // Phase timing: event k is recorded at the start (k = 0) / end of each forward phase, and
   // kEvBwd0 .. at the start / end of each backward phase.
   cudaEvent_t ev[kNumEvents] = {};
@@ -127,6 +130,15 @@ cudaError_t launch_track_loss(const Views& views, const float* color, const floa
 cudaError_t launch_pose_adam(int n_views, float lr, float beta1, float beta2, float eps,
                              int iterations, const float* d_pose, float* adam_state,
                              int32_t* step, float* world_to_cam, cudaStream_t stream);
+cudaError_t launch_covisibility(const float* alpha_a, const float* alpha_b, int64_t n,
+                                int n_pairs, float tau, unsigned long long* counts, float* iou,
+                                cudaStream_t stream);
+cudaError_t launch_map_ema(int64_t n, const float* means, float* ema, float eta,
+                           cudaStream_t stream);
+cudaError_t launch_prune_mask(int64_t n, const float* log_scales, const float* logits,
+                              const uint32_t* obs_count, const float* vis_score, float min_opacity,
+                              float max_trace, uint32_t min_observations, float min_visibility,
+                              uint8_t* keep, uint32_t* n_keep, cudaStream_t stream);
 }  // namespace rgs
 
 struct TuneChoice {
@@ -333,6 +345,7 @@ void destroy_state(State* s) {
   free_region(s->r_scratch);
   free_region(s->r_pose);
   free_region(s->r_counters);
+  free_region(s->r_reg);
   delete s;
 }
 
@@ -829,10 +842,35 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
 }
 }  // namespace
 
+namespace {
+rgs_status render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads* grads,
+                           uint32_t grad_mask, float* d_means, float* d_log_scales,
+                           float* d_quats, float* d_opacity_logits, float* d_sh, float* d_pose,
+                           const rgs_map_reg* reg, void* stream_ptr);
+}  // namespace
+
 rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads* grads,
                                uint32_t grad_mask, float* d_means, float* d_log_scales,
                                float* d_quats, float* d_opacity_logits, float* d_sh,
                                float* d_pose, void* stream_ptr) {
+  return render_backward(ctx, handle, grads, grad_mask, d_means, d_log_scales, d_quats,
+                         d_opacity_logits, d_sh, d_pose, nullptr, stream_ptr);
+}
+
+rgs_status rgs_render_backward_mapping(rgs_ctx* ctx, uint64_t handle,
+                                       const rgs_image_grads* grads, uint32_t grad_mask,
+                                       float* d_means, float* d_log_scales, float* d_quats,
+                                       float* d_opacity_logits, float* d_sh, float* d_pose,
+                                       const rgs_map_reg* reg, void* stream_ptr) {
+  return render_backward(ctx, handle, grads, grad_mask, d_means, d_log_scales, d_quats,
+                         d_opacity_logits, d_sh, d_pose, reg, stream_ptr);
+}
+
+namespace {
+rgs_status render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads* grads,
+                           uint32_t grad_mask, float* d_means, float* d_log_scales,
+                           float* d_quats, float* d_opacity_logits, float* d_sh, float* d_pose,
+                           const rgs_map_reg* reg, void* stream_ptr) {
   if (!ctx) return RGS_ERR_INVALID_ARG;
   ctx->last_error.clear();
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
@@ -861,6 +899,30 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_gr
   if (cudaSetDevice(ctx->device) != cudaSuccess)
     return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
   const bool capturing = is_capturing(stream);
+  MapReg mreg{};
+  if (reg) {
+    if (!std::isfinite(reg->lambda_iso) || !std::isfinite(reg->lambda_alpha) ||
+        !std::isfinite(reg->lambda_mu))
+      return fail(ctx, RGS_ERR_INVALID_ARG, "regulariser weights must be finite");
+    mreg.lambda_iso = reg->lambda_iso;
+    mreg.lambda_alpha = reg->lambda_alpha;
+    mreg.lambda_mu = reg->lambda_mu;
+    mreg.ema_means = reg->ema_means;
+    mreg.obs_count = reg->obs_count;
+    mreg.vis_score = reg->vis_score;
+    mreg.value = reg->value;
+    if (reg->value && n > 0) {
+      if (s->reg_cap < n) {
+        if (capturing)
+          return fail(ctx, RGS_ERR_CAPACITY, "regulariser scratch: make a first call outside capture");
+        free_region(s->r_reg);
+        RGS_CUDA(alloc_region(s->r_reg, sizeof(float) * (size_t)n), "allocate regulariser scratch");
+        s->reg_vals = static_cast<float*>(s->r_reg.base);
+        s->reg_cap = n;
+      }
+      mreg.values = s->reg_vals;
+    }
+  }
   const uint64_t launches0 = launch_counter();
   s->bwd_timed = ctx->timing;
   RGS_CUDA(mark(ctx, *s, kEvBwd0, stream, capturing), "event");
@@ -872,12 +934,13 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_gr
   RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->vis_mask, s->order,
                                       s->counters, s->vn, s->g2d, grad_mask, d_means,
                                       d_log_scales, d_quats, d_opacity_logits, d_sh,
-                                      s->pose_partial, d_pose, stream),
+                                      s->pose_partial, d_pose, reg ? &mreg : nullptr, stream),
            "preprocess backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 2, stream, capturing), "event");
   s->bwd_launches = (uint32_t)(launch_counter() - launches0);
   return RGS_OK;
 }
+}  // namespace
 
 rgs_status rgs_set_phase_timing(rgs_ctx* ctx, int32_t enable) {
   if (!ctx) return RGS_ERR_INVALID_ARG;
@@ -1315,4 +1378,72 @@ rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
   cudaStreamSynchronize(stream);
   cudaFree(base);
   return result;
+}
+
+rgs_status rgs_covisibility(rgs_ctx* ctx, const float* alpha_a, const float* alpha_b, int64_t n,
+                            int32_t n_pairs, float tau, uint64_t* counts, float* iou,
+                            void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n < 0 || n_pairs < 0 || n_pairs > 65535 || !std::isfinite(tau))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n, n_pairs (0..65535) or tau out of range");
+  if (n_pairs > 0 && (!counts || !iou || (n > 0 && (!alpha_a || !alpha_b))))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null array");
+  if (n_pairs == 0) return RGS_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_covisibility(alpha_a, alpha_b, n, n_pairs, tau,
+                               reinterpret_cast<unsigned long long*>(counts), iou,
+                               static_cast<cudaStream_t>(stream_ptr)),
+           "co-visibility");
+  return RGS_OK;
+}
+
+// ---- Mapping maintenance ----
+
+rgs_status rgs_map_ema(rgs_ctx* ctx, int64_t n, const float* means, float* ema_means, float eta,
+                       void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n < 0 || !(eta > 0.0f && eta < 1.0f))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "n must be >= 0 and eta in (0, 1)");
+  if (n > 0 && (!means || !ema_means)) return fail(ctx, RGS_ERR_INVALID_ARG, "null array");
+  if (n == 0) return RGS_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_map_ema(n, means, ema_means, eta, static_cast<cudaStream_t>(stream_ptr)),
+           "anchor update");
+  return RGS_OK;
+}
+
+void rgs_prune_config_default(rgs_prune_config* cfg) {
+  if (!cfg) return;
+  cfg->min_opacity = 0.005f;
+  cfg->max_trace = 1.0f;
+  cfg->min_observations = 5;
+  cfg->min_visibility = 1.0f;
+}
+
+rgs_status rgs_prune_mask(rgs_ctx* ctx, int64_t n, const float* log_scales,
+                          const float* opacity_logits, const uint32_t* obs_count,
+                          const float* vis_score, const rgs_prune_config* cfg_in, uint8_t* keep,
+                          uint32_t* n_keep, void* stream_ptr) {
+  if (!ctx) return RGS_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n < 0 || n >= (1ll << 31)) return fail(ctx, RGS_ERR_INVALID_ARG, "n out of range");
+  if (!n_keep || (n > 0 && (!log_scales || !opacity_logits || !obs_count || !vis_score || !keep)))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "null array");
+  rgs_prune_config cfg;
+  if (cfg_in) cfg = *cfg_in; else rgs_prune_config_default(&cfg);
+  if (!std::isfinite(cfg.min_opacity) || !std::isfinite(cfg.min_visibility) ||
+      std::isnan(cfg.max_trace))
+    return fail(ctx, RGS_ERR_INVALID_ARG, "prune bounds out of range");
+  if (cudaSetDevice(ctx->device) != cudaSuccess)
+    return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice failed");
+  RGS_CUDA(launch_prune_mask(n, log_scales, opacity_logits, obs_count, vis_score,
+                             cfg.min_opacity, cfg.max_trace, cfg.min_observations,
+                             cfg.min_visibility, keep, n_keep,
+                             static_cast<cudaStream_t>(stream_ptr)),
+           "prune mask");
+  return RGS_OK;
 }

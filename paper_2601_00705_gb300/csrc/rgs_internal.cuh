@@ -462,6 +462,17 @@ inline int64_t sort_hist_entries(int64_t n_cap, int items = kSortItems) {
   return (sort_blocks(n_cap, items) + 1) * kRadixBins;
 }
 
+// Mapping regulariser and maintenance state, fused into the per-Gaussian backward phase
+// (Eq. reg, Eq. app-ema). A null pointer disables its part.
+struct MapReg {
+  float lambda_iso, lambda_alpha, lambda_mu;
+  const float* ema_means;  // [n][3] anchor of the position term
+  uint32_t* obs_count;     // [n]: += number of views of the forward that see the Gaussian
+  float* vis_score;        // [n]: += that number times its opacity
+  float* values;           // [n] scratch: the Gaussian's share of R (for the reduction)
+  double* value;           // [1]: R summed over the Gaussians
+};
+
 // Per-view camera data in double precision (built on the host from the float cameras).
 struct SeedCams {
   int n_views;

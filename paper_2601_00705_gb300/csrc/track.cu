@@ -6,10 +6,14 @@
 //   * the exposure fit (g, b) = argmin sum_x ||I(x) - g I^(x) - b||^2 per view, the weighted L1
 //     loss sum_x w_alpha(x) w_grad(x) ||I(x) - (g I^(x) + b)||_1 and its gradient with respect to
 //     the rendered colour, which is the upstream gradient of the backward;
-//   * one Adam step on the twist xi of every view, applied as T <- exp(xi^) T.
+//   * one Adam step on the twist xi of every view, applied as T <- exp(xi^) T;
+//   * co-visibility of frame pairs for the keyframe test (Eq. iou): intersection and union of
+//     the pixels whose accumulated opacity exceeds a threshold.
 // All passes are elementwise or reductions over the images (HBM-bound) except the pose update
 // (one thread per view).
 #include <math.h>
+
+#include <algorithm>
 
 #include "rgs_internal.cuh"
 
@@ -292,6 +296,56 @@ __global__ void pose_adam_kernel(int n_views, float lr, float beta1, float beta2
   if (threadIdx.x == 0) *step = k + 1;
 }
 
+// ------------------------------------------------------------------------------------------
+// Co-visibility (Eq. iou, with the per-pixel visibility masks of the keyframe scheduling): for
+// pair j, V_a = {p : alpha_a(p) > tau}, V_b likewise, counts |V_a n V_b| and |V_a u V_b| over
+// the n pixels of the pair's two images; IoU = intersection / union (0 for an empty union).
+// Grid rows are pairs; each block reduces its share with ballots and one atomic per count.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTrackThreads) covis_count_kernel(
+    const float* __restrict__ alpha_a, const float* __restrict__ alpha_b, int64_t n, float tau,
+    unsigned long long* __restrict__ counts) {
+  chain_wait();
+  const int j = blockIdx.y;
+  const float* a = alpha_a + (size_t)j * n;
+  const float* b = alpha_b + (size_t)j * n;
+  unsigned long long inter = 0, uni = 0;
+  for (int64_t p = (int64_t)blockIdx.x * kTrackThreads + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * kTrackThreads) {
+    const bool va = a[p] > tau, vb = b[p] > tau;
+    inter += (va && vb) ? 1u : 0u;
+    uni += (va || vb) ? 1u : 0u;
+  }
+  __shared__ unsigned long long s_i[kTrackThreads / 32], s_u[kTrackThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    inter += __shfl_xor_sync(0xffffffffu, inter, o);
+    uni += __shfl_xor_sync(0xffffffffu, uni, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_i[threadIdx.x >> 5] = inter;
+    s_u[threadIdx.x >> 5] = uni;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long ti = 0, tu = 0;
+    for (int w = 0; w < kTrackThreads / 32; ++w) {
+      ti += s_i[w];
+      tu += s_u[w];
+    }
+    atomicAdd(counts + 2 * j, ti);
+    atomicAdd(counts + 2 * j + 1, tu);
+  }
+}
+
+__global__ void covis_iou_kernel(int n_pairs, const unsigned long long* __restrict__ counts,
+                                 float* __restrict__ iou) {
+  chain_wait();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n_pairs)
+    iou[j] = counts[2 * j + 1] ? (float)((double)counts[2 * j] / (double)counts[2 * j + 1]) : 0.0f;
+}
+
 // Grid rows per view, columns enough to cover the largest view (at most 2 waves of blocks).
 dim3 view_grid(const Views& views) {
   int max_px = 1;
@@ -338,6 +392,25 @@ cudaError_t launch_track_loss(const Views& views, const float* color, const floa
   e = launch_chained(track_loss_kernel, grid, dim3(kTrackThreads), stream, views, color, alpha,
                      obs, w_grad, (const double*)sums, 1.0f / tau_alpha, fit_exposure ? 1 : 0,
                      d_color, loss, gain_bias);
+  RGS_LAUNCHED();
+  return e;
+}
+
+cudaError_t launch_covisibility(const float* alpha_a, const float* alpha_b, int64_t n,
+                                int n_pairs, float tau, unsigned long long* counts, float* iou,
+                                cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * 2 * n_pairs, stream);
+  if (e != cudaSuccess || n_pairs == 0) return e;
+  if (n > 0) {
+    const int64_t want = (n + kTrackThreads * 8 - 1) / (kTrackThreads * 8);
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 4 * 152 / n_pairs + 1));
+    e = launch_chained(covis_count_kernel, dim3(gx, (unsigned)n_pairs), dim3(kTrackThreads),
+                       stream, alpha_a, alpha_b, n, tau, counts);
+    RGS_LAUNCHED();
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_chained(covis_iou_kernel, dim3((unsigned)((n_pairs + 255) / 256)), dim3(256), stream,
+                     n_pairs, (const unsigned long long*)counts, iou);
   RGS_LAUNCHED();
   return e;
 }

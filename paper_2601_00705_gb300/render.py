@@ -86,10 +86,12 @@ class Renderer:
         return color, depth, alpha, state
 
     def backward_raw(self, state: int, n: int, K: int, n_views: int, d_color=None, d_depth=None,
-                     d_alpha=None, grad_mask: int = binding.GRAD_ALL, out: dict | None = None):
+                     d_alpha=None, grad_mask: int = binding.GRAD_ALL, out: dict | None = None,
+                     reg: "binding.MapReg | None" = None):
         """Runs the backward of `state`; returns a dict of gradient tensors (None if not asked).
         `out` may supply preallocated float32 tensors (keys means, log_scales, quats,
-        opacity_logits, sh, pose)."""
+        opacity_logits, sh, pose). `reg` adds the mapping regulariser (Eq. reg) and advances the
+        maintenance counters (see ``mapping.MapRegularizer``)."""
         dev = self.device
 
         def prep(t, shape):
@@ -121,8 +123,13 @@ class Renderer:
                                    d_depth.data_ptr() if d_depth is not None else None,
                                    d_alpha.data_ptr() if d_alpha is not None else None)
         ptr = {k: (v.data_ptr() if v is not None else 0) for k, v in out.items()}
-        self.ctx.backward(state, grads, grad_mask, ptr["means"], ptr["log_scales"], ptr["quats"],
-                          ptr["opacity_logits"], ptr["sh"], ptr["pose"], self.stream_handle())
+        names = ("means", "log_scales", "quats", "opacity_logits", "sh", "pose")
+        if reg is None:
+            self.ctx.backward(state, grads, grad_mask, *[ptr[k] for k in names],
+                              self.stream_handle())
+        else:
+            self.ctx.backward_mapping(state, grads, grad_mask, [ptr[k] for k in names], reg,
+                                      self.stream_handle())
         return out
 
     def autotune(self, means, log_scales, quats, opacity_logits, sh, cameras) -> dict:

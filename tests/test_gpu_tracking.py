@@ -229,3 +229,23 @@ def test_captured_tracking_iterations_lower_loss_and_pose_error():
     T_end = tr.world_to_cam.cpu().numpy().reshape(3, 4)
     assert np.abs(T_end - T_true).max() < 0.5 * np.abs(T_start - T_true).max()
     r.release(tr.state)
+
+
+@pytest.mark.parametrize("n,pairs", [(1, 1), (19200, 3), (307200, 2), (0, 2)])
+def test_covisibility_matches_oracle(n, pairs):
+    rng = np.random.default_rng(n + pairs)
+    a = rng.random((pairs, n)).astype(np.float32)
+    b = rng.random((pairs, n)).astype(np.float32)
+    if n:
+        a[0, : n // 3] = 0.0           # some empty and some exactly-at-threshold pixels
+        b[-1, : n // 5] = 0.25
+    r = renderer()
+    ad, bd = to_dev(a), to_dev(b)
+    counts = torch.empty((pairs, 2), dtype=torch.int64, device="cuda")
+    iou = torch.empty(pairs, device="cuda")
+    r.ctx.covisibility(ad.data_ptr(), bd.data_ptr(), n, pairs, 0.25, counts.data_ptr(),
+                       iou.data_ptr(), r.stream_handle())
+    torch.cuda.synchronize()
+    inter, union, ref = otrack.covisibility(a, b, np.float32(0.25))
+    np.testing.assert_array_equal(counts.cpu().numpy(), np.stack([inter, union], 1))
+    np.testing.assert_array_equal(iou.cpu().numpy(), ref.astype(np.float32))

@@ -216,3 +216,13 @@ def test_one_tracking_step_on_the_rasterizer_oracle_lowers_the_loss():
     T1h[:3] = T1[0]
     l1 = loss_at(T1h)[0]
     assert l1 < l0
+
+
+def test_covisibility_hand_counts():
+    a = np.array([[0.9, 0.2, 0.6, 0.0, 0.51], [0.0, 0.0, 0.0, 0.0, 0.0]])
+    b = np.array([[0.8, 0.7, 0.1, 0.0, 0.5], [0.0, 0.0, 0.0, 0.0, 0.0]])
+    inter, union, iou = tracking.covisibility(a, b, 0.5)
+    # Pair 0: V_a = {0, 2, 4}, V_b = {0, 1} (0.5 is not above 0.5): intersection {0}, union
+    # {0, 1, 2, 4}. Pair 1: both empty.
+    assert list(inter) == [1, 0] and list(union) == [4, 0]
+    assert list(iou) == [0.25, 0.0]
