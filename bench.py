@@ -386,6 +386,65 @@ def measure_seeding(r, steps):
                                "two count read-backs, ~15 kernels)"}
 
 
+def measure_mapping(r, params, cameras, images, mask, steps, hbm_peak):
+    """Mapping maintenance on the bench workload: the backward with the fused regulariser and
+    counters against the plain backward (eager, events around each), and the co-visibility of
+    each consecutive pair of views from the accumulated opacity."""
+    import torch
+    from paper_2601_00705_gb300 import binding
+    from paper_2601_00705_gb300.mapping import MapRegularizer
+
+    dev = r.device
+    n, K, V = int(params[0].shape[0]), int(params[4].shape[1]), len(cameras)
+    _, _, _, state = r.forward_raw(*params, binding.make_cameras(cameras))
+    up = torch.full_like(images[0], 1e-3)
+    mr = MapRegularizer(r.ctx, params[0])
+    out = {k: torch.empty(s, device=dev) for k, s in dict(
+        means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity_logits=(n,), sh=(n, K, 3),
+        pose=(V, 6)).items()}
+
+    def timed(reg):
+        ts = []
+        for _ in range(max(steps, 5) + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r.backward_raw(state, n, K, V, up, None, None, mask, out=out,
+                           reg=mr.reg() if reg else None)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts[2:]))
+
+    plain, with_reg = timed(False), timed(True)
+    r.release(state)
+    alpha = images[2]
+    Vp = V - 1
+    res = {"backward_ms": plain, "backward_with_regularizer_ms": with_reg,
+           "regularizer_overhead_us": (with_reg - plain) * 1e3, "gaussians": n}
+    sizes = {(c["width"], c["height"]) for c in cameras}
+    if Vp >= 1 and len(sizes) == 1:
+        P1 = cameras[0]["width"] * cameras[0]["height"]
+        a = alpha[:Vp * P1]
+        b = alpha[P1:V * P1]
+        counts = torch.empty((Vp, 2), dtype=torch.int64, device=dev)
+        iou = torch.empty(Vp, device=dev)
+        ts = []
+        for _ in range(max(steps, 5) + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r.ctx.covisibility(a.data_ptr(), b.data_ptr(), P1, Vp, 0.5, counts.data_ptr(),
+                               iou.data_ptr(), r.stream_handle())
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        us = float(np.median(ts[2:])) * 1e3
+        res["covisibility"] = {"pairs": Vp, "pixels_per_frame": P1, "us": us,
+                               "iou": [round(float(x), 4) for x in iou.cpu().numpy()],
+                               "achieved_gbs": 8.0 * Vp * P1 / (us * 1e-6) / 1e9,
+                               "peak_gbs": hbm_peak}
+    return res
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2601_00705_gb300 import binding, synthetic
@@ -669,6 +728,8 @@ def run_ours(args, world, rank, local):
     line["tracking"] = measure_tracking(r, params, wl.cameras, images,
                                         float(peaks.get("hbm_gbs", 6800.0)), args.steps, flush)
     line["seeding"] = measure_seeding(r, args.steps)
+    line["mapping"] = measure_mapping(r, params, wl.cameras, images, mask, args.steps,
+                                      float(peaks.get("hbm_gbs", 6800.0)))
     if world == 1 and rank == 0:
         px, dt, threads, frac = oracle_sample(wl, list(range(V)))
         line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": threads,
