@@ -52,6 +52,18 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
   return r;
 }
 
+// Lanes of the warp whose valid keys carry the same digit as this lane's (0 for an invalid
+// lane): one ballot per digit bit, each keeping the lanes that agree on that bit.
+__device__ __forceinline__ uint32_t warp_digit_peers(uint32_t digit, bool valid, int nbits) {
+  uint32_t peers = __ballot_sync(0xffffffffu, valid);
+  for (int b = 0; b < nbits; ++b) {
+    const uint32_t bit = (digit >> b) & 1u;
+    const uint32_t ones = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? ones : ~ones;
+  }
+  return valid ? peers : 0u;
+}
+
 // Loaders: value of element k.
 struct PlainLoad {
   const uint32_t* in;
@@ -271,6 +283,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
   const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
   uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const int nbits = 32 - __clz(mask);  // width of this pass's digit
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     const int64_t idx = wbase + r * 32 + lane;
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     key[r] = valid ? keys_in[idx] : 0u;
     val[r] = (valid && vals_in) ? vals_in[idx] : 0u;
     const uint32_t digit = valid ? ((key[r] >> shift) & mask) : kRadixBins;  // kRadixBins = none
-    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t peers = warp_digit_peers(digit, valid, nbits);
     const uint32_t before = __popc(peers & lt_mask);
     uint32_t prior = 0;
     if (valid) prior = warp_counts[warp][digit];
@@ -410,7 +423,7 @@ __global__ void __launch_bounds__(kCsThreads, 1) cluster_sort_kernel(
           if (has_vals) val[r] = a_vals[e];
         }
         const uint32_t digit = valid ? ((key[r] >> shift) & mask) : (uint32_t)kRadixBins;
-        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t peers = warp_digit_peers(digit, valid, w);
         const uint32_t before = __popc(peers & lt_mask);
         const uint32_t prior = valid ? my_counts[digit] : 0u;
         __syncwarp();
