@@ -21,7 +21,8 @@ def _ctx():
     return renderer().ctx
 
 
-@pytest.mark.parametrize("n", [1, 31, 4095, 4096, 4097, 65537, 1_000_003])
+# Up to 64k elements the scan is one cluster launch, above it three kernels: both are covered.
+@pytest.mark.parametrize("n", [1, 31, 4095, 4096, 4097, 65536, 65537, 1_000_003])
 def test_exclusive_scan_matches_cumsum(n):
     rng = np.random.default_rng(n)
     x = rng.integers(0, 1000, size=n).astype(np.uint32)
