@@ -130,7 +130,8 @@ typedef struct {
 /* Counters of the last forward on a state (read back with a stream synchronisation). */
 typedef struct {
   int64_t n_visible;       /* (view, Gaussian) pairs that touch at least one tile */
-  int64_t n_pairs;         /* duplicated (view, tile, Gaussian) entries */
+  int64_t n_pairs;         /* duplicated (view, tile, Gaussian) entries (of the visible entries
+                              kept, when status bit 2 is set) */
   int64_t n_eval;          /* (pixel, Gaussian) list positions visited by the forward blend */
   int64_t n_contrib;       /* of those, the ones composited (covering, before the stop) */
   int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs */

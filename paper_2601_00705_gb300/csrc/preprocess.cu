@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
   const int nv = views.n_views;
   for (int t = threadIdx.x; t < nv * 6; t += kPreThreads) s_pose[t] = 0.0f;
   __syncthreads();
-  const uint32_t n_visible = counters->n_visible;
+  const uint32_t n_visible = counters->n_visible_kept;
   for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_visible;
        k += gridDim.x * kPreThreads) {
     const uint32_t vi = order[k];
@@ -642,9 +642,27 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     const float* __restrict__ logits, unsigned long long* __restrict__ vis_mask,
     float* __restrict__ g2d, uint32_t grad_mask, float* __restrict__ d_means,
     float* __restrict__ d_log_scales, float* __restrict__ d_quats, float* __restrict__ d_logits,
-    float* __restrict__ d_sh, const MapReg reg) {
+    float* __restrict__ d_sh, const MapReg reg, const float* __restrict__ pose_partial,
+    int pose_blocks, int n_views, float* __restrict__ d_pose) {
   chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
+  // Blocks 0 .. 6 V - 1 first finish the twist gradient: d_pose[v, k] = the sum over phase 1's
+  // blocks of their partials, in double precision (phase 1 is complete when this kernel runs).
+  if (d_pose && (int)blockIdx.x < 6 * n_views) {
+    const int vk = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < pose_blocks; b += kPreThreads)
+      s += (double)pose_partial[(size_t)b * n_views * 6 + vk];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double red[kPreThreads / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kPreThreads / 32; ++w) t += red[w];
+      d_pose[vk] = (float)t;
+    }
+  }
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   if (i >= n) return;
   float m[3];
@@ -864,23 +882,6 @@ __global__ void __launch_bounds__(256) reg_sum_kernel(int n, const float* __rest
   if (threadIdx.x == 0) atomicAdd(value, red[0]);
 }
 
-// d_pose[v,k] = sum over blocks of the partials, in double precision.
-__global__ void pose_finalize_kernel(const float* __restrict__ partial, int n_blocks,
-                                     int n_views, float* __restrict__ d_pose) {
-  chain_wait();
-  const int vk = blockIdx.x;  // v * 6 + k
-  double s = 0.0;
-  for (int b = threadIdx.x; b < n_blocks; b += blockDim.x) s += (double)partial[(size_t)b * n_views * 6 + vk];
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) d_pose[vk] = (float)red[0];
-}
-
 }  // namespace
 
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
@@ -952,13 +953,16 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
     RGS_LAUNCHED();
 #undef RGS_BWD_VIEW
     if (e != cudaSuccess) return e;
-    const int blocks2 = (g.n + kPreThreads - 1) / kPreThreads;
+    float* pose_out = ((grad_mask & RGS_GRAD_POSE) && d_pose) ? d_pose : nullptr;
+    const int blocks2 = std::max((g.n + kPreThreads - 1) / kPreThreads,
+                                 pose_out ? 6 * views.n_views : 1);
     const MapReg no_reg{};
 #define RGS_BWD_GAUSS(D)                                                                          \
   e = launch_chained(reg ? backward_gaussian_kernel<D, true> : backward_gaussian_kernel<D, false>, \
                      dim3(blocks2), dim3(kPreThreads), stream, views, g.n, g.means, g.log_scales, \
                      g.quats, g.opacity_logits, vis_mask, g2d, grad_mask, d_means, d_log_scales,  \
-                     d_quats, d_logits, d_sh, reg ? *reg : no_reg)
+                     d_quats, d_logits, d_sh, reg ? *reg : no_reg, (const float*)pose_partial,    \
+                     blocks1, views.n_views, pose_out)
     switch (g.sh_degree) {
       case 0: RGS_BWD_GAUSS(0); break;
       case 1: RGS_BWD_GAUSS(1); break;
@@ -979,15 +983,9 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
     }
     if (e != cudaSuccess) return e;
   }
-  if ((grad_mask & RGS_GRAD_POSE) && d_pose) {
-    if (g.n > 0) {
-      e = launch_chained(pose_finalize_kernel, dim3(views.n_views * 6), dim3(256), stream,
-                         (const float*)pose_partial, blocks1, views.n_views, d_pose);
-      RGS_LAUNCHED();
-    } else {
-      e = cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * views.n_views, stream);
-    }
-  }
+  // With Gaussians, the per-Gaussian phase above has finished the twist gradient.
+  if ((grad_mask & RGS_GRAD_POSE) && d_pose && g.n == 0)
+    e = cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * views.n_views, stream);
   return e;
 }
 

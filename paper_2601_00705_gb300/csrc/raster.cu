@@ -43,13 +43,22 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const __grid_constant__ Views views, int n, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ ntiles,
     const float4* __restrict__ rec0, const float4* __restrict__ rec1, float log2_alpha_min,
-    uint32_t capacity, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-    Counters* __restrict__ counters) {
+    uint32_t visible_cap, uint32_t capacity, uint32_t* __restrict__ keys,
+    uint32_t* __restrict__ vals, Counters* __restrict__ counters) {
   chain_wait();
   __shared__ uint32_t s_stage[kDupWarps][kDupStage];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* stage = s_stage[warp];
-  const uint32_t n_visible = counters->n_visible;
+  // The sorted list holds at most visible_cap entries; more (only possible under stream
+  // capture) are recorded in the status word. The pair count the tile sort uses is stored here.
+  const uint32_t n_visible_raw = counters->n_visible;
+  const uint32_t n_visible = min(n_visible_raw, visible_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (n_visible_raw > visible_cap) atomicOr(&counters->status, (uint32_t)kStatusVisibleOverflow);
+    counters->n_visible_kept = n_visible;
+    const uint32_t p = counters->n_pairs;
+    counters->n_pairs_stored = p < capacity ? p : capacity;
+  }
   const uint32_t sentinel = (uint32_t)views.total_tiles;
   // Lane l of global warp w takes entry k = round * 32 W + l W + w (W warps in the grid): the
   // nearest entries, whose footprints are the largest, come first in the depth order and are
@@ -174,18 +183,12 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
 
 // Keeps at most `capacity` visible entries (the sorted-list capacity under stream capture): the
 // entries beyond it are dropped from this forward and the overflow is recorded.
-__global__ void clamp_visible_kernel(Counters* counters, uint32_t capacity) {
-  chain_wait();
-  if (counters->n_visible > capacity) {
-    counters->n_visible = capacity;
-    counters->status |= kStatusVisibleOverflow;
-  }
-}
-
 __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
   chain_wait();
   const uint32_t p = counters->n_pairs;
   counters->n_pairs_stored = p < capacity ? p : capacity;
+  if (counters->n_visible > 0) atomicOr(&counters->status, (uint32_t)kStatusVisibleOverflow);
+  counters->n_visible_kept = 0;
 }
 
 // Thread t looks at the four sorted keys 4t .. 4t + 3 (one 16-byte load; the key arrays are
@@ -777,20 +780,15 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
     const unsigned blocks = (unsigned)std::min<int64_t>(need, 8 * 152);
     const cudaError_t e =
         launch_chained(duplicate_kernel, dim3(blocks), dim3(kDupThreads), stream, views, n, order,
-                       offsets, ntiles, rec0, rec1, log2_alpha_min, capacity, keys, vals,
-                       counters);
+                       offsets, ntiles, rec0, rec1, log2_alpha_min,
+                       (uint32_t)std::min<int64_t>(visible_cap, 0xffffffffll), capacity, keys,
+                       vals, counters);
     RGS_LAUNCHED();
-    if (e != cudaSuccess) return e;
+    return e;
   }
-  const cudaError_t e =
-      launch_chained(store_pair_count_kernel, dim3(1), dim3(1), stream, counters, capacity);
-  RGS_LAUNCHED();
-  return e;
-}
-
-cudaError_t launch_clamp_visible(Counters* counters, uint32_t capacity, cudaStream_t stream) {
-  const cudaError_t e =
-      launch_chained(clamp_visible_kernel, dim3(1), dim3(1), stream, counters, capacity);
+  // No visible-list capacity: nothing to duplicate, but the counts still need storing.
+  const cudaError_t e = launch_chained(store_pair_count_kernel, dim3(1), dim3(1), stream, counters,
+                                       capacity);
   RGS_LAUNCHED();
   return e;
 }

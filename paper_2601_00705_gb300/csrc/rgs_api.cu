@@ -41,7 +41,6 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              int64_t visible_cap, uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream);
-cudaError_t launch_clamp_visible(Counters* counters, uint32_t capacity, cudaStream_t stream);
 cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
                                int total_tiles, uint32_t capacity, cudaStream_t stream);
 cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, const uint2* ranges,
@@ -777,7 +776,6 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
     s->vis_cap = vn;
   }
   const int64_t vis_cap = std::min<int64_t>(s->vis_cap, vn);
-  RGS_CUDA(launch_clamp_visible(cnt, (uint32_t)vis_cap, stream), "clamp visible");
   // 3. Stable sort by depth (positive float bits order like the values; the sign bit is 0).
   bool alt = false;
   RGS_CUDA(launch_radix_sort(s->vis_keys[0], s->vis_vals[0], s->vis_keys[1], s->vis_vals[1],

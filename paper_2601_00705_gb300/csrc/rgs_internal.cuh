@@ -108,7 +108,8 @@ struct Counters {
   uint32_t status;
   uint32_t n_nonfinite;
   uint32_t n_candidates;    // entries the cull pass keeps for full projection
-  uint32_t pad[2];
+  uint32_t n_visible_kept;  // min(n_visible, visible-list capacity): the entries sorted and used
+  uint32_t pad;
   unsigned long long n_eval;     // (pixel, Gaussian) positions the forward blend visited
   unsigned long long n_contrib;  // of which composited (covering, before the stop)
 };

@@ -226,13 +226,15 @@ def test_visible_overflow_under_capture_is_reported_then_recovered():
     graph.replay()
     torch.cuda.synchronize()
     st = r.stats(state)
-    assert st["status"] & 2 and seen < st["n_visible"] < 5 * seen, (seen, st)
+    # The stats give the true visible count; the entries beyond the capacity were dropped.
+    assert st["status"] & 2 and st["n_visible"] > 5 * seen, (seen, st)
     # Outside capture the same call sizes the list from the true count and renders completely,
     # exactly as a fresh state does.
     _, _, _, state = r.forward_raw(*[full[k] for k in keys], wl.cameras, state=state, out=imgs)
     torch.cuda.synchronize()
     st2 = r.stats(state)
-    assert st2["status"] == 0 and st2["n_visible"] > st["n_visible"], st2
+    assert st2["status"] == 0 and st2["n_visible"] == st["n_visible"], st2
+    assert st2["n_pairs"] > st["n_pairs"], (st, st2)
     got = [t.clone() for t in imgs]
     r2 = Renderer(0)
     ref = r2.forward_raw(*[full[k] for k in keys], wl.cameras)
