@@ -139,7 +139,9 @@ typedef struct {
   int64_t state_bytes;     /* device bytes held by the state */
   uint32_t status;         /* device status bits: 1 = pair list overflowed its capacity;
                               2 = more visible entries than the sorted-list capacity (both only
-                              under stream capture; the output is then incomplete) */
+                              under stream capture; the output is then incomplete); 4 = a
+                              single-pass scan gave up a bounded wait for another block (the
+                              output is then wrong; not expected) */
   uint32_t kernel_launches; /* kernels launched by the last forward plus the last backward */
 } rgs_stats;
 

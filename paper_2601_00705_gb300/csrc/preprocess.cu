@@ -291,7 +291,9 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ cand,
-    Counters* __restrict__ counters, int views_per_chunk) {
+    uint32_t* __restrict__ vis_bits, int bit_words, Counters* __restrict__ counters,
+    int views_per_chunk) {
+  static_assert(kPreThreads % 32 == 0, "whole words of the visibility bitmask per block");
   chain_wait();
   __shared__ uint32_t s_cand[kPreThreads * kCullMaxViewsPerThread];
   __shared__ uint32_t s_count, s_base;
@@ -360,6 +362,11 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
       }
     }
     if (in_range) ntiles[vi] = 0u;
+    // The block's Gaussians own whole words of row v of the visibility bitmask.
+    if (threadIdx.x < kPreThreads / 32) {
+      const int w = blockIdx.x * (kPreThreads / 32) + threadIdx.x;
+      if (w < bit_words) vis_bits[(size_t)v * bit_words + w] = 0u;
+    }
     const unsigned ballot = __ballot_sync(0xffffffffu, keep);
     if (ballot) {
       const int leader = __ffs(ballot) - 1;
@@ -384,7 +391,8 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, const float* __restrict__ sh,
     const uint32_t* __restrict__ cand, float4* __restrict__ rec0, float4* __restrict__ rec1,
-    float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, Counters* __restrict__ counters) {
+    float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ vis_bits,
+    int bit_words, Counters* __restrict__ counters) {
   chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t n_cand = counters->n_candidates;
@@ -449,6 +457,7 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     rec1[vi] = r1;
     rec2[vi] = r2;
     ntiles[vi] = count;
+    if (count > 0) atomicOr(&vis_bits[(size_t)v * bit_words + (i >> 5)], 1u << (i & 31));
   }
 }
 
@@ -887,8 +896,10 @@ __global__ void __launch_bounds__(256) reg_sum_kernel(int n, const float* __rest
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
                                       float4* rec2, uint32_t* ntiles, uint32_t* cand,
-                                      Counters* counters, cudaStream_t stream) {
+                                      uint32_t* vis_bits, Counters* counters,
+                                      cudaStream_t stream) {
   if (g.n == 0) return cudaSuccess;
+  const int bit_words = (int)vis_bit_words_per_view(g.n);
   // Pass 1: one thread per (Gaussian, chunk of views), enough threads to fill every SM a few
   // times over.
   const int blocks_x = (g.n + kPreThreads - 1) / kPreThreads;
@@ -899,7 +910,7 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   const dim3 grid((unsigned)blocks_x, (unsigned)((views.n_views + per_chunk - 1) / per_chunk));
   cudaError_t e = launch_chained(cull_kernel, grid, dim3(kPreThreads), stream, views, c, g.n,
                                  g.means, g.log_scales, g.quats, g.opacity_logits, ntiles, cand,
-                                 counters, per_chunk);
+                                 vis_bits, bit_words, counters, per_chunk);
   RGS_LAUNCHED();
   if (e != cudaSuccess) return e;
   // Pass 2: grid-stride over the candidates.
@@ -909,7 +920,7 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   e = launch_chained(views.pose_dev ? project_kernel<D, true> : project_kernel<D, false>,         \
                      dim3(blocks2), dim3(kPreThreads), stream, views, c, g.n, g.means,            \
                      g.log_scales, g.quats, g.opacity_logits, g.sh, (const uint32_t*)cand, rec0, \
-                     rec1, rec2, ntiles, counters)
+                     rec1, rec2, ntiles, vis_bits, bit_words, counters)
   switch (g.sh_degree) {
     case 0: RGS_PROJECT(0); break;
     case 1: RGS_PROJECT(1); break;

@@ -26,7 +26,8 @@ namespace rgs {
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
                                       float4* rec2, uint32_t* ntiles, uint32_t* cand,
-                                      Counters* counters, cudaStream_t stream);
+                                      uint32_t* vis_bits, Counters* counters,
+                                      cudaStream_t stream);
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, unsigned long long* vis_mask,
@@ -88,6 +89,9 @@ struct State {
   uint32_t *vis_keys[2] = {nullptr, nullptr}, *vis_vals[2] = {nullptr, nullptr};
   uint32_t* offsets = nullptr;
   float* g2d = nullptr;
+  // Visibility bits of the last forward: row v (ceil(n / 32) words) has bit i set iff entry
+  // (v, i) touches a tile.
+  uint32_t* vis_bits = nullptr;
   // Per Gaussian: bit v set by the backward's phase 1 for every view v that sees it, cleared by
   // phase 2 (zero between backward calls).
   unsigned long long* vis_mask = nullptr;
@@ -240,7 +244,8 @@ rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t n, int64_t pose
     RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
     const int64_t cap = vn;
     size_t bytes = 3 * align_up(sizeof(float4) * cap) + 6 * align_up(sizeof(uint32_t) * cap) +
-                   align_up(sizeof(float) * kG2Stride * cap);
+                   align_up(sizeof(float) * kG2Stride * cap) +
+                   align_up(sizeof(uint32_t) * vis_bit_words_cap(cap));
     RGS_CUDA(alloc_region(s.r_vn, bytes), "allocate per-Gaussian buffers");
     char* p = static_cast<char*>(s.r_vn.base);
     s.rec0 = carve<float4>(p, cap);
@@ -253,6 +258,7 @@ rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t n, int64_t pose
     s.vis_vals[1] = carve<uint32_t>(p, cap);
     s.offsets = carve<uint32_t>(p, cap);
     s.g2d = carve<float>(p, kG2Stride * cap);
+    s.vis_bits = carve<uint32_t>(p, vis_bit_words_cap(cap));
     // The screen-space gradient accumulators start at zero; every backward leaves them zero.
     RGS_CUDA(cudaMemsetAsync(s.g2d, 0, sizeof(float) * kG2Stride * cap, stream), "zero g2d");
     s.vn_cap = cap;
@@ -724,15 +730,19 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   if (st != RGS_OK) return st;
   st = ensure_scratch(ctx, *s, std::max<int64_t>(vn, s->pair_cap), capturing);
   if (st != RGS_OK) return st;
-  if (!s->r_counters.base) {
-    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "state must be created outside capture");
-    RGS_CUDA(alloc_region(s->r_counters,
-                          align_up(sizeof(Counters)) + sizeof(float) * 16 * kMaxViews),
-             "allocate counters");
-    s->counters = static_cast<Counters*>(s->r_counters.base);
-    s->pose_records = reinterpret_cast<float*>(static_cast<char*>(s->r_counters.base) +
-                                               align_up(sizeof(Counters)));
+  // Pose records, then the counters and the bookkeeping of the two single-pass scans (the
+  // compaction and the pair offsets), which one memset zeroes at the start of every forward.
+  const size_t pose_bytes = align_up(sizeof(float) * 16 * kMaxViews);
+  const size_t lb_bytes = align_up(lookback_bytes(s->vn_cap));
+  const size_t reset_bytes = align_up(sizeof(Counters)) + 2 * lb_bytes;
+  if (s->r_counters.bytes < pose_bytes + reset_bytes) {
+    if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "counters grow during capture");
+    if (s->r_counters.base) RGS_CUDA(cudaDeviceSynchronize(), "sync before counters growth");
+    RGS_CUDA(alloc_region(s->r_counters, pose_bytes + reset_bytes), "allocate counters");
   }
+  s->pose_records = static_cast<float*>(s->r_counters.base);
+  s->counters = reinterpret_cast<Counters*>(static_cast<char*>(s->r_counters.base) + pose_bytes);
+  char* lb_area = reinterpret_cast<char*>(s->counters) + align_up(sizeof(Counters));
   if (world_to_cam) views.pose_dev = s->pose_records;
   s->g = *g;
   s->views = views;
@@ -741,7 +751,7 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   Counters* cnt = s->counters;
   const uint64_t launches0 = launch_counter();
   s->fwd_timed = ctx->timing;
-  RGS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), stream), "reset counters");
+  RGS_CUDA(cudaMemsetAsync(cnt, 0, reset_bytes, stream), "reset counters");
   // Tiles without pairs keep the empty range [0, 0); the range kernel writes the others.
   RGS_CUDA(cudaMemsetAsync(s->ranges, 0, sizeof(uint2) * (size_t)views.total_tiles, stream),
            "reset tile ranges");
@@ -754,12 +764,13 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   // The cull pass's candidate list lives in the depth sort's second key buffer, which is free
   // until the sort starts.
   RGS_CUDA(launch_preprocess_forward(views, consts, *g, s->rec0, s->rec1, s->rec2, s->ntiles,
-                                     s->vis_keys[1], cnt, stream),
+                                     s->vis_keys[1], s->vis_bits, cnt, stream),
            "preprocess");
   RGS_CUDA(mark(ctx, *s, 1, stream, capturing), "event");
   // 2. Visible entries with depth keys, in (view, Gaussian) order.
-  RGS_CUDA(launch_compact_visible(s->ntiles, s->rec2, vn, s->vis_keys[0], s->vis_vals[0],
-                                  &cnt->n_visible, s->block_sums, stream),
+  RGS_CUDA(launch_compact_visible(s->vis_bits, n_views, g->n, s->rec2, s->vis_keys[0],
+                                  s->vis_vals[0], &cnt->n_visible,
+                                  lookback_at(lb_area, &cnt->status, s->vn_cap), stream),
            "compact");
   RGS_CUDA(mark(ctx, *s, 2, stream, capturing), "event");
   // Size the sorted list of visible entries (outside capture: read the count back; under
@@ -786,7 +797,8 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   RGS_CUDA(mark(ctx, *s, 3, stream, capturing), "event");
   // 4. Pair offsets in depth order.
   RGS_CUDA(launch_gather_scan(s->ntiles, s->order, vis_cap, &cnt->n_visible, s->offsets,
-                              &cnt->n_pairs, s->block_sums, stream),
+                              &cnt->n_pairs, s->block_sums,
+                              lookback_at(lb_area + lb_bytes, &cnt->status, s->vn_cap), stream),
            "pair offsets");
   RGS_CUDA(mark(ctx, *s, 4, stream, capturing), "event");
   // Size the pair list (outside capture: read the count back and grow if needed).

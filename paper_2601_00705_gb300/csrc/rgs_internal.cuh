@@ -98,6 +98,7 @@ struct Consts {
 enum StatusBits : uint32_t {
   kStatusPairOverflow = 1u,     // the pair list outgrew its capacity
   kStatusVisibleOverflow = 2u,  // the visible entries outgrew the sorted-list capacity
+  kStatusScanWait = 4u,         // a single-pass scan gave up waiting for an earlier block
 };
 
 // Device counters of one forward.
@@ -432,22 +433,54 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
+// Bookkeeping of one single-pass scan (chained scan with decoupled look-back): a ticket counter
+// and one 64-bit state word per tile of kScanTile elements, all zero before the launch.
+struct Lookback {
+  uint32_t* ticket = nullptr;
+  unsigned long long* tiles = nullptr;  // null: the scan runs without look-back
+  uint32_t* status = nullptr;           // kStatusScanWait is recorded here
+  int64_t capacity = 0;                 // tile states in the area
+};
+// Visibility bitmask of a forward: one row of vis_bit_words_per_view(n) words per view, bit i of
+// row v set iff entry (v, i) touches a tile. The allocation for up to vn_cap entries holds every
+// n_views x n layout with n_views * n <= vn_cap.
+inline int64_t vis_bit_words_per_view(int64_t n) { return (n + 31) / 32; }
+inline int64_t vis_bit_words_cap(int64_t vn_cap) { return (vn_cap + 31) / 32 + kMaxViews; }
+
+// Tile states of one Lookback area serving up to n_cap elements: a scan of n_cap elements
+// takes scan_blocks(n_cap) tiles; the bitmask compaction of n_views x n <= n_cap entries
+// (tiles of 256 words, n_views <= RGS_MAX_VIEWS <= 256) takes at most n_cap / 8192 + 2.
+static_assert(RGS_MAX_VIEWS <= 256, "bound of the bitmask compaction's tiles");
+inline int64_t lookback_tiles(int64_t n_cap) { return scan_blocks(n_cap) + 2; }
+// Bytes of one Lookback area (a 16-byte header, then the tile states).
+inline size_t lookback_bytes(int64_t n_cap) { return 16 + 8 * (size_t)lookback_tiles(n_cap); }
+inline Lookback lookback_at(void* area, uint32_t* status, int64_t n_cap) {
+  Lookback lb;
+  lb.ticket = static_cast<uint32_t*>(area);
+  lb.tiles = reinterpret_cast<unsigned long long*>(static_cast<char*>(area) + 16);
+  lb.status = status;
+  lb.capacity = lookback_tiles(n_cap);
+  return lb;
+}
+
 // Exclusive scan of in[0..n) (n read from n_dev if non-null, capped at n_cap) into out, total
 // into *total (may be null).
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_cap,
                                   const uint32_t* n_dev, uint32_t* total, uint32_t* block_sums,
                                   cudaStream_t stream);
 
-// Compaction of visible entries: for vi in [0, n) with ntiles[vi] > 0, writes
-// keys[pos] = float bits of rec2[vi].w (depth), vals[pos] = vi, count into *n_out.
-cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec2, int64_t n,
-                                   uint32_t* keys, uint32_t* vals, uint32_t* n_out,
-                                   uint32_t* block_sums, cudaStream_t stream);
+// Compaction of the visible entries, in (view, Gaussian) order: for every set bit i of row v of
+// the visibility bitmask (n_views rows for n Gaussians), writes keys[pos] = float bits of
+// rec2[v n + i].w (depth) and vals[pos] = v n + i; the count into *n_out. One single-pass
+// launch; lb must be zeroed.
+cudaError_t launch_compact_visible(const uint32_t* vis_bits, int n_views, int n,
+                                   const float4* rec2, uint32_t* keys, uint32_t* vals,
+                                   uint32_t* n_out, Lookback lb, cudaStream_t stream);
 
 // offs[k] = exclusive scan of ntiles[order[k]] for k < *n_dev; total into *total.
 cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, int64_t n_cap,
                                const uint32_t* n_dev, uint32_t* offs, uint32_t* total,
-                               uint32_t* block_sums, cudaStream_t stream);
+                               uint32_t* block_sums, Lookback lb, cudaStream_t stream);
 
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;       // keys per thread for large sorts (2048 per block)

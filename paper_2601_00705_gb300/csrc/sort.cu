@@ -1,9 +1,10 @@
 // sort.cu -- prefix scans, visibility compaction and the stable LSD radix sort that build the
 // front-to-back ordered covering lists (Section 3.1: per pixel, the covering Gaussians near to
 // far). All scans are reduce-then-scan (three kernels, no inter-block waiting), so no kernel
-// here ever spins on another block. Sorts that fit in the shared memory of one thread-block
-// cluster run as a single launch whose blocks meet only at the hardware cluster barrier (the
-// blocks of a cluster are co-scheduled by construction).
+// here ever spins on another block, except the single-pass scan, whose waits are bounded and
+// only ever on blocks that have already started. Sorts that fit in the shared memory of one
+// thread-block cluster run as a single launch whose blocks meet only at the hardware cluster
+// barrier (the blocks of a cluster are co-scheduled by construction).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -69,10 +70,6 @@ struct PlainLoad {
   const uint32_t* in;
   __device__ uint32_t operator()(uint32_t k) const { return in[k]; }
 };
-struct FlagLoad {
-  const uint32_t* in;
-  __device__ uint32_t operator()(uint32_t k) const { return in[k] > 0u ? 1u : 0u; }
-};
 struct GatherLoad {
   const uint32_t* in;
   const uint32_t* order;
@@ -134,17 +131,6 @@ struct PlainStore {
   __device__ void operator()(uint32_t k, uint32_t value, uint32_t prefix) const {
     (void)value;
     out[k] = prefix;
-  }
-};
-struct CompactStore {
-  const float4* rec2;  // .w = depth
-  uint32_t* keys;
-  uint32_t* vals;
-  __device__ void operator()(uint32_t k, uint32_t value, uint32_t prefix) const {
-    if (value) {
-      keys[prefix] = __float_as_uint(rec2[k].w);
-      vals[prefix] = k;
-    }
   }
 };
 
@@ -322,17 +308,194 @@ bool try_cluster_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_d
   return true;
 }
 
-// Exclusive scan of the loaded values: one cluster launch when they fit in a cluster's shared
-// memory (held as T), else three kernels.
+// ------------------------------------------------------------------------------------------
+// Single-pass scan: the chained scan with decoupled look-back of Merrill and Garland
+// ("Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016), in one launch of one
+// block per tile of kScanTile elements. A block takes its tile from a ticket counter, so tiles
+// are handed out in the order blocks start: a block only ever waits for tiles of blocks that
+// are already running, which therefore finish. It scans its tile, publishes the tile total (an
+// "aggregate") and, unless it is tile 0, walks back over the earlier tiles 32 at a time (one per
+// lane of warp 0), adding aggregates until it meets a published inclusive prefix; then it
+// publishes its own inclusive prefix and stores its results. A state word packs the flag in bits 62..63 (0 not yet published, 1 aggregate,
+// 2 inclusive prefix) and the value in bits 0..31. It is written and read whole (an aligned
+// 64-bit access), and nothing else is published through it, so relaxed accesses suffice. Each
+// wait is bounded: past kLookbackSpins polls the block records kStatusScanWait and takes the
+// tile as 0 (a wrong result, reported; never expected, since the waited-for block is running).
+// ------------------------------------------------------------------------------------------
+constexpr unsigned long long kTileAggregate = 1ull << 62, kTileInclusive = 2ull << 62;
+constexpr int kLookbackSpins = 1 << 22;
+
+__device__ __forceinline__ void store_state(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long load_state(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Takes a tile from the ticket counter (thread 0; the result is broadcast to the block).
+__device__ __forceinline__ uint32_t lookback_ticket(const Lookback& lb) {
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(lb.ticket, 1u);
+  __syncthreads();
+  return s_tile;
+}
+
+// Called by the 32 lanes of warp 0 of the block holding tile b, whose elements sum to agg:
+// publishes the aggregate, looks back for the exclusive prefix of the tile, publishes the
+// inclusive prefix and returns the exclusive one (in every lane).
+__device__ uint32_t lookback_prefix(const Lookback& lb, uint32_t b, uint32_t agg) {
+  const int lane = threadIdx.x & 31;
+  if (b == 0) {
+    if (lane == 0) store_state(&lb.tiles[0], kTileInclusive | agg);
+    return 0u;
+  }
+  if (lane == 0) store_state(&lb.tiles[b], kTileAggregate | agg);
+  uint32_t prefix = 0;
+  bool timed_out = false;
+  for (int64_t end = b; end > 0; end -= 32) {
+    const int64_t j = end - 1 - lane;  // lane 0 looks at the nearest earlier tile
+    unsigned long long w = kTileInclusive;  // before tile 0: an empty inclusive prefix
+    if (j >= 0) {
+      w = load_state(&lb.tiles[j]);
+      for (int spin = 0; (w >> 62) == 0; ++spin) {
+        if (spin >= kLookbackSpins) {
+          timed_out = true;
+          w = kTileInclusive;
+          break;
+        }
+        __nanosleep(32);
+        w = load_state(&lb.tiles[j]);
+      }
+    }
+    const uint32_t inclusive = __ballot_sync(0xffffffffu, (w >> 62) == 2ull);
+    // Tiles nearer than the nearest inclusive prefix contribute their aggregates, that prefix
+    // contributes itself, and the farther tiles nothing.
+    const int stop = inclusive ? __ffs(inclusive) - 1 : 32;
+    uint32_t x = lane <= stop ? (uint32_t)w : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    prefix += x;
+    if (inclusive) break;
+  }
+  if (__any_sync(0xffffffffu, timed_out) && lane == 0)
+    atomicOr(lb.status, (uint32_t)kStatusScanWait);
+  if (lane == 0) store_state(&lb.tiles[b], kTileInclusive | (prefix + agg));
+  return prefix;
+}
+
+template <typename Load, typename Store>
+__global__ void __launch_bounds__(kScanThreads) lookback_scan_kernel(Load load, Store store,
+                                                                     int64_t n_cap,
+                                                                     const uint32_t* n_dev,
+                                                                     uint32_t* total,
+                                                                     Lookback lb,
+                                                                     uint32_t n_tiles) {
+  chain_wait();
+  __shared__ uint32_t s_prefix;
+  const uint32_t b = lookback_ticket(lb);
+  if (b >= n_tiles) {  // the ticket counter was not zeroed: report, touch nothing
+    if (threadIdx.x == 0) atomicOr(lb.status, (uint32_t)kStatusScanWait);
+    return;
+  }
+  const uint32_t n = read_count(n_dev, n_cap);
+  const int64_t base = (int64_t)b * kScanTile;
+  // Thread t owns the kScanItems consecutive elements base + t * kScanItems + k.
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + k;
+    v[k] = idx < n ? load((uint32_t)idx) : 0u;
+    s += v[k];
+  }
+  uint32_t agg;
+  const uint32_t excl = block_exclusive_scan<kScanThreads>(s, &agg);
+  if (threadIdx.x < 32) {
+    const uint32_t prefix = lookback_prefix(lb, b, agg);
+    if (threadIdx.x == 0) s_prefix = prefix;
+  }
+  __syncthreads();
+  uint32_t pre = s_prefix + excl;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + k;
+    if (idx < n) store((uint32_t)idx, v[k], pre);
+    pre += v[k];
+  }
+  if (b == n_tiles - 1 && threadIdx.x == 0 && total) *total = s_prefix + agg;
+}
+
+// ------------------------------------------------------------------------------------------
+// Compaction of the visible entries from the visibility bitmask, one single-pass launch. A
+// tile is kBitsThreads words, one per thread (coalesced loads). The exclusive prefix of the set
+// bits over the threads gives each thread the tile-local position of its first visible entry;
+// it writes its entries' indices there, in bit order, into a shared-memory list, while warp 0
+// finds the tile's offset by look-back. The block then stores the list with every thread:
+// independent loads of the depths, contiguous stores. Words are taken in (view, word) order and
+// bits from the lowest, so the output follows (view, Gaussian) order.
+// ------------------------------------------------------------------------------------------
+constexpr int kBitsThreads = 256;
+
+__global__ void __launch_bounds__(kBitsThreads) compact_bits_kernel(
+    const uint32_t* __restrict__ vis_bits, uint32_t n_words, uint32_t words_per_view, uint32_t n,
+    const float4* __restrict__ rec2, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+    uint32_t* __restrict__ n_out, Lookback lb, uint32_t n_tiles) {
+  chain_wait();
+  __shared__ uint32_t s_list[kBitsThreads * 32];
+  __shared__ uint32_t s_prefix;
+  const uint32_t b = lookback_ticket(lb);
+  if (b >= n_tiles) {  // the ticket counter was not zeroed: report, touch nothing
+    if (threadIdx.x == 0) atomicOr(lb.status, (uint32_t)kStatusScanWait);
+    return;
+  }
+  const uint32_t gw = b * kBitsThreads + threadIdx.x;
+  uint32_t m = gw < n_words ? vis_bits[gw] : 0u;
+  uint32_t agg;
+  uint32_t pos = block_exclusive_scan<kBitsThreads>((uint32_t)__popc(m), &agg);
+  if (threadIdx.x < 32) {
+    const uint32_t prefix = lookback_prefix(lb, b, agg);
+    if (threadIdx.x == 0) s_prefix = prefix;
+  }
+  if (m) {
+    const uint32_t v = gw / words_per_view;
+    const uint32_t first = v * n + (gw - v * words_per_view) * 32u;
+    while (m) {
+      s_list[pos++] = first + (uint32_t)(__ffs(m) - 1);
+      m &= m - 1u;
+    }
+  }
+  __syncthreads();
+  const uint32_t prefix = s_prefix;
+  for (uint32_t t = threadIdx.x; t < agg; t += kBitsThreads) {
+    const uint32_t vi = s_list[t];
+    keys[prefix + t] = __float_as_uint(rec2[vi].w);
+    vals[prefix + t] = vi;
+  }
+  if (b == n_tiles - 1 && threadIdx.x == 0) *n_out = prefix + agg;
+}
+
+// Exclusive scan of the loaded values: one single-pass launch when look-back bookkeeping is
+// given; else one cluster launch when they fit in a cluster's shared memory (held as T); else
+// three kernels.
 template <typename Load, typename Store, typename T = uint32_t>
 cudaError_t run_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_dev,
-                     uint32_t* total, uint32_t* block_sums, cudaStream_t stream) {
+                     uint32_t* total, uint32_t* block_sums, cudaStream_t stream,
+                     Lookback lb = Lookback{}) {
   const int64_t nb = scan_blocks(n_cap);
   if (nb == 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), stream);
     return cudaSuccess;
   }
   cudaError_t e = cudaSuccess;
+  if (lb.tiles) {
+    if (nb > lb.capacity) return cudaErrorInvalidValue;
+    e = launch_chained(lookback_scan_kernel<Load, Store>, dim3((unsigned)nb), dim3(kScanThreads),
+                       stream, load, store, n_cap, n_dev, total, lb, (uint32_t)nb);
+    RGS_LAUNCHED();
+    return e;
+  }
   if (try_cluster_scan<Load, Store, T>(load, store, n_cap, n_dev, total, stream, &e)) return e;
   e = launch_chained(scan_reduce_kernel<Load>, dim3((unsigned)nb), dim3(kScanThreads),
                                  stream, load, n_cap, n_dev, block_sums);
@@ -648,18 +811,26 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_c
   return run_scan(PlainLoad{in}, PlainStore{out}, n_cap, n_dev, total, block_sums, stream);
 }
 
-cudaError_t launch_compact_visible(const uint32_t* ntiles, const float4* rec2, int64_t n,
-                                   uint32_t* keys, uint32_t* vals, uint32_t* n_out,
-                                   uint32_t* block_sums, cudaStream_t stream) {
-  return run_scan<FlagLoad, CompactStore, uint8_t>(FlagLoad{ntiles}, CompactStore{rec2, keys, vals},
-                                                   n, nullptr, n_out, block_sums, stream);
+cudaError_t launch_compact_visible(const uint32_t* vis_bits, int n_views, int n,
+                                   const float4* rec2, uint32_t* keys, uint32_t* vals,
+                                   uint32_t* n_out, Lookback lb, cudaStream_t stream) {
+  const int64_t words = (int64_t)n_views * vis_bit_words_per_view(n);
+  if (words == 0) return cudaMemsetAsync(n_out, 0, sizeof(uint32_t), stream);
+  const int64_t tiles = (words + kBitsThreads - 1) / kBitsThreads;
+  if (tiles > lb.capacity) return cudaErrorInvalidValue;
+  const cudaError_t e = launch_chained(
+      compact_bits_kernel, dim3((unsigned)tiles), dim3(kBitsThreads), stream, vis_bits,
+      (uint32_t)words, (uint32_t)vis_bit_words_per_view(n), (uint32_t)n, rec2, keys, vals, n_out,
+      lb, (uint32_t)tiles);
+  RGS_LAUNCHED();
+  return e;
 }
 
 cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, int64_t n_cap,
                                const uint32_t* n_dev, uint32_t* offs, uint32_t* total,
-                               uint32_t* block_sums, cudaStream_t stream) {
+                               uint32_t* block_sums, Lookback lb, cudaStream_t stream) {
   return run_scan(GatherLoad{ntiles, order}, PlainStore{offs}, n_cap, n_dev, total, block_sums,
-                  stream);
+                  stream, lb);
 }
 
 template <int ITEMS>

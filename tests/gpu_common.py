@@ -48,6 +48,8 @@ def gpu_render(g, cams, d_color=None, d_depth=None, d_alpha=None, grad_mask=bind
                depth=depth.cpu().numpy().astype(np.float64),
                alpha=alpha.cpu().numpy().astype(np.float64))
     out["stats"] = r.stats(state)
+    # No overflow (bits 1, 2) and no abandoned wait in a single-pass scan (bit 4).
+    assert out["stats"]["status"] == 0, out["stats"]
     if d_color is not None or d_depth is not None or d_alpha is not None:
         n = g["means"].shape[0]
         K = g["sh"].shape[1]
