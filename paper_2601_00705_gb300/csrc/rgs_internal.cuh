@@ -283,10 +283,14 @@ constexpr float kLog2e = 1.4426950408889634f;
 // Tile coverage of a projected Gaussian: the tiles whose pixel centres may lie inside the
 // alpha >= alpha_min ellipse {d : d^T Q d <= kappa} (Q = conic), padded by kTilePad pixels so
 // that the per-pixel FP32 test in the blend can never find a covered pixel outside the listed
-// tiles. Visits tile rows ty0..ty1 and, per row, the column span [tx0, tx1] of the ellipse
-// restricted to the row's pixel band.
+// tiles. The two tests differ only by rounding: a few ulps relative to the footprint's extent
+// (the blend adds the low part of the mean, below 1e-4 px; the extent here comes from
+// approximate reciprocals and square roots), and kappa is already widened by 1e-4 relative
+// below, so a sixteenth of a pixel is a wide margin. Each listed tile without a covered pixel
+// costs a full pass over the tile in both blends. Visits tile rows ty0..ty1 and, per row, the
+// column span [tx0, tx1] of the ellipse restricted to the row's pixel band.
 // ------------------------------------------------------------------------------------------
-constexpr float kTilePad = 1.0f;
+constexpr float kTilePad = 0.0625f;
 
 struct Ellipse {
   float mx, my;           // centre

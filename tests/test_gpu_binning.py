@@ -74,3 +74,73 @@ def test_long_tile_runs_are_merged_in_order_with_depth_ties():
     orc = oracle.render(g, wl.cameras)
     gpu = gpu_render(g, wl.cameras)
     print("crowded", max_run, compare_forward(gpu, orc), gpu["stats"])
+
+
+def _uncovered_pixels(name, sample=None, eps=1e-4, seed=0):
+    """Pixels that the blend's coverage test could accept but whose tile is not listed for the
+    entry: for each sampled entry, every pixel whose exponent (the blend's quadratic form of
+    Eq. alpha in base 2, from the GPU's own records, in float64) lies above log2(alpha_min) - eps
+    must be in one of the entry's listed tiles. The FP32 exponent differs from this one by a few
+    1e-6 at the boundary, so a complete list passes with a wide margin."""
+    wl = synthetic.make(name)
+    g = wl.gaussians.as_dict()
+    n = g["means"].shape[0]
+    V = len(wl.cameras)
+    r, color, depth, alpha, state = gpu_forward(g, wl.cameras)
+    tiles_x = [(c["width"] + 15) // 16 for c in wl.cameras]
+    tiles_per_view = [tx * ((c["height"] + 15) // 16) for tx, c in zip(tiles_x, wl.cameras)]
+    total_tiles = int(sum(tiles_per_view))
+    vals, ranges = r.ctx.tile_lists(state, total_tiles)
+    rec, ntiles = r.ctx.records(state, V * n)
+    r.release(state)
+    nonempty = ranges[:, 1] > ranges[:, 0]
+    starts, ends = ranges[nonempty, 0].astype(np.int64), ranges[nonempty, 1].astype(np.int64)
+    tile_of = np.repeat(np.nonzero(nonempty)[0], ends - starts)
+    order = np.argsort(vals, kind="stable")
+    s_vals, s_tiles = vals[order], tile_of[order]
+    entries = np.nonzero(ntiles > 0)[0]
+    if sample is not None and entries.size > sample:
+        entries = np.sort(np.random.default_rng(seed).choice(entries, sample, replace=False))
+    lo = np.searchsorted(s_vals, entries, "left")
+    hi = np.searchsorted(s_vals, entries, "right")
+    view_base = np.concatenate([[0], np.cumsum(tiles_per_view)])
+    log2_amin = np.log2(np.float64(np.float32(1.0 / 255.0)))
+    missing, checked = [], 0
+    for e, a, b in zip(entries, lo, hi):
+        listed = set(s_tiles[a:b].tolist())
+        v = int(e // n)
+        W, H = int(wl.cameras[v]["width"]), int(wl.cameras[v]["height"])
+        r0 = rec[e].astype(np.float64)
+        mx, my = r0[0] + r0[2], r0[1] + r0[3]
+        qa, qb, qc, l2o = r0[4], r0[5], r0[6], r0[7]
+        # Pixels with A dx^2 + B dx dy + C dy^2 <= k (A = -qa, B = -qb, C = -qc).
+        A, B, C, k = -qa, -qb, -qc, l2o - (log2_amin - eps)
+        det = 4.0 * A * C - B * B
+        if k < 0 or not (A > 0 and det > 0):
+            continue
+        ry = np.sqrt(4.0 * A * k / det)
+        ys = np.arange(max(0, int(np.ceil(my - ry))), min(H - 1, int(np.floor(my + ry))) + 1)
+        if ys.size == 0:
+            continue
+        dy = ys - my
+        disc = (B * dy) ** 2 - 4.0 * A * (C * dy * dy - k)
+        ok = disc >= 0
+        sq = np.sqrt(np.maximum(disc, 0.0))
+        xl = np.maximum(np.ceil(mx + (-B * dy - sq) / (2 * A)), 0).astype(np.int64)
+        xr = np.minimum(np.floor(mx + (-B * dy + sq) / (2 * A)), W - 1).astype(np.int64)
+        for y, l, rr, good in zip(ys, xl, xr, ok):
+            if not good or l > rr:
+                continue
+            for tx in range(l // 16, rr // 16 + 1):
+                checked += 1
+                t = int(view_base[v] + (y // 16) * tiles_x[v] + tx)
+                if t not in listed:
+                    missing.append((int(e), int(y), int(tx)))
+    return missing, checked
+
+
+@pytest.mark.parametrize("name,sample", [("tiny", None), ("tum", 3000)])
+def test_tile_lists_hold_every_pixel_the_blend_can_cover(name, sample):
+    missing, checked = _uncovered_pixels(name, sample)
+    assert checked > 1000
+    assert not missing, missing[:10]
