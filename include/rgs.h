@@ -494,6 +494,25 @@ rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
 rgs_status rgs_exclusive_scan_u32_static(const uint32_t* in, uint32_t* out, int64_t n,
                                          uint32_t* total_out, void* stream);
 
+/* Single-pass exclusive scan (the forward's compaction and pair offsets run on it): one launch,
+ * the blocks chaining their prefixes by decoupled look-back (Merrill and Garland, 2016) through
+ * caller-owned bookkeeping, so that nothing is allocated and nothing synchronises.
+ *   in, out: device u32 arrays of n elements (out may equal in); total_out: device u32 or NULL.
+ *   n: 0 <= n < 2^31.
+ *   work: device memory of at least rgs_single_pass_scan_bytes(n) bytes, 16-byte aligned, ALL
+ *     ZERO when the scan starts (e.g. cudaMemsetAsync on the same stream); the scan leaves it
+ *     non-zero. work_bytes: its size.
+ *   status: device u32; the scan ORs in 4 if a block gave up its bounded wait (about a second)
+ *     for an earlier block's prefix. That is never expected; it means the work area was not
+ *     zero or the device is not running the earlier blocks, and the output is then wrong.
+ *   stream: cudaStream_t as void*. Asynchronous: no host synchronisation.
+ * Returns RGS_ERR_INVALID_ARG for null or misaligned pointers, a negative or too large n or a
+ * small work area, before any GPU work; RGS_ERR_CUDA if the launch fails. */
+int64_t rgs_single_pass_scan_bytes(int64_t n);
+rgs_status rgs_exclusive_scan_u32_single_pass(const uint32_t* in, uint32_t* out, int64_t n,
+                                              uint32_t* total_out, void* work, int64_t work_bytes,
+                                              uint32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ EXPORTED = ("rgs_create", "rgs_destroy", "rgs_config_default", "rgs_last_error",
             "rgs_track_config_default", "rgs_adam_config_default", "rgs_track_grad_weight",
             "rgs_track_loss", "rgs_pose_adam_step", "rgs_seed_config_default", "rgs_triangulate",
             "rgs_init_seeds", "rgs_covisibility", "rgs_render_backward_mapping", "rgs_map_ema",
-            "rgs_prune_config_default", "rgs_prune_mask")
+            "rgs_prune_config_default", "rgs_prune_mask", "rgs_single_pass_scan_bytes",
+            "rgs_exclusive_scan_u32_single_pass")
 
 PHASES = ("preprocess", "compact", "depth_sort", "offsets", "duplicate", "tile_sort", "ranges",
           "blend_forward", "blend_backward", "preprocess_backward")
@@ -142,6 +143,8 @@ def load(build_if_needed: bool = True):
             "rgs_radix_sort_u32": (S, [P, P, P, I64, I32, I32, P]),
             "rgs_exclusive_scan_u32": (S, [P, P, P, I64, P, P]),
             "rgs_exclusive_scan_u32_static": (S, [P, P, I64, P, P]),
+            "rgs_single_pass_scan_bytes": (I64, [I64]),
+            "rgs_exclusive_scan_u32_single_pass": (S, [P, P, I64, P, P, I64, P, P]),
             "rgs_copy_tile_lists": (S, [P, U64, P, I64, P, ctypes.POINTER(I64), P]),
             "rgs_copy_records": (S, [P, U64, P, P, P]),
             "rgs_autotune": (S, [P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), I32,

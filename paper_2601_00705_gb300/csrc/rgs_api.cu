@@ -1110,6 +1110,30 @@ rgs_status rgs_exclusive_scan_u32(rgs_ctx* ctx, const uint32_t* in, uint32_t* ou
   return RGS_OK;
 }
 
+int64_t rgs_single_pass_scan_bytes(int64_t n) {
+  return n < 0 ? 0 : (int64_t)lookback_bytes(n);
+}
+
+rgs_status rgs_exclusive_scan_u32_single_pass(const uint32_t* in, uint32_t* out, int64_t n,
+                                              uint32_t* total_out, void* work, int64_t work_bytes,
+                                              uint32_t* status, void* stream_ptr) {
+  if (n < 0 || n >= (1ll << 31) || (n > 0 && (!in || !out)) || !work || !status ||
+      (reinterpret_cast<uintptr_t>(work) & 15u) != 0 ||
+      work_bytes < rgs_single_pass_scan_bytes(n))
+    return RGS_ERR_INVALID_ARG;
+  if (n == 0) {
+    if (total_out &&
+        cudaMemsetAsync(total_out, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream_ptr)) !=
+            cudaSuccess)
+      return RGS_ERR_CUDA;
+    return RGS_OK;
+  }
+  Lookback lb = lookback_at(work, status, n);
+  const cudaError_t e = launch_exclusive_scan_single_pass(
+      in, out, n, total_out, lb, static_cast<cudaStream_t>(stream_ptr));
+  return e == cudaSuccess ? RGS_OK : RGS_ERR_CUDA;
+}
+
 }  // extern "C"
 
 // ---- Tracking step ----

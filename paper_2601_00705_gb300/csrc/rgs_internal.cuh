@@ -473,6 +473,10 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_c
                                   const uint32_t* n_dev, uint32_t* total, uint32_t* block_sums,
                                   cudaStream_t stream);
 
+// The same scan in one launch through zeroed look-back bookkeeping.
+cudaError_t launch_exclusive_scan_single_pass(const uint32_t* in, uint32_t* out, int64_t n,
+                                              uint32_t* total, Lookback lb, cudaStream_t stream);
+
 // Compaction of the visible entries, in (view, Gaussian) order: for every set bit i of row v of
 // the visibility bitmask (n_views rows for n Gaussians), writes keys[pos] = float bits of
 // rec2[v n + i].w (depth) and vals[pos] = v n + i; the count into *n_out. One single-pass

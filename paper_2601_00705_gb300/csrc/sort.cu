@@ -323,7 +323,7 @@ bool try_cluster_scan(Load load, Store store, int64_t n_cap, const uint32_t* n_d
 // tile as 0 (a wrong result, reported; never expected, since the waited-for block is running).
 // ------------------------------------------------------------------------------------------
 constexpr unsigned long long kTileAggregate = 1ull << 62, kTileInclusive = 2ull << 62;
-constexpr int kLookbackSpins = 1 << 22;
+constexpr int kLookbackSpins = 1 << 20;  // polls of ~1 us each
 
 __device__ __forceinline__ void store_state(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -809,6 +809,11 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n_c
                                   const uint32_t* n_dev, uint32_t* total, uint32_t* block_sums,
                                   cudaStream_t stream) {
   return run_scan(PlainLoad{in}, PlainStore{out}, n_cap, n_dev, total, block_sums, stream);
+}
+
+cudaError_t launch_exclusive_scan_single_pass(const uint32_t* in, uint32_t* out, int64_t n,
+                                              uint32_t* total, Lookback lb, cudaStream_t stream) {
+  return run_scan(PlainLoad{in}, PlainStore{out}, n, nullptr, total, nullptr, stream, lb);
 }
 
 cudaError_t launch_compact_visible(const uint32_t* vis_bits, int n_views, int n,
