@@ -51,8 +51,8 @@ BWD_FLOP_PER_EVAL = 40
 # this kernel build on exactly this workload and tile configuration; any other combination
 # reports null. Keyed by (workload, kernel, tile_w x tile_h x pixels per thread).
 MEASURED_TRAFFIC: dict[tuple[str, str, str], float] = {
-    ("tum", "blend_backward", "16x16x8"): 79.6e6,
-    ("tum", "blend_forward", "16x16x4"): 46.1e6,
+    ("tum", "blend_backward", "16x16x8"): 79.5e6,
+    ("tum", "blend_forward", "16x16x4"): 45.7e6,
 }
 
 
@@ -694,8 +694,20 @@ def run_ours(args, world, rank, local):
                     "peak_source": f"FP32 FMA pipe: 128 lanes x 2 FLOP x {props.multi_processor_count}"
                                    f" SMs x {sm_max:.0f} MHz ({peak_src} max SM clock)"}
     else:
-        roofline = {"kernel": dominant, "bound": "hbm", "achieved": None,
-                    "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "frac": None,
+        # Byte models of the other phases (algorithmic bytes per step): the backward preprocess
+        # reads and writes a 64-byte record per visible entry and reads the parameters and
+        # writes their gradients once per Gaussian (11 + 3K floats each way); the forward
+        # preprocess reads the parameters once and writes 52 bytes per candidate entry.
+        param_bytes = 4 * (11 + 3 * K)
+        bytes_model = {
+            "preprocess_backward": 64 * stats["n_visible"] + 2 * param_bytes * n,
+            "preprocess": param_bytes * n + 4 * V * n + 52 * stats["n_visible"],
+        }
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = (bytes_model[dominant] / (phases[dominant] / 1e3) / 1e9
+                    if dominant in bytes_model else None)
+        roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm if achieved is not None else None,
                     "traffic": None}
 
     line = {
