@@ -606,8 +606,11 @@ def run_ours(args, world, rank, local):
     d2h += sum(t.numel() * 4 for t in img_host)
 
     # The copies that do not feed the next kernel overlap with compute, on streams of their own:
-    # the upstream gradients travel during the forward, the images come back during the backward.
+    # the SH coefficients travel while the forward projects and sorts (it waits for them only
+    # where it first reads them, through sh_event), the upstream gradients during the rest of
+    # the forward, and the images come back during the backward.
     s_params, s_upstream, s_images = (torch.cuda.Stream(dev) for _ in range(3))
+    sh_done = torch.cuda.Event()
 
     def step_e2e(st):
         cur = torch.cuda.current_stream(dev)
@@ -615,17 +618,20 @@ def run_ours(args, world, rank, local):
             s_.wait_stream(cur)
         with torch.cuda.stream(s_params):
             p = [pin[k].to(dev, non_blocking=True)
-                 for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
-        # The upstream gradients queue behind the parameters, so that the forward starts as
-        # soon as its own inputs have arrived.
+                 for k in ("means", "log_scales", "quats", "opacity_logits")]
+        cur.wait_stream(s_params)  # the geometry only
+        with torch.cuda.stream(s_params):
+            p.append(pin["sh"].to(dev, non_blocking=True))
+            sh_done.record(s_params)
+        # The upstream gradients queue behind the parameters, so that each copy starts once the
+        # link is free for it.
         s_upstream.wait_stream(s_params)
         with torch.cuda.stream(s_upstream):
             uc = up_pin[0].to(dev, non_blocking=True)
             ud = up_pin[1].to(dev, non_blocking=True) if wl.depth_weight else None
-        cur.wait_stream(s_params)
         for t in p:
             t.record_stream(cur)
-        c, d, a, st = r.forward_raw(*p, cams, state=st)
+        c, d, a, st = r.forward_raw(*p, cams, state=st, sh_event=sh_done)
         s_images.wait_stream(cur)
         with torch.cuda.stream(s_images):
             for hbuf, dbuf in zip(img_host, (c, d, a)):

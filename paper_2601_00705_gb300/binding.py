@@ -56,7 +56,8 @@ class Config(ctypes.Structure):
                 ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("pixels_per_thread", ctypes.c_int32),
-                ("backward_pixels_per_thread", ctypes.c_int32)]
+                ("backward_pixels_per_thread", ctypes.c_int32),
+                ("sh_ready_event", ctypes.c_void_p)]
 
 
 class Images(ctypes.Structure):

@@ -383,25 +383,25 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
 }
 
 // Forward, pass 2 (project): one thread per candidate entry (grid-stride). Full projection
-// (Eq. proj), colour (Eq. app-sh) and tile count; writes the entry's records and tile count.
-// Entries that are not candidates keep ntiles = 0 and unwritten records.
-template <int DEG, bool kDevPose>
+// (Eq. proj) and tile count; writes the entry's records (depth in rec2.w; the colour follows in
+// colour_kernel, for the visible entries only) and tile count. Entries that are not candidates
+// keep ntiles = 0 and unwritten records.
+template <bool kDevPose>
 __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ logits, const float* __restrict__ sh,
-    const uint32_t* __restrict__ cand, float4* __restrict__ rec0, float4* __restrict__ rec1,
-    float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ vis_bits,
-    int bit_words, Counters* __restrict__ counters) {
+    const float* __restrict__ logits, const uint32_t* __restrict__ cand,
+    float4* __restrict__ rec0, float4* __restrict__ rec1, float4* __restrict__ rec2,
+    uint32_t* __restrict__ ntiles, uint32_t* __restrict__ vis_bits, int bit_words,
+    Counters* __restrict__ counters) {
   chain_wait();
-  constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t n_cand = counters->n_candidates;
   for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_cand;
        k += gridDim.x * kPreThreads) {
     const uint32_t vi = cand[k];
     const int v = (int)(vi / (uint32_t)n);
     const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
-    float m[3], ls[3], q[4], shc[3 * K];
+    float m[3], ls[3], q[4];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       m[a] = __ldg(means + 3 * (size_t)i + a);
@@ -412,14 +412,6 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     q[1] = q4.y;
     q[2] = q4.z;
     q[3] = q4.w;
-    load_sh<DEG>(sh, i, shc);
-    bool sh_finite = true;
-#pragma unroll
-    for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
-    if (!sh_finite) {
-      atomicAdd(&counters->n_nonfinite, 1u);
-      continue;
-    }
     GaussianLocal g;
     gaussian_local(m, ls, q, __ldg(logits + i), g);
     const ViewParams& vp = views.v[v];
@@ -430,9 +422,54 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const float4 r1 =
         make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
                     __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
-    // Colour from SH of the direction camera centre -> Gaussian (Eq. app-sh).
-    float d0 = g.m[0] - ps.c[0], d1 = g.m[1] - ps.c[1],
-          d2 = g.m[2] - ps.c[2];
+    const float4 r2 = make_float4(0.0f, 0.0f, 0.0f, p.mc[2]);
+    uint32_t count = 0;
+    Ellipse e;
+    if (make_ellipse(r0, r1, c.log2_alpha_min, e))
+      for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
+                        [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
+    rec0[vi] = r0;
+    rec1[vi] = r1;
+    rec2[vi] = r2;
+    ntiles[vi] = count;
+    if (count > 0) atomicOr(&vis_bits[(size_t)v * bit_words + (i >> 5)], 1u << (i & 31));
+  }
+}
+
+// Forward, pass 3 (after the tile lists are built, before the blend): one thread per visible
+// entry (grid-stride). The colour from the SH coefficients for the direction camera centre ->
+// Gaussian (Eq. app-sh), clamped at 0, into rec2.xyz. An entry with a non-finite coefficient
+// gets log2 opacity -inf, so that it covers no pixel in either blend, and is counted as culled.
+template <int DEG, bool kDevPose>
+__global__ void __launch_bounds__(kPreThreads) colour_kernel(
+    const __grid_constant__ Views views, int n, const float* __restrict__ means,
+    const float* __restrict__ sh, const uint32_t* __restrict__ order, float4* __restrict__ rec1,
+    float4* __restrict__ rec2, Counters* __restrict__ counters) {
+  chain_wait();
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const uint32_t n_visible = counters->n_visible_kept;
+  for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_visible;
+       k += gridDim.x * kPreThreads) {
+    const uint32_t vi = order[k];
+    const int v = (int)(vi / (uint32_t)n);
+    const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
+    float shc[3 * K];
+    load_sh<DEG>(sh, i, shc);
+    bool sh_finite = true;
+#pragma unroll
+    for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
+    float4 r2 = rec2[vi];
+    if (!sh_finite) {
+      atomicAdd(&counters->n_nonfinite, 1u);
+      reinterpret_cast<float*>(rec1 + vi)[3] = -INFINITY;
+      r2.x = r2.y = r2.z = 0.0f;
+      rec2[vi] = r2;
+      continue;
+    }
+    const PoseRef ps = view_pose<kDevPose>(views, v);
+    float d0 = __ldg(means + 3 * (size_t)i) - ps.c[0];
+    float d1 = __ldg(means + 3 * (size_t)i + 1) - ps.c[1];
+    float d2 = __ldg(means + 3 * (size_t)i + 2) - ps.c[2];
     const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     d0 *= rn;
     d1 *= rn;
@@ -447,17 +484,10 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
       for (int a = 0; a < K; ++a) acc += shc[3 * a + ch] * Y[a];
       rgb[ch] = fmaxf(acc, 0.0f);
     }
-    const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], p.mc[2]);
-    uint32_t count = 0;
-    Ellipse e;
-    if (make_ellipse(r0, r1, c.log2_alpha_min, e))
-      for_each_tile_row(e, views.tile_w, views.tile_h, vp.tiles_x, vp.tiles_y,
-                        [&](int, int tx0, int tx1) { count += (uint32_t)(tx1 - tx0 + 1); });
-    rec0[vi] = r0;
-    rec1[vi] = r1;
+    r2.x = rgb[0];
+    r2.y = rgb[1];
+    r2.z = rgb[2];
     rec2[vi] = r2;
-    ntiles[vi] = count;
-    if (count > 0) atomicOr(&vis_bits[(size_t)v * bit_words + (i >> 5)], 1u << (i & 31));
   }
 }
 
@@ -504,6 +534,12 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     q[2] = q4.z;
     q[3] = q4.w;
     load_sh<DEG>(sh, i, shc);
+    // An entry with a non-finite SH coefficient covered no pixel (colour_kernel): its record
+    // holds no moments and stays zero, and the view is left out of the Gaussian's mask.
+    bool sh_finite = true;
+#pragma unroll
+    for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
+    if (!sh_finite) continue;
     GaussianLocal g;
     gaussian_local(m, ls, q, __ldg(logits + i), g);
     const ViewParams& vp = views.v[v];
@@ -916,19 +952,32 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   // Pass 2: grid-stride over the candidates.
   const int64_t vn = (int64_t)views.n_views * g.n;
   const int blocks2 = (int)std::min<int64_t>((vn + kPreThreads - 1) / kPreThreads, 16 * 152);
-#define RGS_PROJECT(D)                                                                          \
-  e = launch_chained(views.pose_dev ? project_kernel<D, true> : project_kernel<D, false>,         \
-                     dim3(blocks2), dim3(kPreThreads), stream, views, c, g.n, g.means,            \
-                     g.log_scales, g.quats, g.opacity_logits, g.sh, (const uint32_t*)cand, rec0, \
-                     rec1, rec2, ntiles, vis_bits, bit_words, counters)
+  e = launch_chained(views.pose_dev ? project_kernel<true> : project_kernel<false>, dim3(blocks2),
+                     dim3(kPreThreads), stream, views, c, g.n, g.means, g.log_scales, g.quats,
+                     g.opacity_logits, (const uint32_t*)cand, rec0, rec1, rec2, ntiles, vis_bits,
+                     bit_words, counters);
+  RGS_LAUNCHED();
+  return e;
+}
+
+cudaError_t launch_colour(const Views& views, const rgs_gaussians& g, const uint32_t* order,
+                          int64_t vis_cap, float4* rec1, float4* rec2, Counters* counters,
+                          cudaStream_t stream) {
+  if (g.n == 0 || vis_cap == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((vis_cap + kPreThreads - 1) / kPreThreads, 8 * 152);
+  cudaError_t e = cudaSuccess;
+#define RGS_COLOUR(D)                                                                           \
+  e = launch_chained(views.pose_dev ? colour_kernel<D, true> : colour_kernel<D, false>,           \
+                     dim3(blocks), dim3(kPreThreads), stream, views, g.n, g.means, g.sh, order,   \
+                     rec1, rec2, counters)
   switch (g.sh_degree) {
-    case 0: RGS_PROJECT(0); break;
-    case 1: RGS_PROJECT(1); break;
-    case 2: RGS_PROJECT(2); break;
-    default: RGS_PROJECT(3); break;
+    case 0: RGS_COLOUR(0); break;
+    case 1: RGS_COLOUR(1); break;
+    case 2: RGS_COLOUR(2); break;
+    default: RGS_COLOUR(3); break;
   }
   RGS_LAUNCHED();
-#undef RGS_PROJECT
+#undef RGS_COLOUR
   return e;
 }
 

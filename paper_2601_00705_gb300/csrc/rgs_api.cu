@@ -28,6 +28,9 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       float4* rec2, uint32_t* ntiles, uint32_t* cand,
                                       uint32_t* vis_bits, Counters* counters,
                                       cudaStream_t stream);
+cudaError_t launch_colour(const Views& views, const rgs_gaussians& g, const uint32_t* order,
+                          int64_t vis_cap, float4* rec1, float4* rec2, Counters* counters,
+                          cudaStream_t stream);
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, unsigned long long* vis_mask,
@@ -467,6 +470,7 @@ void rgs_config_default(rgs_config* cfg) {
   cfg->tile_h = 16;
   cfg->pixels_per_thread = 4;
   cfg->backward_pixels_per_thread = 0;
+  cfg->sh_ready_event = nullptr;
 }
 
 rgs_status rgs_create(rgs_ctx** out, int device) {
@@ -580,6 +584,7 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
         trial.tile_h = sh.tile_h;
         trial.pixels_per_thread = ppt;
         trial.backward_pixels_per_thread = ppt;
+        trial.sh_ready_event = nullptr;  // the trials run on coefficients already on the device
         float t_f = 0.0f, t_b = 0.0f;
         for (int it = 0; it < 4 && result == RGS_OK; ++it) {
           cudaEventRecord(e0, stream);
@@ -839,6 +844,12 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   RGS_CUDA(launch_tile_ranges(sorted_keys, cnt, s->ranges, views.total_tiles,
                               (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), stream),
            "tile ranges");
+  // Colours of the visible entries: the first read of the SH coefficients, so the caller's
+  // upload of them may run until here.
+  if (cfg.sh_ready_event)
+    RGS_CUDA(cudaStreamWaitEvent(stream, static_cast<cudaEvent_t>(cfg.sh_ready_event), 0),
+             "wait for the SH coefficients");
+  RGS_CUDA(launch_colour(views, *g, s->order, vis_cap, s->rec1, s->rec2, cnt, stream), "colours");
   RGS_CUDA(mark(ctx, *s, 7, stream, capturing), "event");
   // 8. Blend.
   RGS_CUDA(launch_blend(true, views, consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,

@@ -44,12 +44,16 @@ class Renderer:
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def forward_raw(self, means, log_scales, quats, opacity_logits, sh, cameras, state: int = 0,
-                    out=None, world_to_cam: torch.Tensor | None = None):
+                    out=None, world_to_cam: torch.Tensor | None = None,
+                    sh_event: "torch.cuda.Event | None" = None):
         """Runs the forward; returns (color [P,3], depth [P], alpha [P], state handle).
 
         world_to_cam: optional device float32 tensor [V,12] (or [V,3,4]) of row-major [R|t]
         poses that replace the cameras' poses (read on the device, so a pose the device updates
-        needs no host round trip)."""
+        needs no host round trip).
+        sh_event: optional recorded CUDA event after which `sh` holds its values; the forward
+        waits for it only where it first reads the coefficients (after the sorts), so their
+        upload can overlap the projection and the sorts."""
         dev = self.device
         n = int(means.shape[0])
         K = int(sh.shape[1]) if sh.dim() == 3 else 0
@@ -72,14 +76,20 @@ class Renderer:
         g = binding.Gaussians(n, deg, means.data_ptr(), log_scales.data_ptr(), quats.data_ptr(),
                               opacity_logits.data_ptr(), sh.data_ptr())
         imgs = binding.Images(color.data_ptr(), depth.data_ptr(), alpha.data_ptr())
+        cfg = self.config
+        if sh_event is not None:
+            if not sh_event.cuda_event:
+                raise ValueError("sh_event must have been recorded")
+            cfg = binding.Config.from_buffer_copy(self.config)
+            cfg.sh_ready_event = sh_event.cuda_event
         if world_to_cam is None:
-            state = self.ctx.forward(g, cams, self.config, imgs, state, self.stream_handle())
+            state = self.ctx.forward(g, cams, cfg, imgs, state, self.stream_handle())
         else:
             if (world_to_cam.device != dev or world_to_cam.dtype != torch.float32
                     or not world_to_cam.is_contiguous() or world_to_cam.numel() != 12 * len(cams)):
                 raise ValueError("world_to_cam must be a contiguous float32 [V,12] tensor on the "
                                  "renderer's device")
-            state = self.ctx.forward_posed(g, cams, world_to_cam.data_ptr(), self.config, imgs,
+            state = self.ctx.forward_posed(g, cams, world_to_cam.data_ptr(), cfg, imgs,
                                            state, self.stream_handle())
         # Keep the (possibly copied) parameter tensors alive for the backward.
         self._last_inputs = (means, log_scales, quats, opacity_logits, sh)

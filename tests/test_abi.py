@@ -34,12 +34,13 @@ def test_library_builds_loads_and_exports_every_symbol():
 def test_ctypes_structs_match_c_layout(tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rgs.h"\n'
-                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
                    "sizeof(rgs_gaussians), sizeof(rgs_camera), sizeof(rgs_config),"
                    "sizeof(rgs_images), sizeof(rgs_image_grads), sizeof(rgs_stats),"
                    "offsetof(rgs_config, tile_w), sizeof(rgs_track_config),"
                    "sizeof(rgs_adam_config), offsetof(rgs_adam_config, iterations),"
-                   "sizeof(rgs_seed_config), sizeof(rgs_map_reg), sizeof(rgs_prune_config));"
+                   "sizeof(rgs_seed_config), sizeof(rgs_map_reg), sizeof(rgs_prune_config),"
+                   "offsetof(rgs_config, sh_ready_event));"
                    "return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -52,7 +53,7 @@ def test_ctypes_structs_match_c_layout(tmp_path):
                      binding.Config.tile_w.offset, ctypes.sizeof(binding.TrackConfig),
                      ctypes.sizeof(binding.AdamConfig), binding.AdamConfig.iterations.offset,
                      ctypes.sizeof(binding.SeedConfig), ctypes.sizeof(binding.MapReg),
-                     ctypes.sizeof(binding.PruneConfig)]
+                     ctypes.sizeof(binding.PruneConfig), binding.Config.sh_ready_event.offset]
 
 
 def test_create_without_gpu_fails_cleanly():

@@ -301,3 +301,45 @@ def test_invalid_arguments_and_handles_return_error_codes():
     assert st == binding.RGS_ERR_INVALID_ARG
     assert lib.rgs_release_state(ctx.handle, h) == binding.RGS_OK
     assert lib.rgs_release_state(ctx.handle, h) == binding.RGS_ERR_STATE
+
+
+def test_sh_event_defers_the_wait_for_the_coefficients():
+    # The coefficients reach the device only after a long wait on a side stream; the forward,
+    # given the event, must wait for them where it first reads them and render exactly what a
+    # forward on resident coefficients renders (a forward that read them early would see
+    # zeros). The backward then runs on the same stream.
+    wl = synthetic.tiny(seed=5)
+    g = wl.gaussians.as_dict()
+    rng = np.random.default_rng(5)
+    sh3 = np.concatenate([g["sh"], rng.normal(0, 0.1, size=(g["sh"].shape[0], 15, 3))],
+                         axis=1).astype(np.float32)
+    keys = ("means", "log_scales", "quats", "opacity_logits")
+    p = [to_dev(g[k]) for k in keys]
+    sh = to_dev(sh3)
+    n, K, V = int(p[0].shape[0]), 16, len(wl.cameras)
+    P = wl.n_pixels
+    up = to_dev(rng.normal(0, 1e-3, size=(P, 3)))
+    r = Renderer(0)
+    ref = r.forward_raw(*p, sh, wl.cameras)
+    ref_g = r.backward_raw(ref[3], n, K, V, up, None, None, binding.GRAD_ALL)
+    torch.cuda.synchronize()
+    r2 = Renderer(0)
+    late = torch.zeros_like(sh)
+    side = torch.cuda.Stream()
+    ev = torch.cuda.Event()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(100_000_000)  # ~50 ms of GPU cycles before the copy
+        late.copy_(sh)
+        ev.record(side)
+    got = r2.forward_raw(*p, late, wl.cameras, sh_event=ev)
+    got_g = r2.backward_raw(got[3], n, K, V, up, None, None, binding.GRAD_ALL)
+    torch.cuda.synchronize()
+    for a, b in zip(got[:3], ref[:3]):
+        assert torch.equal(a, b)
+    for k in ("means", "sh", "pose"):
+        np.testing.assert_allclose(got_g[k].cpu().numpy(), ref_g[k].cpu().numpy(), rtol=1e-5,
+                                   atol=1e-7 * float(ref_g[k].abs().max()))
+    assert r2.stats(got[3])["status"] == 0
+    r.release(ref[3])
+    r2.release(got[3])
