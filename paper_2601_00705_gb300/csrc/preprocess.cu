@@ -436,20 +436,59 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
   }
 }
 
-// Forward, pass 3 (after the tile lists are built, before the blend): one thread per visible
-// entry (grid-stride). The colour from the SH coefficients for the direction camera centre ->
-// Gaussian (Eq. app-sh), clamped at 0, into rec2.xyz. An entry with a non-finite coefficient
-// gets log2 opacity -inf, so that it covers no pixel in either blend, and is counted as culled.
+// Forward, pass 3 (after the tile lists are built, before the blend), one launch of two
+// independent parts.
+//  * Blocks [0, range_blocks): tile ranges. Thread t looks at the four sorted keys 4t .. 4t + 3
+//    (one 16-byte load; the key arrays are 256-byte aligned) and the key before them, and writes
+//    the run boundaries among them into `ranges` (zero on entry: tiles without pairs keep
+//    [0, 0)).
+//  * The other blocks: one thread per visible entry (grid-stride). The colour from the SH
+//    coefficients for the direction camera centre -> Gaussian (Eq. app-sh), clamped at 0, into
+//    rec2.xyz. An entry with a non-finite coefficient gets log2 opacity -inf, so that it covers
+//    no pixel in either blend, and is counted as culled.
+constexpr int kRangesColourThreads = 256;
+
 template <int DEG, bool kDevPose>
-__global__ void __launch_bounds__(kPreThreads) colour_kernel(
-    const __grid_constant__ Views views, int n, const float* __restrict__ means,
-    const float* __restrict__ sh, const uint32_t* __restrict__ order, float4* __restrict__ rec1,
-    float4* __restrict__ rec2, Counters* __restrict__ counters) {
+__global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
+    const uint32_t* __restrict__ keys, uint32_t total_tiles, uint2* __restrict__ ranges,
+    uint32_t range_blocks, const __grid_constant__ Views views, int n,
+    const float* __restrict__ means, const float* __restrict__ sh,
+    const uint32_t* __restrict__ order, float4* __restrict__ rec1, float4* __restrict__ rec2,
+    Counters* __restrict__ counters) {
   chain_wait();
+  if (blockIdx.x < range_blocks) {
+    const uint32_t np = counters->n_pairs_stored;
+    const uint32_t p0 = 4u * (blockIdx.x * kRangesColourThreads + threadIdx.x);
+    if (p0 >= np) return;
+    uint32_t k[5];  // k[0] = key before p0 (or none), k[1..4] = keys p0 .. p0 + 3
+    k[0] = p0 > 0 ? keys[p0 - 1] : 0xffffffffu;
+    if (p0 + 4 <= np) {
+      const uint4 q = *reinterpret_cast<const uint4*>(keys + p0);
+      k[1] = q.x;
+      k[2] = q.y;
+      k[3] = q.z;
+      k[4] = q.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j + 1] = p0 + j < np ? keys[p0 + j] : 0xffffffffu;
+    }
+    const uint32_t next = p0 + 4 < np ? keys[p0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t p = p0 + j;
+      const uint32_t key = k[j + 1];
+      if (p >= np || key >= total_tiles) continue;
+      const uint32_t after = j < 3 ? k[j + 2] : next;
+      if (p == 0 || k[j] != key) ranges[key].x = p;
+      if (p == np - 1 || after != key) ranges[key].y = p + 1;
+    }
+    return;
+  }
   constexpr int K = (DEG + 1) * (DEG + 1);
   const uint32_t n_visible = counters->n_visible_kept;
-  for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_visible;
-       k += gridDim.x * kPreThreads) {
+  const uint32_t stride = (gridDim.x - range_blocks) * kRangesColourThreads;
+  for (uint32_t k = (blockIdx.x - range_blocks) * kRangesColourThreads + threadIdx.x;
+       k < n_visible; k += stride) {
     const uint32_t vi = order[k];
     const int v = (int)(vi / (uint32_t)n);
     const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
@@ -960,24 +999,33 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   return e;
 }
 
-cudaError_t launch_colour(const Views& views, const rgs_gaussians& g, const uint32_t* order,
-                          int64_t vis_cap, float4* rec1, float4* rec2, Counters* counters,
-                          cudaStream_t stream) {
-  if (g.n == 0 || vis_cap == 0) return cudaSuccess;
-  const int blocks = (int)std::min<int64_t>((vis_cap + kPreThreads - 1) / kPreThreads, 8 * 152);
+cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* ranges,
+                                 uint32_t pair_capacity, const Views& views,
+                                 const rgs_gaussians& g, const uint32_t* order, int64_t vis_cap,
+                                 float4* rec1, float4* rec2, Counters* counters,
+                                 cudaStream_t stream) {
+  const uint32_t range_blocks =
+      (uint32_t)(((int64_t)pair_capacity + 4 * kRangesColourThreads - 1) /
+                 (4 * kRangesColourThreads));
+  const int64_t colour_items = g.n > 0 ? vis_cap : 0;
+  const uint32_t colour_blocks = (uint32_t)std::min<int64_t>(
+      (colour_items + kRangesColourThreads - 1) / kRangesColourThreads, 4 * 152);
+  if (range_blocks + colour_blocks == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-#define RGS_COLOUR(D)                                                                           \
-  e = launch_chained(views.pose_dev ? colour_kernel<D, true> : colour_kernel<D, false>,           \
-                     dim3(blocks), dim3(kPreThreads), stream, views, g.n, g.means, g.sh, order,   \
-                     rec1, rec2, counters)
+#define RGS_RANGES_COLOUR(D)                                                                   \
+  e = launch_chained(views.pose_dev ? ranges_colour_kernel<D, true>                             \
+                                    : ranges_colour_kernel<D, false>,                           \
+                     dim3(range_blocks + colour_blocks), dim3(kRangesColourThreads), stream,    \
+                     keys, (uint32_t)total_tiles, ranges, range_blocks, views, g.n, g.means,    \
+                     g.sh, order, rec1, rec2, counters)
   switch (g.sh_degree) {
-    case 0: RGS_COLOUR(0); break;
-    case 1: RGS_COLOUR(1); break;
-    case 2: RGS_COLOUR(2); break;
-    default: RGS_COLOUR(3); break;
+    case 0: RGS_RANGES_COLOUR(0); break;
+    case 1: RGS_RANGES_COLOUR(1); break;
+    case 2: RGS_RANGES_COLOUR(2); break;
+    default: RGS_RANGES_COLOUR(3); break;
   }
   RGS_LAUNCHED();
-#undef RGS_COLOUR
+#undef RGS_RANGES_COLOUR
   return e;
 }
 

@@ -191,39 +191,6 @@ __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
   counters->n_visible_kept = 0;
 }
 
-// Thread t looks at the four sorted keys 4t .. 4t + 3 (one 16-byte load; the key arrays are
-// 256-byte aligned) and the key before them, and writes the run boundaries among them.
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys,
-                                   const Counters* __restrict__ counters, uint32_t total_tiles,
-                                   uint2* __restrict__ ranges) {
-  chain_wait();
-  const uint32_t n = counters->n_pairs_stored;
-  const uint32_t p0 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (p0 >= n) return;
-  uint32_t k[5];  // k[0] = key before p0 (or none), k[1..4] = keys p0 .. p0 + 3
-  k[0] = p0 > 0 ? keys[p0 - 1] : 0xffffffffu;
-  if (p0 + 4 <= n) {
-    const uint4 q = *reinterpret_cast<const uint4*>(keys + p0);
-    k[1] = q.x;
-    k[2] = q.y;
-    k[3] = q.z;
-    k[4] = q.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) k[j + 1] = p0 + j < n ? keys[p0 + j] : 0xffffffffu;
-  }
-  const uint32_t next = p0 + 4 < n ? keys[p0 + 4] : 0xffffffffu;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t p = p0 + j;
-    const uint32_t key = k[j + 1];
-    if (p >= n || key >= total_tiles) continue;
-    const uint32_t after = j < 3 ? k[j + 2] : next;
-    if (p == 0 || k[j] != key) ranges[key].x = p;
-    if (p == n - 1 || after != key) ranges[key].y = p + 1;
-  }
-}
-
 // ------------------------------------------------------------------------------------------
 // Staging of a batch of Gaussians in shared memory. For an even number of pixels per thread every
 // per-Gaussian operand is stored twice, as (x, x) pairs, so the packed f32x2 arithmetic of two
@@ -790,19 +757,6 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
   const cudaError_t e = launch_chained(store_pair_count_kernel, dim3(1), dim3(1), stream, counters,
                                        capacity);
   RGS_LAUNCHED();
-  return e;
-}
-
-// `ranges` must hold zeros on entry (tiles without pairs keep [0, 0)).
-cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
-                               int total_tiles, uint32_t capacity, cudaStream_t stream) {
-  cudaError_t e = cudaSuccess;
-  if (capacity > 0) {
-    const uint32_t threads = (capacity + 3) / 4;
-    e = launch_chained(tile_ranges_kernel, dim3((threads + 255) / 256), dim3(256), stream, keys,
-                       counters, (uint32_t)total_tiles, ranges);
-    RGS_LAUNCHED();
-  }
   return e;
 }
 

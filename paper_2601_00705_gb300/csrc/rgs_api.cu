@@ -28,9 +28,11 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       float4* rec2, uint32_t* ntiles, uint32_t* cand,
                                       uint32_t* vis_bits, Counters* counters,
                                       cudaStream_t stream);
-cudaError_t launch_colour(const Views& views, const rgs_gaussians& g, const uint32_t* order,
-                          int64_t vis_cap, float4* rec1, float4* rec2, Counters* counters,
-                          cudaStream_t stream);
+cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* ranges,
+                                 uint32_t pair_capacity, const Views& views,
+                                 const rgs_gaussians& g, const uint32_t* order, int64_t vis_cap,
+                                 float4* rec1, float4* rec2, Counters* counters,
+                                 cudaStream_t stream);
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, unsigned long long* vis_mask,
@@ -45,8 +47,6 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
                              int64_t visible_cap, uint32_t capacity,
                              uint32_t* keys, uint32_t* vals, Counters* counters,
                              cudaStream_t stream);
-cudaError_t launch_tile_ranges(const uint32_t* keys, const Counters* counters, uint2* ranges,
-                               int total_tiles, uint32_t capacity, cudaStream_t stream);
 cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, const uint2* ranges,
                          const uint32_t* pair_vals, const float4* rec0, const float4* rec1,
                          const float4* rec2, float* color, float* depth, float* alpha,
@@ -841,15 +841,15 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   s->sorted_vals = s->pair_vals[alt ? 1 : 0];
   RGS_CUDA(mark(ctx, *s, 6, stream, capturing), "event");
   // 7. Tile ranges.
-  RGS_CUDA(launch_tile_ranges(sorted_keys, cnt, s->ranges, views.total_tiles,
-                              (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), stream),
-           "tile ranges");
-  // Colours of the visible entries: the first read of the SH coefficients, so the caller's
-  // upload of them may run until here.
+  // Tile ranges and the colours of the visible entries, in one launch: the colours are the
+  // first read of the SH coefficients, so the caller's upload of them may run until here.
   if (cfg.sh_ready_event)
     RGS_CUDA(cudaStreamWaitEvent(stream, static_cast<cudaEvent_t>(cfg.sh_ready_event), 0),
              "wait for the SH coefficients");
-  RGS_CUDA(launch_colour(views, *g, s->order, vis_cap, s->rec1, s->rec2, cnt, stream), "colours");
+  RGS_CUDA(launch_ranges_colour(sorted_keys, views.total_tiles, s->ranges,
+                                (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), views, *g,
+                                s->order, vis_cap, s->rec1, s->rec2, cnt, stream),
+           "tile ranges and colours");
   RGS_CUDA(mark(ctx, *s, 7, stream, capturing), "event");
   // 8. Blend.
   RGS_CUDA(launch_blend(true, views, consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
