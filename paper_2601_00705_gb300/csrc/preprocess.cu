@@ -532,9 +532,11 @@ __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
 
 // ------------------------------------------------------------------------------------------
 // Backward, phase 1: one thread per visible (view, Gaussian) entry (grid-stride over the
-// compacted list). Chains the entry's screen-space gradients through Eq. proj and the colour
-// model to the view-dependent quantities that phase 2 needs, and reduces the view's twist
-// gradient over the block. The entry's gradient record is overwritten with
+// compacted list in (view, Gaussian) order: neighbouring threads read neighbouring Gaussians
+// and mostly share a view, whose twist a full warp then sums by shuffles). Chains the entry's screen-space gradients through
+// Eq. proj and the colour model to the view-dependent quantities that phase 2 needs, and
+// reduces the view's twist gradient over the block. The entry's gradient record is overwritten
+// with
 //   [0..2] dL/dmu^W (projection and viewing-direction paths), [3..8] dL/dSigma^W (xx, xy, xz,
 //   yy, yz, zz; off-diagonal entries hold the sum of both symmetric partners), [9..11] dL/d(raw
 //   colour) after the clamp, [12] dL/do.
@@ -701,8 +703,22 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
       pose[3] = p.mc[1] * gmc[2] - p.mc[2] * gmc[1] + p.J02 * GJ[1] + p.J12 * GJ[4] - p.J11 * GJ[5];
       pose[4] = p.mc[2] * gmc[0] - p.mc[0] * gmc[2] + p.J00 * GJ[2] - p.J02 * GJ[0] - p.J12 * GJ[3];
       pose[5] = p.mc[0] * gmc[1] - p.mc[1] * gmc[0] + p.J11 * GJ[3] - p.J00 * GJ[1];
+      // A full warp on one view sums its twists by shuffles and adds them once; otherwise each
+      // lane adds its own (a shared-memory atomic per lane and component).
+      const unsigned active = __activemask();
+      const unsigned same = __match_any_sync(active, v);
+      if (active == 0xffffffffu && same == 0xffffffffu) {
 #pragma unroll
-      for (int a2 = 0; a2 < 6; ++a2) atomicAdd(&s_pose[v * 6 + a2], pose[a2]);
+        for (int a2 = 0; a2 < 6; ++a2)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) pose[a2] += __shfl_xor_sync(0xffffffffu, pose[a2], o);
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+          for (int a2 = 0; a2 < 6; ++a2) atomicAdd(&s_pose[v * 6 + a2], pose[a2]);
+      } else {
+#pragma unroll
+        for (int a2 = 0; a2 < 6; ++a2) atomicAdd(&s_pose[v * 6 + a2], pose[a2]);
+      }
     }
   }
   if (grad_mask & RGS_GRAD_POSE) {
@@ -749,9 +765,21 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
   }
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   if (i >= n) return;
-  float m[3];
+  // Every parameter read is issued here, together, ahead of the records' loads.
+  float m[3], ls[3], q[4];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) m[a] = __ldg(means + 3 * (size_t)i + a);
+  for (int a = 0; a < 3; ++a) {
+    m[a] = __ldg(means + 3 * (size_t)i + a);
+    ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
+  }
+  {
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
+    q[0] = q4.x;
+    q[1] = q4.y;
+    q[2] = q4.z;
+    q[3] = q4.w;
+  }
+  const float logit = __ldg(logits + i);
   float gm[3] = {0, 0, 0}, gSw[6] = {0, 0, 0, 0, 0, 0}, gop = 0.0f;
   float gsh[3 * K];
 #pragma unroll
@@ -828,16 +856,8 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
   // A Gaussian culled in every view gets zero gradients; its local quantities may be
   // non-finite and must not enter the chain below.
   if (any_visible) {
-    float ls[3], q[4];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
-    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + i);
-    q[0] = q4.x;
-    q[1] = q4.y;
-    q[2] = q4.z;
-    q[3] = q4.w;
     GaussianLocal g;
-    gaussian_local(m, ls, q, __ldg(logits + i), g);
+    gaussian_local(m, ls, q, logit, g);
     glogit = gop * g.opacity * (1.0f - g.opacity);
     if (grad_mask & (RGS_GRAD_SCALES | RGS_GRAD_QUATS)) {
       // Sigma^W = M M^T, M = Rq diag(s): G_M = 2 G_Sym M with G_Sym the symmetric matrix whose
@@ -885,10 +905,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     //     for the logit l (d psi / d l = 2 alpha - 1),
     //   lambda_mu |mu - mu_bar|^2 (d / d mu = 2 lambda_mu (mu - mu_bar)).
     // Non-finite parameters contribute nothing. The counters add the views that see it.
-    float ls[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ls[a] = __ldg(log_scales + 3 * (size_t)i + a);
-    const float l = __ldg(logits + i);
+    const float l = logit;
     float val = 0.0f;
     const bool finite = isfinite(ls[0]) && isfinite(ls[1]) && isfinite(ls[2]) && isfinite(l) &&
                         isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]);

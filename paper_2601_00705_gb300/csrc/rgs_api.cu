@@ -91,6 +91,10 @@ struct State {
   uint32_t* ntiles = nullptr;
   uint32_t *vis_keys[2] = {nullptr, nullptr}, *vis_vals[2] = {nullptr, nullptr};
   uint32_t* offsets = nullptr;
+  // The visible entries in (view, Gaussian) order (the compaction's output, kept past the depth
+  // sort): the backward's per-entry pass walks it, so that neighbouring threads read
+  // neighbouring Gaussians and mostly share a view.
+  uint32_t* vis_list = nullptr;
   float* g2d = nullptr;
   // Visibility bits of the last forward: row v (ceil(n / 32) words) has bit i set iff entry
   // (v, i) touches a tile.
@@ -246,7 +250,7 @@ rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t n, int64_t pose
     if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "per-Gaussian buffers grow during capture");
     RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
     const int64_t cap = vn;
-    size_t bytes = 3 * align_up(sizeof(float4) * cap) + 6 * align_up(sizeof(uint32_t) * cap) +
+    size_t bytes = 3 * align_up(sizeof(float4) * cap) + 7 * align_up(sizeof(uint32_t) * cap) +
                    align_up(sizeof(float) * kG2Stride * cap) +
                    align_up(sizeof(uint32_t) * vis_bit_words_cap(cap));
     RGS_CUDA(alloc_region(s.r_vn, bytes), "allocate per-Gaussian buffers");
@@ -260,6 +264,7 @@ rgs_status ensure_vn(rgs_ctx* ctx, State& s, int64_t vn, int64_t n, int64_t pose
     s.vis_vals[0] = carve<uint32_t>(p, cap);
     s.vis_vals[1] = carve<uint32_t>(p, cap);
     s.offsets = carve<uint32_t>(p, cap);
+    s.vis_list = carve<uint32_t>(p, cap);
     s.g2d = carve<float>(p, kG2Stride * cap);
     s.vis_bits = carve<uint32_t>(p, vis_bit_words_cap(cap));
     // The screen-space gradient accumulators start at zero; every backward leaves them zero.
@@ -774,7 +779,7 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   RGS_CUDA(mark(ctx, *s, 1, stream, capturing), "event");
   // 2. Visible entries with depth keys, in (view, Gaussian) order.
   RGS_CUDA(launch_compact_visible(s->vis_bits, n_views, g->n, s->rec2, s->vis_keys[0],
-                                  s->vis_vals[0], &cnt->n_visible,
+                                  s->vis_vals[0], s->vis_list, &cnt->n_visible,
                                   lookback_at(lb_area, &cnt->status, s->vn_cap), stream),
            "compact");
   RGS_CUDA(mark(ctx, *s, 2, stream, capturing), "event");
@@ -952,7 +957,7 @@ rgs_status render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads*
                         s->g2d, s->counters, stream),
            "blend backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 1, stream, capturing), "event");
-  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->vis_mask, s->order,
+  RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->vis_mask, s->vis_list,
                                       s->counters, s->vn, s->g2d, grad_mask, d_means,
                                       d_log_scales, d_quats, d_opacity_logits, d_sh,
                                       s->pose_partial, d_pose, reg ? &mreg : nullptr, stream),

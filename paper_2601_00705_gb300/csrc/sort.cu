@@ -441,7 +441,7 @@ constexpr int kBitsThreads = 256;
 __global__ void __launch_bounds__(kBitsThreads) compact_bits_kernel(
     const uint32_t* __restrict__ vis_bits, uint32_t n_words, uint32_t words_per_view, uint32_t n,
     const float4* __restrict__ rec2, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-    uint32_t* __restrict__ n_out, Lookback lb, uint32_t n_tiles) {
+    uint32_t* __restrict__ list, uint32_t* __restrict__ n_out, Lookback lb, uint32_t n_tiles) {
   chain_wait();
   __shared__ uint32_t s_list[kBitsThreads * 32];
   __shared__ uint32_t s_prefix;
@@ -472,6 +472,7 @@ __global__ void __launch_bounds__(kBitsThreads) compact_bits_kernel(
     const uint32_t vi = s_list[t];
     keys[prefix + t] = __float_as_uint(rec2[vi].w);
     vals[prefix + t] = vi;
+    list[prefix + t] = vi;
   }
   if (b == n_tiles - 1 && threadIdx.x == 0) *n_out = prefix + agg;
 }
@@ -818,15 +819,16 @@ cudaError_t launch_exclusive_scan_single_pass(const uint32_t* in, uint32_t* out,
 
 cudaError_t launch_compact_visible(const uint32_t* vis_bits, int n_views, int n,
                                    const float4* rec2, uint32_t* keys, uint32_t* vals,
-                                   uint32_t* n_out, Lookback lb, cudaStream_t stream) {
+                                   uint32_t* list, uint32_t* n_out, Lookback lb,
+                                   cudaStream_t stream) {
   const int64_t words = (int64_t)n_views * vis_bit_words_per_view(n);
   if (words == 0) return cudaMemsetAsync(n_out, 0, sizeof(uint32_t), stream);
   const int64_t tiles = (words + kBitsThreads - 1) / kBitsThreads;
   if (tiles > lb.capacity) return cudaErrorInvalidValue;
   const cudaError_t e = launch_chained(
       compact_bits_kernel, dim3((unsigned)tiles), dim3(kBitsThreads), stream, vis_bits,
-      (uint32_t)words, (uint32_t)vis_bit_words_per_view(n), (uint32_t)n, rec2, keys, vals, n_out,
-      lb, (uint32_t)tiles);
+      (uint32_t)words, (uint32_t)vis_bit_words_per_view(n), (uint32_t)n, rec2, keys, vals, list,
+      n_out, lb, (uint32_t)tiles);
   RGS_LAUNCHED();
   return e;
 }
