@@ -442,7 +442,10 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
 //    (one 16-byte load; the key arrays are 256-byte aligned) and the key before them, and writes
 //    the run boundaries among them into `ranges` (zero on entry: tiles without pairs keep
 //    [0, 0)).
-//  * The other blocks: one thread per visible entry (grid-stride). The colour from the SH
+//  * The other blocks: one thread per visible entry, in (view, Gaussian) order (grid-stride
+//    over `order`, the compacted list: neighbouring threads read neighbouring Gaussians' SH
+//    rows; in depth order the reads are scattered, which costs ~0.5 ms on 3M Gaussians whose
+//    coefficients do not fit in L2). The colour from the SH
 //    coefficients for the direction camera centre -> Gaussian (Eq. app-sh), clamped at 0, into
 //    rec2.xyz. An entry with a non-finite coefficient gets log2 opacity -inf, so that it covers
 //    no pixel in either blend, and is counted as culled.

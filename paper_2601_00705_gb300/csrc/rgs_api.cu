@@ -92,8 +92,8 @@ struct State {
   uint32_t *vis_keys[2] = {nullptr, nullptr}, *vis_vals[2] = {nullptr, nullptr};
   uint32_t* offsets = nullptr;
   // The visible entries in (view, Gaussian) order (the compaction's output, kept past the depth
-  // sort): the backward's per-entry pass walks it, so that neighbouring threads read
-  // neighbouring Gaussians and mostly share a view.
+  // sort): the colour pass and the backward's per-entry pass walk it, so that neighbouring
+  // threads read neighbouring Gaussians and mostly share a view.
   uint32_t* vis_list = nullptr;
   float* g2d = nullptr;
   // Visibility bits of the last forward: row v (ceil(n / 32) words) has bit i set iff entry
@@ -853,7 +853,7 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
              "wait for the SH coefficients");
   RGS_CUDA(launch_ranges_colour(sorted_keys, views.total_tiles, s->ranges,
                                 (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), views, *g,
-                                s->order, vis_cap, s->rec1, s->rec2, cnt, stream),
+                                s->vis_list, vis_cap, s->rec1, s->rec2, cnt, stream),
            "tile ranges and colours");
   RGS_CUDA(mark(ctx, *s, 7, stream, capturing), "event");
   // 8. Blend.

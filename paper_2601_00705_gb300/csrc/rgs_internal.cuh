@@ -480,8 +480,8 @@ cudaError_t launch_exclusive_scan_single_pass(const uint32_t* in, uint32_t* out,
 // Compaction of the visible entries, in (view, Gaussian) order: for every set bit i of row v of
 // the visibility bitmask (n_views rows for n Gaussians), writes keys[pos] = float bits of
 // rec2[v n + i].w (depth) and vals[pos] = list[pos] = v n + i (vals feeds the depth sort, list
-// keeps the order for the backward's per-entry pass); the count into *n_out. One single-pass
-// launch; lb must be zeroed.
+// keeps the order for the colour pass and the backward's per-entry pass); the count into *n_out.
+// One single-pass launch; lb must be zeroed.
 cudaError_t launch_compact_visible(const uint32_t* vis_bits, int n_views, int n,
                                    const float4* rec2, uint32_t* keys, uint32_t* vals,
                                    uint32_t* list, uint32_t* n_out, Lookback lb,
