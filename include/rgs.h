@@ -101,13 +101,17 @@ typedef struct {
                                          pixels_per_thread. The two blends share only the tile
                                          shape: the per-pixel state between them is stored in
                                          image order */
-  void* sh_ready_event; /* optional cudaEvent_t, or NULL. The forward reads the SH coefficients
-                           only after the tile lists are built (the colours of the visible
-                           entries are evaluated just before the forward blend); with an event
-                           given, it waits for the event on its stream right there, so that the
-                           caller's upload of the coefficients can overlap the projection and the
-                           sorts. The event must have been recorded (on any stream) before the
-                           call; under stream capture the wait becomes a graph dependency. */
+  void* sh_ready_event; /* optional cudaEvent_t, or NULL. NULL: the projection evaluates the
+                           colours (Eq. app-sh) and culls entries with a non-finite coefficient.
+                           An event: the forward reads the SH coefficients only after the tile
+                           lists are built (the colours of the visible entries are evaluated just
+                           before the forward blend) and waits for the event on its stream right
+                           there, so that the caller's upload of the coefficients can overlap the
+                           projection and the sorts; an entry with a non-finite coefficient then
+                           stays in the lists but covers no pixel. Images and gradients are the
+                           same either way. The event must have been recorded (on any stream)
+                           before the call; under stream capture the wait becomes a graph
+                           dependency. */
 } rgs_config;
 
 /* Forward outputs (device, caller-owned, P = sum_v W_v H_v): color [P,3], depth [P], alpha [P]. */
@@ -141,9 +145,9 @@ typedef struct {
                               kept, when status bit 2 is set) */
   int64_t n_eval;          /* (pixel, Gaussian) list positions visited by the forward blend */
   int64_t n_contrib;       /* of those, the ones composited (covering, before the stop) */
-  int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs (non-finite SH
-                              coefficients are found, and counted, for the entries that reach
-                              the tile lists; such an entry covers no pixel) */
+  int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs (with an SH event,
+                              non-finite SH coefficients are found, and counted, for the entries
+                              that reach the tile lists) */
   int64_t pair_capacity;   /* allocated pair-list capacity */
   int64_t state_bytes;     /* device bytes held by the state */
   uint32_t status;         /* device status bits: 1 = pair list overflowed its capacity;
@@ -309,8 +313,8 @@ rgs_status rgs_pose_adam_step(rgs_ctx* ctx, int32_t n_views, const rgs_adam_conf
 #define RGS_PHASE_OFFSETS 3        /* pair offsets (scan of tile counts in depth order) */
 #define RGS_PHASE_DUPLICATE 4      /* (tile, Gaussian) pair emission */
 #define RGS_PHASE_TILE_SORT 5      /* radix sort of the pairs by tile */
-#define RGS_PHASE_RANGES 6         /* per-tile [first, last + 1), then the colours of the visible
-                                      entries (the first read of the SH coefficients) */
+#define RGS_PHASE_RANGES 6         /* per-tile [first, last + 1) (with an SH event, also the
+                                      colours of the visible entries) */
 #define RGS_PHASE_BLEND_FORWARD 7  /* front-to-back compositing (Eq. alpha) */
 #define RGS_PHASE_BLEND_BACKWARD 8 /* back-to-front screen-space gradients */
 #define RGS_PHASE_PREPROCESS_BACKWARD 9 /* parameter and twist gradients (Eq. muCjac..sigmaIjac) */

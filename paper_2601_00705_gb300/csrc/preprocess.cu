@@ -382,19 +382,44 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
   for (uint32_t t = threadIdx.x; t < s_count; t += kPreThreads) cand[s_base + t] = s_cand[t];
 }
 
+// Colour of a Gaussian from its SH coefficients (Eq. app-sh) for the direction camera centre ->
+// mean, clamped at 0. Both passes that evaluate it call this, so their results are the same bits.
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const float* shc, const float* m, const PoseRef& ps,
+                                          float* rgb) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  float d0 = m[0] - ps.c[0], d1 = m[1] - ps.c[1], d2 = m[2] - ps.c[2];
+  const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  d0 *= rn;
+  d1 *= rn;
+  d2 *= rn;
+  float Y[16];
+  sh_basis<DEG>(d0, d1, d2, Y);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float acc = 0.5f;
+#pragma unroll
+    for (int a = 0; a < K; ++a) acc += shc[3 * a + ch] * Y[a];
+    rgb[ch] = fmaxf(acc, 0.0f);
+  }
+}
+
 // Forward, pass 2 (project): one thread per candidate entry (grid-stride). Full projection
-// (Eq. proj) and tile count; writes the entry's records (depth in rec2.w; the colour follows in
-// colour_kernel, for the visible entries only) and tile count. Entries that are not candidates
-// keep ntiles = 0 and unwritten records.
-template <bool kDevPose>
+// (Eq. proj), tile count and, for DEG >= 0, the colour; writes the entry's records and tile count.
+// An entry with a non-finite SH coefficient is culled here and counted. With DEG = -1 (the
+// caller's SH coefficients may still be in flight) the colour is left to the pass after the
+// sorts (rec2.xyz = 0 until then). Entries that are not candidates keep ntiles = 0 and unwritten
+// records.
+template <int DEG, bool kDevPose>
 __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ logits, const uint32_t* __restrict__ cand,
-    float4* __restrict__ rec0, float4* __restrict__ rec1, float4* __restrict__ rec2,
-    uint32_t* __restrict__ ntiles, uint32_t* __restrict__ vis_bits, int bit_words,
-    Counters* __restrict__ counters) {
+    const float* __restrict__ logits, const float* __restrict__ sh,
+    const uint32_t* __restrict__ cand, float4* __restrict__ rec0, float4* __restrict__ rec1,
+    float4* __restrict__ rec2, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ vis_bits,
+    int bit_words, Counters* __restrict__ counters) {
   chain_wait();
+  constexpr int K = DEG >= 0 ? (DEG + 1) * (DEG + 1) : 1;
   const uint32_t n_cand = counters->n_candidates;
   for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_cand;
        k += gridDim.x * kPreThreads) {
@@ -412,6 +437,17 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     q[1] = q4.y;
     q[2] = q4.z;
     q[3] = q4.w;
+    float shc[3 * K];
+    if constexpr (DEG >= 0) {
+      load_sh<DEG>(sh, i, shc);
+      bool sh_finite = true;
+#pragma unroll
+      for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
+      if (!sh_finite) {
+        atomicAdd(&counters->n_nonfinite, 1u);
+        continue;
+      }
+    }
     GaussianLocal g;
     gaussian_local(m, ls, q, __ldg(logits + i), g);
     const ViewParams& vp = views.v[v];
@@ -422,7 +458,9 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     const float4 r1 =
         make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
                     __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
-    const float4 r2 = make_float4(0.0f, 0.0f, 0.0f, p.mc[2]);
+    float rgb[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (DEG >= 0) sh_colour<DEG>(shc, g.m, ps, rgb);
+    const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], p.mc[2]);
     uint32_t count = 0;
     Ellipse e;
     if (make_ellipse(r0, r1, c.log2_alpha_min, e))
@@ -509,23 +547,10 @@ __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
       continue;
     }
     const PoseRef ps = view_pose<kDevPose>(views, v);
-    float d0 = __ldg(means + 3 * (size_t)i) - ps.c[0];
-    float d1 = __ldg(means + 3 * (size_t)i + 1) - ps.c[1];
-    float d2 = __ldg(means + 3 * (size_t)i + 2) - ps.c[2];
-    const float rn = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    d0 *= rn;
-    d1 *= rn;
-    d2 *= rn;
-    float Y[16];
-    sh_basis<DEG>(d0, d1, d2, Y);
+    const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1),
+                        __ldg(means + 3 * (size_t)i + 2)};
     float rgb[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float acc = 0.5f;
-#pragma unroll
-      for (int a = 0; a < K; ++a) acc += shc[3 * a + ch] * Y[a];
-      rgb[ch] = fmaxf(acc, 0.0f);
-    }
+    sh_colour<DEG>(shc, m, ps, rgb);
     r2.x = rgb[0];
     r2.y = rgb[1];
     r2.z = rgb[2];
@@ -991,7 +1016,7 @@ __global__ void __launch_bounds__(256) reg_sum_kernel(int n, const float* __rest
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
                                       float4* rec2, uint32_t* ntiles, uint32_t* cand,
-                                      uint32_t* vis_bits, Counters* counters,
+                                      uint32_t* vis_bits, bool defer_colour, Counters* counters,
                                       cudaStream_t stream) {
   if (g.n == 0) return cudaSuccess;
   const int bit_words = (int)vis_bit_words_per_view(g.n);
@@ -1011,23 +1036,35 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
   // Pass 2: grid-stride over the candidates.
   const int64_t vn = (int64_t)views.n_views * g.n;
   const int blocks2 = (int)std::min<int64_t>((vn + kPreThreads - 1) / kPreThreads, 16 * 152);
-  e = launch_chained(views.pose_dev ? project_kernel<true> : project_kernel<false>, dim3(blocks2),
-                     dim3(kPreThreads), stream, views, c, g.n, g.means, g.log_scales, g.quats,
-                     g.opacity_logits, (const uint32_t*)cand, rec0, rec1, rec2, ntiles, vis_bits,
-                     bit_words, counters);
+#define RGS_PROJECT(D)                                                                          \
+  e = launch_chained(views.pose_dev ? project_kernel<D, true> : project_kernel<D, false>,         \
+                     dim3(blocks2), dim3(kPreThreads), stream, views, c, g.n, g.means,            \
+                     g.log_scales, g.quats, g.opacity_logits, g.sh, (const uint32_t*)cand, rec0, \
+                     rec1, rec2, ntiles, vis_bits, bit_words, counters)
+  if (defer_colour) {
+    RGS_PROJECT(-1);
+  } else {
+    switch (g.sh_degree) {
+      case 0: RGS_PROJECT(0); break;
+      case 1: RGS_PROJECT(1); break;
+      case 2: RGS_PROJECT(2); break;
+      default: RGS_PROJECT(3); break;
+    }
+  }
   RGS_LAUNCHED();
+#undef RGS_PROJECT
   return e;
 }
 
 cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* ranges,
                                  uint32_t pair_capacity, const Views& views,
                                  const rgs_gaussians& g, const uint32_t* order, int64_t vis_cap,
-                                 float4* rec1, float4* rec2, Counters* counters,
+                                 bool colour, float4* rec1, float4* rec2, Counters* counters,
                                  cudaStream_t stream) {
   const uint32_t range_blocks =
       (uint32_t)(((int64_t)pair_capacity + 4 * kRangesColourThreads - 1) /
                  (4 * kRangesColourThreads));
-  const int64_t colour_items = g.n > 0 ? vis_cap : 0;
+  const int64_t colour_items = colour && g.n > 0 ? vis_cap : 0;
   const uint32_t colour_blocks = (uint32_t)std::min<int64_t>(
       (colour_items + kRangesColourThreads - 1) / kRangesColourThreads, 4 * 152);
   if (range_blocks + colour_blocks == 0) return cudaSuccess;

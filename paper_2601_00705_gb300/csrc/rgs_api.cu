@@ -26,12 +26,12 @@ namespace rgs {
 cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
                                       const rgs_gaussians& g, float4* rec0, float4* rec1,
                                       float4* rec2, uint32_t* ntiles, uint32_t* cand,
-                                      uint32_t* vis_bits, Counters* counters,
+                                      uint32_t* vis_bits, bool defer_colour, Counters* counters,
                                       cudaStream_t stream);
 cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* ranges,
                                  uint32_t pair_capacity, const Views& views,
-                                 const rgs_gaussians& g, const uint32_t* order, int64_t vis_cap,
-                                 float4* rec1, float4* rec2, Counters* counters,
+                                 const rgs_gaussians& g, const uint32_t* list, int64_t vis_cap,
+                                 bool colour, float4* rec1, float4* rec2, Counters* counters,
                                  cudaStream_t stream);
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
@@ -773,8 +773,11 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   // 1. Projection.
   // The cull pass's candidate list lives in the depth sort's second key buffer, which is free
   // until the sort starts.
+  // The colours are evaluated in the projection, unless the caller's SH coefficients may still
+  // be in flight: then after the sorts, behind the caller's event.
+  const bool defer_colour = cfg.sh_ready_event != nullptr;
   RGS_CUDA(launch_preprocess_forward(views, consts, *g, s->rec0, s->rec1, s->rec2, s->ntiles,
-                                     s->vis_keys[1], s->vis_bits, cnt, stream),
+                                     s->vis_keys[1], s->vis_bits, defer_colour, cnt, stream),
            "preprocess");
   RGS_CUDA(mark(ctx, *s, 1, stream, capturing), "event");
   // 2. Visible entries with depth keys, in (view, Gaussian) order.
@@ -846,14 +849,16 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
   s->sorted_vals = s->pair_vals[alt ? 1 : 0];
   RGS_CUDA(mark(ctx, *s, 6, stream, capturing), "event");
   // 7. Tile ranges.
-  // Tile ranges and the colours of the visible entries, in one launch: the colours are the
-  // first read of the SH coefficients, so the caller's upload of them may run until here.
-  if (cfg.sh_ready_event)
+  // Tile ranges and, when deferred, the colours of the visible entries, in one launch: the
+  // colours are then the first read of the SH coefficients, so the caller's upload of them may
+  // run until here.
+  if (defer_colour)
     RGS_CUDA(cudaStreamWaitEvent(stream, static_cast<cudaEvent_t>(cfg.sh_ready_event), 0),
              "wait for the SH coefficients");
   RGS_CUDA(launch_ranges_colour(sorted_keys, views.total_tiles, s->ranges,
                                 (uint32_t)std::min<int64_t>(pair_bound, s->pair_cap), views, *g,
-                                s->vis_list, vis_cap, s->rec1, s->rec2, cnt, stream),
+                                s->vis_list, vis_cap, defer_colour, s->rec1, s->rec2, cnt,
+                                stream),
            "tile ranges and colours");
   RGS_CUDA(mark(ctx, *s, 7, stream, capturing), "event");
   // 8. Blend.

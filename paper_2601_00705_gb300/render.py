@@ -52,8 +52,9 @@ class Renderer:
         poses that replace the cameras' poses (read on the device, so a pose the device updates
         needs no host round trip).
         sh_event: optional recorded CUDA event after which `sh` holds its values; the forward
-        waits for it only where it first reads the coefficients (after the sorts), so their
-        upload can overlap the projection and the sorts."""
+        then evaluates the colours after the sorts and waits for it only there, so the upload of
+        the coefficients can overlap the projection and the sorts (without it the projection
+        evaluates them)."""
         dev = self.device
         n = int(means.shape[0])
         K = int(sh.shape[1]) if sh.dim() == 3 else 0

@@ -343,3 +343,41 @@ def test_sh_event_defers_the_wait_for_the_coefficients():
     assert r2.stats(got[3])["status"] == 0
     r.release(ref[3])
     r2.release(got[3])
+
+
+def test_deferred_colours_treat_nonfinite_sh_like_the_projection():
+    # With an SH event the colours are evaluated after the sorts, and an entry with a non-finite
+    # coefficient is kept in the lists but covers no pixel; without one the projection culls it.
+    # Images are identical and gradients agree; both count the entry as culled.
+    wl = synthetic.tiny(n=300)
+    g = {k: v.copy() for k, v in wl.gaussians.as_dict().items()}
+    proj = oracle.project(g, wl.cameras)
+    m2 = proj["mean2d"][0]
+    on = np.nonzero(proj["valid"][0] & (m2[:, 0] > 10) & (m2[:, 0] < 150) & (m2[:, 1] > 10) &
+                    (m2[:, 1] < 110))[0]
+    bad = int(on[5])
+    g["sh"][bad, 0, 1] = np.nan
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    p = [to_dev(g[k]) for k in keys]
+    n, K, V, P = 300, int(g["sh"].shape[1]), len(wl.cameras), wl.n_pixels
+    up = to_dev(np.random.default_rng(7).normal(0, 1e-3, size=(P, 3)))
+    ev = torch.cuda.Event()
+    ev.record()
+    outs = []
+    for kw in ({}, {"sh_event": ev}):
+        r = Renderer(0)
+        c, d, a, st = r.forward_raw(*p, wl.cameras, **kw)
+        gr = r.backward_raw(st, n, K, V, up, None, None, binding.GRAD_ALL)
+        torch.cuda.synchronize()
+        outs.append(((c, d, a), gr, r.stats(st)))
+        r.release(st)
+    (img0, g0, s0), (img1, g1, s1) = outs
+    for x, y in zip(img0, img1):
+        assert torch.equal(x, y)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose"):
+        a0, a1 = g0[k].cpu().numpy(), g1[k].cpu().numpy()
+        assert np.isfinite(a1).all(), k
+        np.testing.assert_allclose(a1, a0, rtol=1e-5, atol=1e-7 * float(np.abs(a0).max()))
+    assert not g1["means"][bad].any() and not g1["sh"][bad].any()
+    assert s0["n_nonfinite"] == 1 and s1["n_nonfinite"] == 1
+    assert s0["status"] == 0 and s1["status"] == 0
