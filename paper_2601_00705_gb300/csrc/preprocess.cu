@@ -525,36 +525,38 @@ __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
     }
     return;
   }
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  const uint32_t n_visible = counters->n_visible_kept;
-  const uint32_t stride = (gridDim.x - range_blocks) * kRangesColourThreads;
-  for (uint32_t k = (blockIdx.x - range_blocks) * kRangesColourThreads + threadIdx.x;
-       k < n_visible; k += stride) {
-    const uint32_t vi = order[k];
-    const int v = (int)(vi / (uint32_t)n);
-    const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
-    float shc[3 * K];
-    load_sh<DEG>(sh, i, shc);
-    bool sh_finite = true;
-#pragma unroll
-    for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
-    float4 r2 = rec2[vi];
-    if (!sh_finite) {
-      atomicAdd(&counters->n_nonfinite, 1u);
-      reinterpret_cast<float*>(rec1 + vi)[3] = -INFINITY;
-      r2.x = r2.y = r2.z = 0.0f;
+  if constexpr (DEG >= 0) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const uint32_t n_visible = counters->n_visible_kept;
+    const uint32_t stride = (gridDim.x - range_blocks) * kRangesColourThreads;
+    for (uint32_t k = (blockIdx.x - range_blocks) * kRangesColourThreads + threadIdx.x;
+         k < n_visible; k += stride) {
+      const uint32_t vi = order[k];
+      const int v = (int)(vi / (uint32_t)n);
+      const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
+      float shc[3 * K];
+      load_sh<DEG>(sh, i, shc);
+      bool sh_finite = true;
+  #pragma unroll
+      for (int a = 0; a < 3 * K; ++a) sh_finite = sh_finite && isfinite(shc[a]);
+      float4 r2 = rec2[vi];
+      if (!sh_finite) {
+        atomicAdd(&counters->n_nonfinite, 1u);
+        reinterpret_cast<float*>(rec1 + vi)[3] = -INFINITY;
+        r2.x = r2.y = r2.z = 0.0f;
+        rec2[vi] = r2;
+        continue;
+      }
+      const PoseRef ps = view_pose<kDevPose>(views, v);
+      const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1),
+                          __ldg(means + 3 * (size_t)i + 2)};
+      float rgb[3];
+      sh_colour<DEG>(shc, m, ps, rgb);
+      r2.x = rgb[0];
+      r2.y = rgb[1];
+      r2.z = rgb[2];
       rec2[vi] = r2;
-      continue;
     }
-    const PoseRef ps = view_pose<kDevPose>(views, v);
-    const float m[3] = {__ldg(means + 3 * (size_t)i), __ldg(means + 3 * (size_t)i + 1),
-                        __ldg(means + 3 * (size_t)i + 2)};
-    float rgb[3];
-    sh_colour<DEG>(shc, m, ps, rgb);
-    r2.x = rgb[0];
-    r2.y = rgb[1];
-    r2.z = rgb[2];
-    rec2[vi] = r2;
   }
 }
 
@@ -1069,6 +1071,15 @@ cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* r
       (colour_items + kRangesColourThreads - 1) / kRangesColourThreads, 4 * 152);
   if (range_blocks + colour_blocks == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
+  if (colour_blocks == 0) {
+    // Ranges only: the instance without the colour code keeps the registers, and so the
+    // occupancy, of a plain scan over the pairs.
+    e = launch_chained(ranges_colour_kernel<-1, false>, dim3(range_blocks),
+                       dim3(kRangesColourThreads), stream, keys, (uint32_t)total_tiles, ranges,
+                       range_blocks, views, g.n, g.means, g.sh, order, rec1, rec2, counters);
+    RGS_LAUNCHED();
+    return e;
+  }
 #define RGS_RANGES_COLOUR(D)                                                                   \
   e = launch_chained(views.pose_dev ? ranges_colour_kernel<D, true>                             \
                                     : ranges_colour_kernel<D, false>,                           \
