@@ -51,8 +51,8 @@ BWD_FLOP_PER_EVAL = 40
 # this kernel build on exactly this workload and tile configuration; any other combination
 # reports null. Keyed by (workload, kernel, tile_w x tile_h x pixels per thread).
 MEASURED_TRAFFIC: dict[tuple[str, str, str], float] = {
-    ("tum", "blend_backward", "16x16x8"): 79.5e6,
-    ("tum", "blend_forward", "16x16x4"): 45.7e6,
+    ("tum", "blend_backward", "16x16x8"): 79.4e6,
+    ("tum", "blend_forward", "16x16x4"): 45.6e6,
 }
 
 
