@@ -64,3 +64,30 @@ def test_create_without_gpu_fails_cleanly():
     h = ctypes.c_void_p()
     assert lib.rgs_create(ctypes.byref(h), 0) == binding.RGS_ERR_INVALID_ARG
     assert lib.rgs_create(None, 0) == binding.RGS_ERR_INVALID_ARG
+
+
+def test_single_pass_scan_sizes_and_refuses_bad_arguments_before_any_gpu_work():
+    lib = binding.load()
+    # Work area: a 16-byte header, then one 8-byte state per tile of 4096 elements, plus two
+    # (the bound the bitmask compaction also fits in).
+    for n in (0, 1, 4095, 4096, 4097, 1 << 20):
+        assert lib.rgs_single_pass_scan_bytes(n) == 16 + 8 * ((n + 4095) // 4096 + 2), n
+    assert lib.rgs_single_pass_scan_bytes(-1) == 0
+    p = ctypes.c_void_p
+    fake = 1 << 20  # never dereferenced: every call below returns before any GPU work
+    need = lib.rgs_single_pass_scan_bytes(4096)
+
+    def call(n, inp=fake, work=fake, nbytes=need, status=fake):
+        return lib.rgs_exclusive_scan_u32_single_pass(p(inp), p(fake), n, None, p(work), nbytes,
+                                                      p(status), None)
+
+    bad = binding.RGS_ERR_INVALID_ARG
+    assert call(-1) == bad
+    assert call(1 << 31) == bad
+    assert call(4096, nbytes=need - 8) == bad
+    assert call(4096, work=fake + 8) == bad  # not 16-byte aligned
+    assert call(4096, work=None) == bad
+    assert call(4096, status=None) == bad
+    assert call(4096, inp=None) == bad
+    # Nothing to scan and no total to write: nothing runs.
+    assert call(0, inp=None) == binding.RGS_OK
