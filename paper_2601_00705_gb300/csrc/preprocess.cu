@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
 //    the run boundaries among them into `ranges` (zero on entry: tiles without pairs keep
 //    [0, 0)).
 //  * The other blocks: one thread per visible entry, in (view, Gaussian) order (grid-stride
-//    over `order`, the compacted list: neighbouring threads read neighbouring Gaussians' SH
-//    rows; in depth order the reads are scattered, which costs ~0.5 ms on 3M Gaussians whose
+//    over `list`, the compacted list: neighbouring threads read neighbouring Gaussians' SH
+//    rows; in depth order the reads are scattered, which costs ~0.15 ms on 3M Gaussians whose
 //    coefficients do not fit in L2). The colour from the SH
 //    coefficients for the direction camera centre -> Gaussian (Eq. app-sh), clamped at 0, into
 //    rec2.xyz. An entry with a non-finite coefficient gets log2 opacity -inf, so that it covers
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
     const uint32_t* __restrict__ keys, uint32_t total_tiles, uint2* __restrict__ ranges,
     uint32_t range_blocks, const __grid_constant__ Views views, int n,
     const float* __restrict__ means, const float* __restrict__ sh,
-    const uint32_t* __restrict__ order, float4* __restrict__ rec1, float4* __restrict__ rec2,
+    const uint32_t* __restrict__ list, float4* __restrict__ rec1, float4* __restrict__ rec2,
     Counters* __restrict__ counters) {
   chain_wait();
   if (blockIdx.x < range_blocks) {
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
     const uint32_t stride = (gridDim.x - range_blocks) * kRangesColourThreads;
     for (uint32_t k = (blockIdx.x - range_blocks) * kRangesColourThreads + threadIdx.x;
          k < n_visible; k += stride) {
-      const uint32_t vi = order[k];
+      const uint32_t vi = list[k];
       const int v = (int)(vi / (uint32_t)n);
       const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
       float shc[3 * K];
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const __grid_constant__ Views views, const Consts c, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, const float* __restrict__ sh,
-    const uint32_t* __restrict__ order, const Counters* __restrict__ counters,
+    const uint32_t* __restrict__ list, const Counters* __restrict__ counters,
     float* __restrict__ g2d, unsigned long long* __restrict__ vis_mask, uint32_t grad_mask,
     float* __restrict__ pose_partial) {
   chain_wait();
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
   const uint32_t n_visible = counters->n_visible_kept;
   for (uint32_t k = blockIdx.x * kPreThreads + threadIdx.x; k < n_visible;
        k += gridDim.x * kPreThreads) {
-    const uint32_t vi = order[k];
+    const uint32_t vi = list[k];
     const int v = (int)(vi / (uint32_t)n);
     const int i = (int)(vi - (uint32_t)v * (uint32_t)n);
     float m[3], ls[3], q[4], shc[3 * K];
@@ -1060,7 +1060,7 @@ cudaError_t launch_preprocess_forward(const Views& views, const Consts& c,
 
 cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* ranges,
                                  uint32_t pair_capacity, const Views& views,
-                                 const rgs_gaussians& g, const uint32_t* order, int64_t vis_cap,
+                                 const rgs_gaussians& g, const uint32_t* list, int64_t vis_cap,
                                  bool colour, float4* rec1, float4* rec2, Counters* counters,
                                  cudaStream_t stream) {
   const uint32_t range_blocks =
@@ -1076,7 +1076,7 @@ cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* r
     // occupancy, of a plain scan over the pairs.
     e = launch_chained(ranges_colour_kernel<-1, false>, dim3(range_blocks),
                        dim3(kRangesColourThreads), stream, keys, (uint32_t)total_tiles, ranges,
-                       range_blocks, views, g.n, g.means, g.sh, order, rec1, rec2, counters);
+                       range_blocks, views, g.n, g.means, g.sh, list, rec1, rec2, counters);
     RGS_LAUNCHED();
     return e;
   }
@@ -1085,7 +1085,7 @@ cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* r
                                     : ranges_colour_kernel<D, false>,                           \
                      dim3(range_blocks + colour_blocks), dim3(kRangesColourThreads), stream,    \
                      keys, (uint32_t)total_tiles, ranges, range_blocks, views, g.n, g.means,    \
-                     g.sh, order, rec1, rec2, counters)
+                     g.sh, list, rec1, rec2, counters)
   switch (g.sh_degree) {
     case 0: RGS_RANGES_COLOUR(0); break;
     case 1: RGS_RANGES_COLOUR(1); break;
@@ -1106,7 +1106,7 @@ int preprocess_backward_blocks(int64_t vn) {
 
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, unsigned long long* vis_mask,
-                                       const uint32_t* order, const Counters* counters,
+                                       const uint32_t* list, const Counters* counters,
                                        int64_t vn, float* g2d, uint32_t grad_mask,
                                        float* d_means, float* d_log_scales, float* d_quats,
                                        float* d_logits, float* d_sh, float* pose_partial,
@@ -1118,7 +1118,7 @@ cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
   e = launch_chained(views.pose_dev ? backward_view_kernel<D, true>                               \
                                     : backward_view_kernel<D, false>,                             \
                      dim3(blocks1), dim3(kPreThreads), stream, views, c, g.n, g.means,            \
-                     g.log_scales, g.quats, g.opacity_logits, g.sh, order, counters, g2d,         \
+                     g.log_scales, g.quats, g.opacity_logits, g.sh, list, counters, g2d,          \
                      vis_mask, grad_mask, pose_partial)
     switch (g.sh_degree) {
       case 0: RGS_BWD_VIEW(0); break;

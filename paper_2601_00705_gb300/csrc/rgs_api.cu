@@ -36,7 +36,7 @@ cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* r
 int preprocess_backward_blocks(int64_t vn);
 cudaError_t launch_preprocess_backward(const Views& views, const Consts& c,
                                        const rgs_gaussians& g, unsigned long long* vis_mask,
-                                       const uint32_t* order, const Counters* counters,
+                                       const uint32_t* list, const Counters* counters,
                                        int64_t vn, float* g2d, uint32_t grad_mask,
                                        float* d_means, float* d_log_scales, float* d_quats,
                                        float* d_logits, float* d_sh, float* pose_partial,
