@@ -29,7 +29,7 @@ def _scan(lib, x, out, work, status, total=None):
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def _work(lib, n):
+def _zeroed_area(lib, n):
     nbytes = int(lib.rgs_single_pass_scan_bytes(n))
     return torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
 
@@ -48,7 +48,7 @@ def test_matches_numpy(n):
     out = torch.empty_like(x)
     total = torch.zeros(1, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    work = _work(lib, n)
+    work = _zeroed_area(lib, n)
     assert _scan(lib, x, out, work, status, total) == 0
     torch.cuda.synchronize()
     ref = np.concatenate([[0], np.cumsum(a, dtype=np.uint32)[:-1]]).astype(np.uint32)
@@ -68,7 +68,7 @@ def test_empty_input_writes_zero_total():
     x = torch.zeros(1, dtype=torch.int32, device="cuda")
     total = torch.full((1,), 7, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    work = _work(lib, 0)
+    work = _zeroed_area(lib, 0)
     assert lib.rgs_exclusive_scan_u32_single_pass(
         ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 0,
         ctypes.c_void_p(total.data_ptr()), ctypes.c_void_p(work.data_ptr()), work.numel(),
@@ -83,7 +83,7 @@ def test_wait_for_an_unpublished_tile_is_bounded_and_reported():
     x = _u32(np.ones(n, np.uint32))
     out = torch.empty_like(x)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    work = _work(lib, n)
+    work = _zeroed_area(lib, n)
     work[0] = 1  # ticket counter starts at 1: no block takes tile 0, which nothing publishes
     t0 = time.time()
     assert _scan(lib, x, out, work, status) == 0
@@ -104,7 +104,7 @@ def test_bad_arguments_are_refused():
     lib = binding.load()
     x = torch.zeros(4096, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    work = _work(lib, 4096)
+    work = _zeroed_area(lib, 4096)
     small = int(lib.rgs_single_pass_scan_bytes(4096)) - 8
     p = ctypes.c_void_p
     assert lib.rgs_exclusive_scan_u32_single_pass(p(x.data_ptr()), p(x.data_ptr()), 4096, None,
