@@ -5,13 +5,19 @@ One step = one forward + backward of the whole hot path over one batch: preproce
 projection), compaction, depth sort, pair duplication, tile sort, tile ranges, forward blend,
 backward blend, backward preprocess with the per-view SE(3) twist gradient, for every view of the
 batch in one launch sequence, replayed as one CUDA graph. Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed
-steps. The default workload is the TUM-shaped mapping window: 10 keyframes at 640x480 over
-150k Gaussians with SH degree 3, all parameter gradients and the per-view pose gradients.
+steps. The default workload is the largest single-GPU one: 16 views at 1920x1080 over 3M Gaussians
+(log-scales N(-4, 0.7), SH degree 3), all parameter gradients and the per-view pose gradients;
+`--workload tum` selects the TUM-shaped 10-keyframe 640x480 window over 150k Gaussians.
 
 Under torchrun each rank renders its own replica of the workload on its own GPU (weak scaling,
 no collective on the data path); `value` is the pixels of all ranks over the slowest rank's time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+`--profile-step` instead runs --steps eager forward + backward steps in a fixed tile configuration
+(`--tile WxHxP`, `--backward-ppt P`), with no autotuning, no graph and no timing, so that a
+kernel profiler's launch filter sees exactly --steps launches of each kernel (forward, then
+backward); with `--seeding M` it runs --steps dense initialisations of M matched pixels instead.
 """
 from __future__ import annotations
 
@@ -47,13 +53,27 @@ L2_FLUSH_BYTES = 256 << 20
 FWD_FLOP_PER_EVAL = 15
 BWD_FLOP_PER_EVAL = 40
 
-# DRAM bytes (read + written) per launch of a dominant kernel, from one ncu capture of exactly
-# this kernel build on exactly this workload and tile configuration; any other combination
-# reports null. Keyed by (workload, kernel, tile_w x tile_h x pixels per thread).
-MEASURED_TRAFFIC: dict[tuple[str, str, str], float] = {
-    ("tum", "blend_backward", "16x16x8"): 79.4e6,
-    ("tum", "blend_forward", "16x16x4"): 45.6e6,
-}
+# DRAM bytes (read + written) per launch of a dominant kernel come from the ncu captures
+# summarised in this file's table (one row per workload, kernel and tile configuration); a
+# combination without a row reports null.
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+
+
+def measured_traffic(workload: str, kernel: str, tile: str):
+    """DRAM bytes per launch of `kernel` on `workload` at tile configuration `tile`
+    ("16x16x8": tile width x height x pixels per thread), from the table rows
+    `| workload | kernel | tile | bytes per launch | ... |`, or None."""
+    if not os.path.exists(TRAFFIC_TABLE):
+        return None
+    with open(TRAFFIC_TABLE) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 4 and cells[:3] == [workload, kernel, tile]:
+                try:
+                    return float(cells[3])
+                except ValueError:
+                    return None
+    return None
 
 
 def parse():
@@ -61,9 +81,69 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", default="tum", choices=sorted(WORKLOAD_NAMES))
+    p.add_argument("--workload", default="large", choices=sorted(WORKLOAD_NAMES))
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--profile-step", action="store_true",
+                   help="eager steps for a kernel profiler (no timing, no autotuning)")
+    p.add_argument("--tile", default="16x16x8", help="--profile-step: tile_w x tile_h x pixels "
+                   "per thread of the forward blend")
+    p.add_argument("--backward-ppt", type=int, default=0,
+                   help="--profile-step: pixels per thread of the backward blend (0: as forward)")
+    p.add_argument("--seeding", type=int, default=0,
+                   help="--profile-step: run the dense initialisation on this many matched pixels")
+    p.add_argument("--views", type=int, default=0,
+                   help="--profile-step: number of views of the workload (0: its own)")
     return p.parse_args()
+
+
+def run_profile_step(args):
+    """Eager steps for a kernel profiler: the library's public path, fixed configuration, the
+    counters of the last forward printed as one JSON line."""
+    import torch
+    from paper_2601_00705_gb300 import binding, synthetic
+    from paper_2601_00705_gb300.render import Renderer
+    dev = torch.device("cuda", 0)
+    if args.seeding:
+        from paper_2601_00705_gb300 import seeding
+        r = Renderer(dev)
+        c = synthetic.correspondences(m=args.seeding, k=4)
+        for _ in range(args.steps):
+            tri = seeding.triangulate(r.ctx, c.cameras, c.ref_view, c.ref_xy, c.nb_view, c.nb_xy,
+                                      c.nb_conf, r.device, r.stream_handle())
+            seeds = seeding.init_seeds(r.ctx, c.cameras, tri, c.observed, c.gain_bias, r.device)
+        torch.cuda.synchronize()
+        print(json.dumps({"seeding": args.seeding, "steps": args.steps,
+                          "hypotheses": int((c.nb_view >= 0).sum()),
+                          "accepted": int(tri["valid"].sum().item()),
+                          "seeds": int(seeds["index"].numel())}))
+        return
+    tw, th, ppt = (int(x) for x in args.tile.split("x"))
+    wl = synthetic.make(args.workload)
+    if args.views:  # the same scene seen from the first views only (a smaller capture)
+        wl = synthetic.Workload(wl.name, wl.gaussians, wl.cameras[:args.views], wl.grad_mask,
+                                wl.depth_weight)
+    g = wl.gaussians.as_dict()
+    n, K, V = g["means"].shape[0], g["sh"].shape[1], len(wl.cameras)
+
+    def up(a):
+        return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+
+    params = [up(g[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    d_color, d_depth, _ = synthetic.upstream(wl)
+    d_color = up(d_color)
+    d_depth = up(d_depth) if wl.depth_weight else None
+    mask = binding.GRAD_POSE if wl.grad_mask == "pose" else binding.GRAD_ALL
+    r = Renderer(dev, tile_w=tw, tile_h=th, pixels_per_thread=ppt,
+                 backward_pixels_per_thread=args.backward_ppt)
+    cams = binding.make_cameras(wl.cameras)
+    state = 0
+    for _ in range(args.steps):
+        _, _, _, state = r.forward_raw(*params, cams, state=state)
+        r.backward_raw(state, n, K, V, d_color, d_depth, None, mask)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"workload": args.workload, "tile": args.tile,
+                      "backward_ppt": args.backward_ppt or ppt, "steps": args.steps,
+                      "counters": r.stats(state)}))
 
 
 def dist_setup(args):
@@ -206,6 +286,32 @@ class ClockSampler:
 # ------------------------------------------------------------------------------ oracle (CPU)
 
 CPU_SAMPLE_PIXELS = 3_000_000  # bounds the oracle's share of a default run to seconds
+CPU_BASELINE_PIXELS = 240_000   # all host cores: pixels per timed oracle call
+CPU_BASELINE_PIXELS_1T = 24_000  # one thread
+REFERENCE_STEP_PIXELS = 120_000  # the --impl reference arm: pixels per step
+
+
+def _oracle_inputs(wl, views, max_pixels, seed=4001):
+    """The oracle's inputs for the given views of the workload: the Gaussians, cameras, upstream
+    gradients and, above max_pixels, a seeded mask of whole 16x16 patches."""
+    from paper_2601_00705_gb300 import synthetic
+    cams = [wl.cameras[v] for v in views]
+    sub = synthetic.Workload(wl.name, wl.gaussians, cams, wl.grad_mask, wl.depth_weight)
+    d_color, d_depth, _ = synthetic.upstream(sub)
+    total = sum(c["width"] * c["height"] for c in cams)
+    mask = None
+    if total > max_pixels:
+        mask = synthetic.patch_mask(cams, fraction=max_pixels / total, patch=16, seed=seed)
+    pixels = total if mask is None else int(mask.sum())
+    return cams, d_color, (d_depth if wl.depth_weight else None), mask, pixels, total
+
+
+def _time_oracle(wl, cams, d_color, d_depth, mask, threads, backward):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.render(wl.gaussians.as_dict(), cams, d_color=d_color if backward else None,
+                  d_depth=d_depth if backward else None, pixel_mask=mask, threads=threads)
+    return time.perf_counter() - t0
 
 
 def oracle_sample(wl, views, max_pixels=CPU_SAMPLE_PIXELS):
@@ -213,23 +319,51 @@ def oracle_sample(wl, views, max_pixels=CPU_SAMPLE_PIXELS):
     max_pixels it renders a seeded subset of whole 16x16 patches of those views. Returns
     (pixels rendered, seconds, threads, fraction of the views' pixels rendered)."""
     import oracle
-    from paper_2601_00705_gb300 import synthetic
-    g = wl.gaussians.as_dict()
-    cams = [wl.cameras[v] for v in views]
-    sub = synthetic.Workload(wl.name, wl.gaussians, cams, wl.grad_mask, wl.depth_weight)
-    d_color, d_depth, _ = synthetic.upstream(sub)
-    total = sum(c["width"] * c["height"] for c in cams)
-    mask = None
-    if total > max_pixels:
-        mask = synthetic.patch_mask(cams, fraction=max_pixels / total, patch=16, seed=4001)
-    threads = oracle.default_threads()
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.render(g, cams, d_color=d_color, d_depth=d_depth if wl.depth_weight else None,
-                  pixel_mask=mask, threads=threads)
-    dt = time.perf_counter() - t0
-    pixels = total if mask is None else int(mask.sum())
+    cams, d_color, d_depth, mask, pixels, total = _oracle_inputs(wl, views, max_pixels)
+    threads = oracle.default_threads()
+    dt = _time_oracle(wl, cams, d_color, d_depth, mask, threads, True)
     return pixels, dt, threads, pixels / total
+
+
+def cpu_baseline(wl, reps=3):
+    """The FP64 oracle on this host: forward alone and forward + backward (the backward's time is
+    their difference), each the median of `reps` calls, on every host core and on one thread,
+    over seeded 16x16-patch samples: CPU_BASELINE_PIXELS of all views on every core,
+    CPU_BASELINE_PIXELS_1T of the first view on one thread (each call also projects every
+    Gaussian into each of its views). A baseline, not the target."""
+    import oracle
+    oracle.build()
+    views = list(range(len(wl.cameras)))
+    out = {}
+    for label, vs, budget, threads in (
+            ("all_cores", views, CPU_BASELINE_PIXELS, oracle.default_threads()),
+            ("threads_1", views[:1], CPU_BASELINE_PIXELS_1T, 1)):
+        cams, d_color, d_depth, mask, pixels, total = _oracle_inputs(wl, vs, budget)
+        fwd = float(np.median([_time_oracle(wl, cams, d_color, d_depth, mask, threads, False)
+                               for _ in range(reps)]))
+        fb = float(np.median([_time_oracle(wl, cams, d_color, d_depth, mask, threads, True)
+                              for _ in range(reps)]))
+        out[label] = {"threads": threads, "pixels": pixels, "fraction": pixels / total,
+                      "fwd_s": fwd, "fwd_bwd_s": fb, "fwd_mpix_s": pixels / fwd / 1e6,
+                      "bwd_mpix_s": pixels / max(fb - fwd, 1e-9) / 1e6,
+                      "fwd_bwd_mpix_s": pixels / fb / 1e6}
+    a = out["all_cores"]
+    return {"value": a["fwd_bwd_mpix_s"], "unit": "Mpix/s", "cores": a["threads"],
+            "nproc": os.cpu_count(), "kind": "oracle", "median_of": reps,
+            "fwd": {"value": a["fwd_mpix_s"], "unit": "Mpix/s"},
+            "bwd": {"value": a["bwd_mpix_s"], "unit": "Mpix/s"},
+            "threads_1": {"value": out["threads_1"]["fwd_bwd_mpix_s"],
+                          "fwd": out["threads_1"]["fwd_mpix_s"],
+                          "bwd": out["threads_1"]["bwd_mpix_s"], "unit": "Mpix/s",
+                          "pixels": out["threads_1"]["pixels"]},
+            "sample": f"seeded whole 16x16 patches: {a['pixels']} pixels of all {len(views)} views "
+                      f"({100 * a['fraction']:.1f} %) on {a['threads']} threads, "
+                      f"{out['threads_1']['pixels']} pixels of the first view on one thread; "
+                      "forward alone and "
+                      f"forward + backward, median of {reps} calls each (the projection of "
+                      "every Gaussian in every view is part of each call)",
+            "detail": out}
 
 
 def run_reference(args, world, rank):
@@ -240,10 +374,10 @@ def run_reference(args, world, rank):
     wl = synthetic.make(args.workload)
     V = len(wl.cameras)
     for w in range(args.warmup):
-        oracle_sample(wl, [w % V])
+        oracle_sample(wl, [w % V], REFERENCE_STEP_PIXELS)
     total_px, total_s, threads, frac = 0, 0.0, 1, 1.0
     for k in range(args.steps):
-        px, dt, threads, frac = oracle_sample(wl, [k % V])
+        px, dt, threads, frac = oracle_sample(wl, [k % V], REFERENCE_STEP_PIXELS)
         total_px += px
         total_s += dt
     value = total_px / total_s / 1e6
@@ -255,8 +389,9 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOAD_NAMES[args.workload], "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
                          "sample": f"one view of the {V}-view window per step, views in turn "
-                                   f"(forward + backward; {100 * frac:.0f} % of its pixels, "
-                                   "whole 16x16 patches, when it exceeds 3 Mpix)"},
+                                   f"(forward + backward; {100 * frac:.1f} % of its pixels, "
+                                   f"whole 16x16 patches, when it exceeds "
+                                   f"{REFERENCE_STEP_PIXELS} pixels)"},
         "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -531,6 +666,16 @@ def run_ours(args, world, rank, local):
     ms_per_step = total_ms / args.steps
     value = throughput(world, pixels, args.steps, total_ms)
     stats = r.stats(state)
+    # Device footprint of the timed step: everything the library holds for it (saved state,
+    # pair lists, scratch) plus the caller's tensors the step reads and writes; and the device's
+    # used memory as the driver reports it right after the timed region (the CUDA context, the
+    # L2-flush buffer and torch's cache included).
+    step_tensors = params + [u for u in ups if u is not None] + list(images) + list(grads.values())
+    caller_bytes = sum(t.numel() * t.element_size() for t in step_tensors)
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    memory = {"state_bytes": int(stats["state_bytes"]), "caller_bytes": int(caller_bytes),
+              "peak_hbm_bytes": int(stats["state_bytes"] + caller_bytes),
+              "device_used_bytes": int(total_b - free_b), "device_total_bytes": int(total_b)}
 
     # Phase breakdown (outside the timed region): the same step captured with an event at every
     # phase boundary, replayed with the same L2 flush.
@@ -693,8 +838,8 @@ def run_ours(args, world, rank, local):
         achieved = work[dominant] / (phases[dominant] / 1e3) / 1e12
         ppt = tuned["pixels_per_thread" if dominant == "blend_forward"
                     else "backward_pixels_per_thread"]
-        traffic = MEASURED_TRAFFIC.get(
-            (args.workload, dominant, f"{tuned['tile_w']}x{tuned['tile_h']}x{ppt}"))
+        traffic = measured_traffic(args.workload, dominant,
+                                   f"{tuned['tile_w']}x{tuned['tile_h']}x{ppt}")
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                     "peak_source": f"FP32 FMA pipe: 128 lanes x 2 FLOP x {props.multi_processor_count}"
@@ -736,6 +881,7 @@ def run_ours(args, world, rank, local):
                 "cuda_graph": True},
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
         "roofline": roofline,
+        "memory": memory,
         "batched_vs_per_view": {"per_view_loop_ms": loop_ms_per_step,
                                 "batched_ms": ms_per_step,
                                 "speedup": loop_ms_per_step / ms_per_step},
@@ -749,12 +895,7 @@ def run_ours(args, world, rank, local):
     line["mapping"] = measure_mapping(r, params, wl.cameras, images, mask, args.steps,
                                       float(peaks.get("hbm_gbs", 6800.0)))
     if world == 1 and rank == 0:
-        px, dt, threads, frac = oracle_sample(wl, list(range(V)))
-        line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": threads,
-                                "kind": "oracle",
-                                "sample": f"all {V} views of the workload once, forward + "
-                                          f"backward, {px} pixels ({100 * frac:.0f} % of them, "
-                                          f"whole 16x16 patches), {dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -764,6 +905,9 @@ def run_ours(args, world, rank, local):
 
 def main():
     args = parse()
+    if args.profile_step:
+        run_profile_step(args)
+        return
     if args.impl == "reference":
         # Only rank 0 times the CPU oracle; other ranks exit at once without work.
         if int(os.environ.get("RANK", "0")) == 0:

@@ -497,13 +497,16 @@ rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
  *   n: 0 <= n <= RGS_STATIC_SCAN_MAX_N; larger n returns RGS_ERR_TOO_LARGE before any GPU work.
  *   stream: cudaStream_t as void* (NULL = legacy default stream). Runs on the current device.
  * Its scratch (one u32 per 4096 elements) is a fixed 64 KiB device array inside the library,
- * held by every GPU that loads the library until the process exits. The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture. All calls on a device share the array and keep the
- * last call's contents; nothing in it needs to start at zero. Calls whose executions overlap on
- * the GPU (different streams, or different host threads, without ordering) race on the array:
- * serialise them. Returns RGS_ERR_INVALID_ARG for null arrays with n > 0 and RGS_ERR_CUDA if a
- * CUDA call fails. */
+ * held by every GPU that loads the library until the process exits. Every call looks up that
+ * array's device address in the current context (cudaGetSymbolAddress), so the first call on a
+ * device also loads the library's device code there: make that first call before any stream
+ * capture. All calls on a device share the array and keep the last call's contents; nothing in
+ * it needs to start at zero. Calls whose executions overlap on the GPU (different streams, or
+ * different host threads, without ordering) race on the array: serialise them.
+ * Asynchronous: unlike rgs_exclusive_scan_u32, which synchronises its stream before returning,
+ * this call only enqueues the scan on `stream`; synchronise the stream before reading out or
+ * total_out on the host. Returns RGS_ERR_INVALID_ARG for null arrays with n > 0 and RGS_ERR_CUDA
+ * if a CUDA call fails. */
 #define RGS_STATIC_SCAN_MAX_N (1 << 26)
 rgs_status rgs_exclusive_scan_u32_static(const uint32_t* in, uint32_t* out, int64_t n,
                                          uint32_t* total_out, void* stream);

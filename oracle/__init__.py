@@ -37,10 +37,13 @@ DEFAULT_CONFIG = dict(
     eps2d=0.3,
     jac_clamp=1.3,
     bg=(0.0, 0.0, 0.0),
-    # Ambiguity margins (relative) for the discrete decisions an FP32 renderer may take the other way.
-    margin_alpha=2e-5,
-    margin_t=2e-4,
-    margin_z=1e-12,
+    # Ambiguity margins (relative) for the discrete decisions an FP32 renderer may take the other
+    # way, on top of the modelled float32 error of each quantity (see rgs_oracle.cpp):
+    # margin_alpha around alpha_min / alpha_max in ln(o G) (the hardware exponential's error),
+    # margin_t around t_min in ln T, margin_z the oracle's own depth rounding.
+    margin_alpha=2e-6,
+    margin_t=5e-6,
+    margin_z=1e-15,
     margin_g=1e-5,
     margin_effect=1e-5,
     margin_cont=3e-5,
@@ -50,13 +53,12 @@ DEFAULT_CONFIG = dict(
 # decision (coverage, stop, order, near plane) lies within FP32 rounding of its threshold, so an
 # FP32 renderer may legitimately take the other branch; BACKWARD_AMBIGUOUS adds gradient kinks.
 # AMB_COND (the propagated FP32 error bound of the colour exceeds margin_cont) involves no
-# decision: such pixels are compared in the forward at the full tolerance, but get no upstream
-# gradient in the backward comparison, where derivatives of their ill-conditioned covariances
-# amplify the FP32 error further.
+# decision and excludes nothing: such pixels are compared at the full tolerance in both the
+# forward and the backward comparison; the bit only reports where the bound is large.
 AMB_ALPHA_MIN, AMB_ALPHA_MAX, AMB_T_MIN, AMB_DEPTH_TIE, AMB_NEAR, AMB_GRAD_KINK, AMB_COND = (
     1, 2, 4, 8, 16, 32, 64)
 FORWARD_AMBIGUOUS = AMB_ALPHA_MIN | AMB_T_MIN | AMB_DEPTH_TIE | AMB_NEAR
-BACKWARD_AMBIGUOUS = FORWARD_AMBIGUOUS | AMB_ALPHA_MAX | AMB_GRAD_KINK | AMB_COND
+BACKWARD_AMBIGUOUS = FORWARD_AMBIGUOUS | AMB_ALPHA_MAX | AMB_GRAD_KINK
 
 _lock = threading.Lock()
 _lib = None
@@ -93,6 +95,8 @@ def _load():
             lib.oracle_render.argtypes = [I, I, P, P, P, P, P, I, P, P, P, I, I,
                                           P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.oracle_render.restype = I
+            lib.oracle_log_og_bound.argtypes = [I, I, P, P, P, P, P, I, P, P, I, P, P]
+            lib.oracle_log_og_bound.restype = None
             lib.oracle_set_dense_limit.argtypes = [ctypes.c_double]
             lib.oracle_set_dense_limit.restype = None
             _lib = lib
@@ -182,6 +186,24 @@ def project(g: dict, cameras, config=None) -> dict:
     return dict(valid=out[..., 0] > 0.5, mean2d=out[..., 1:3], cov2d=out[..., 3:6],
                 conic=out[..., 6:9], depth=out[..., 9], opacity=out[..., 10], rgb=out[..., 11:14],
                 kappa=out[..., 14], flags=out[..., 15].astype(np.int32))
+
+
+def log_og_bound(g: dict, cameras, items, config=None) -> tuple[np.ndarray, np.ndarray]:
+    """ln(o G) in double precision at (view, Gaussian, x, y) items [m, 4], and the float32 error
+    bound the oracle's ambiguity flags use there; (-inf, 0) for a Gaussian culled in the view."""
+    lib = _load()
+    means = _f64(g["means"], (-1, 3))
+    n = means.shape[0]
+    sh = _f64(g["sh"])
+    deg = _degree_of(sh)
+    cams = _cam_array(cameras)
+    it = _f64(items, (-1, 4))
+    out = np.zeros((it.shape[0], 2), dtype=np.float64)
+    lib.oracle_log_og_bound(n, deg, _ptr(means), _ptr(_f64(g["log_scales"], (n, 3))),
+                            _ptr(_f64(g["quats"], (n, 4))), _ptr(_f64(g["opacity_logits"], (n,))),
+                            _ptr(sh), cams.shape[0], _ptr(cams), _ptr(_cfg_array(config)),
+                            it.shape[0], _ptr(it), _ptr(out))
+    return out[:, 0], out[:, 1]
 
 
 def render(g: dict, cameras, config=None, *, d_color=None, d_depth=None, d_alpha=None,

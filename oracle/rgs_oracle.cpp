@@ -63,7 +63,7 @@ struct Config {
   double bg[3];
   double margin_alpha;  // relative margin around alpha_min and alpha_max
   double margin_t;      // relative margin around t_min
-  double margin_z;      // relative margin of a depth to the nearest float32 rounding midpoint
+  double margin_z;      // relative slack of this oracle's own depth rounding (see gaussian_forward)
   double margin_g;      // relative margin for per-Gaussian branch points (znear, clamps)
   double margin_effect; // smallest image change a flipped alpha_min decision must be able to
                         // cause for the pixel to be flagged
@@ -83,18 +83,24 @@ enum AmbiguityBits {
   kAmbAlphaMin = 1,     // a covering test alpha >= alpha_min within margin_alpha
   kAmbAlphaMax = 2,     // the alpha clamp at alpha_max within margin_alpha (gradient kink)
   kAmbTMin = 4,         // the stop test T' < t_min within margin_t
-  kAmbDepthTie = 8,     // a covering Gaussian's depth within margin_z of a float32 rounding midpoint
+  kAmbDepthTie = 8,     // a depth key that may round either way next to another key of the list
   kAmbNear = 16,        // a covering Gaussian's depth within margin_g of znear (cull decision)
   kAmbGradKink = 32,    // a covering Gaussian at the Jacobian clamp or colour clamp (gradient kink)
   kAmbCond = 64,        // the float32 evaluation error bound of the pixel exceeds margin_cont
 };
 
-// Unit roundoff of float32. A float32 renderer evaluates ln(o G) at a pixel with an error of a
-// few units of it times the magnitude of the quadratic form's terms, plus the error of the conic
-// itself, which grows like sqrt(cond(Sigma^I)) times |ln G| (rounding J, R and the scales perturbs
-// the thin axis of the projected ellipse by that much). The oracle uses this bound, with a
-// safety factor of 8, to widen its decision margins and to flag pixels whose float32 value
-// cannot be expected within the tolerance.
+// Unit roundoff of float32. The float32 renderer this oracle is compared with evaluates the
+// exponent in whitened coordinates: with L L^T = (log2(e) / 2) Q (lower-triangular L, Q the conic),
+// log2(o G) = log2 o - (t^2 + s^2), (t, s) = L^T d, where t and s are formed from the products
+// l11 dx, l21 dy, l22 dy (dy measured from a tile row at most 8 px away, then moved to the pixel's
+// row). Its error is a few units of the roundoff times (|t| + |s|) times the magnitude of those
+// products, plus the error of the conic itself. Sigma^I = A A^T + eps I with A = J R M
+// (M = R_q diag(s)): rounding J, R, R_q and the scales perturbs A by about the roundoff times
+// |J| s_max (the size A would have if the longest axis were not foreshortened), which moves
+// ln G by at most 2 |ln G| |dA| / sqrt(lambda_min(Sigma^I)); the oracle carries
+// amp = sqrt(max(|J|_F^2 s_max^2, lambda_max) / lambda_min) per (view, Gaussian). It uses this bound,
+// with a safety factor of 8, to widen its decision margins and to flag pixels whose float32
+// value cannot be expected within the tolerance.
 constexpr double kUnitRoundoff32 = 5.9604644775390625e-08;
 
 // ---------------------------------------------------------------------------------------------
@@ -226,17 +232,22 @@ void gaussian_forward(const double* mean, const double* log_scale, const double*
   f.z = f.mu_c[2];
   if (std::fabs(f.z - cfg.znear) <= cfg.margin_g * cfg.znear) f.flags |= 1;
   if (!(f.z > cfg.znear)) return;
-  // Near-to-far order compares depths rounded to float32 (the renderer's key precision).
-  // Flag a depth that lies within margin_z of the midpoint between two float32 values, where
-  // a nearly exact float32 evaluation could round the other way.
+  // Near-to-far order compares depths rounded to float32 (the renderer's key precision). A
+  // renderer that evaluates the depth as a compensated dot product (twice the working precision)
+  // gets the correctly rounded value unless the exact depth lies within that product's error,
+  // about 16 u32^2 (|R_2 . mu^W| summed termwise + |t_2|), of the midpoint between two float32
+  // values; such a depth is marked here (plus margin_z * z for this oracle's own rounding), and
+  // a pixel is flagged only if another Gaussian of its list has a key within one float32 step.
   f.zkey = static_cast<float>(f.z);
   {
     const double up = std::nextafter(f.zkey, std::numeric_limits<float>::infinity());
     const double dn = std::nextafter(f.zkey, -std::numeric_limits<float>::infinity());
     const double mid_up = 0.5 * (static_cast<double>(f.zkey) + up);
     const double mid_dn = 0.5 * (static_cast<double>(f.zkey) + dn);
-    if (std::fabs(f.z - mid_up) <= cfg.margin_z * f.z || std::fabs(f.z - mid_dn) <= cfg.margin_z * f.z)
-      f.flags |= 8;
+    const double sumabs = std::fabs(cam.R[2][0] * mean[0]) + std::fabs(cam.R[2][1] * mean[1]) +
+                          std::fabs(cam.R[2][2] * mean[2]) + std::fabs(cam.t[2]);
+    const double margin = cfg.margin_z * f.z + 16.0 * kUnitRoundoff32 * kUnitRoundoff32 * sumabs;
+    if (std::fabs(f.z - mid_up) <= margin || std::fabs(f.z - mid_dn) <= margin) f.flags |= 8;
   }
   // Unit quaternion and world covariance, Sigma^W = R_q diag(s^2) R_q^T (Appendix C.1).
   f.q_raw_norm = std::sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);
@@ -317,7 +328,8 @@ struct Splat {
   int flags = 0;
   float zkey = 0.0f;
   double mean2d[2], cov2d[3], conic[3], opacity, rgb[3], z;
-  double cond_sqrt;  // sqrt of the condition number of Sigma^I (dilation included)
+  double amp;        // float32 error amplification of the conic (see kUnitRoundoff32)
+  double chol[3] = {0.0, 0.0, 0.0};  // L L^T = (log2(e) / 2) conic (for the error bound)
 };
 
 Splat to_splat(const GaussFwd& f) {
@@ -336,15 +348,36 @@ Splat to_splat(const GaussFwd& f) {
   }
   s.opacity = f.opacity;
   s.z = f.z;
-  s.cond_sqrt = 1.0;
+  s.amp = 1.0;
   if (f.valid) {
     const double tr = f.cov2d[0][0] + f.cov2d[1][1];
     const double disc = std::sqrt(std::max(0.25 * tr * tr - f.det, 0.0));
     const double lmax = 0.5 * tr + disc;
     const double lmin = f.det / lmax;
-    s.cond_sqrt = std::sqrt(lmax / lmin);
+    const double jf2 = f.J[0][0] * f.J[0][0] + f.J[0][2] * f.J[0][2] + f.J[1][1] * f.J[1][1] +
+                       f.J[1][2] * f.J[1][2];
+    const double smax = std::max(f.s[0], std::max(f.s[1], f.s[2]));
+    s.amp = std::sqrt(std::max(jf2 * smax * smax, lmax) / lmin);
+    // L from the covariance: l11^2 = k a, l11 l21 = k b, l21^2 + l22^2 = k c for the conic
+    // (a, b, c) = (Syy, -Sxy, Sxx) / det and k = log2(e) / 2.
+    const double k = 0.5 / std::log(2.0);
+    s.chol[0] = std::sqrt(k * f.cov2d[1][1] / f.det);
+    s.chol[1] = -k * f.cov2d[0][1] / (f.det * s.chol[0]);
+    s.chol[2] = std::sqrt(k / f.cov2d[1][1]);
   }
   return s;
+}
+
+// ln G = -1/2 d^T Q d at offset d = (dx, dy) from the projected mean (Eq. alpha), and the
+// float32 error bound of ln(o G) there (see kUnitRoundoff32): the whitened offsets, the
+// magnitude of the products they are formed from, and the conic's own error.
+void exponent_and_bound(const Splat& f, double dx, double dy, double& power, double& err) {
+  power = -0.5 * (f.conic[0] * dx * dx + f.conic[2] * dy * dy) - f.conic[1] * dx * dy;
+  const double t = f.chol[0] * dx + f.chol[1] * dy, u = f.chol[2] * dy;
+  const double terms = std::fabs(f.chol[0] * dx) +
+                       (std::fabs(f.chol[1]) + std::fabs(f.chol[2])) * (std::fabs(dy) + 8.0);
+  const double mag = std::log(2.0) * ((std::fabs(t) + std::fabs(u)) * terms + t * t + u * u);
+  err = kUnitRoundoff32 * (8.0 * mag + 8.0 * std::fabs(power) * f.amp + 16.0);
 }
 
 // Screen-space gradient slots per (view, Gaussian).
@@ -523,10 +556,8 @@ void shade_pixel(const std::vector<Splat>& F, const std::vector<int>& cands, dou
     const Splat& f = F[idx];
     if (!f.valid) continue;
     const double dx = px - f.mean2d[0], dy = py - f.mean2d[1];
-    const double power = -0.5 * (f.conic[0] * dx * dx + f.conic[2] * dy * dy) - f.conic[1] * dx * dy;
-    const double mag = 0.5 * (std::fabs(f.conic[0]) * dx * dx + std::fabs(f.conic[2]) * dy * dy) +
-                       std::fabs(f.conic[1] * dx * dy);
-    const double err = kUnitRoundoff32 * (8.0 * mag + 8.0 * std::fabs(power) * f.cond_sqrt + 16.0);
+    double power, err;
+    exponent_and_bound(f, dx, dy, power, err);
     const double G = std::exp(power);
     const double oG = f.opacity * G;
     if (std::log(oG) < ln_amin - cfg.margin_alpha - err) continue;
@@ -551,12 +582,24 @@ void shade_pixel(const std::vector<Splat>& F, const std::vector<int>& cands, dou
         cfg.alpha_min * T * cmax >= cfg.margin_effect)
       amb |= kAmbAlphaMin;
     if (h.oG < cfg.alpha_min) continue;
-    if (F[h.idx].flags & 8) amb |= kAmbDepthTie;
+    // A depth key that may round the other way only matters next to another key of the list
+    // within one float32 step (the pair's order, or their tie-break, could change).
+    if (F[h.idx].flags & 8) {
+      for (size_t o = 0; o < hits.size(); ++o)
+        if (o != k && std::fabs(static_cast<double>(hits[o].zkey) - h.zkey) <=
+                          std::fabs(static_cast<double>(
+                              std::nextafter(h.zkey, std::numeric_limits<float>::infinity())) -
+                          h.zkey))
+          amb |= kAmbDepthTie;
+    }
     if (F[h.idx].flags & 1) amb |= kAmbNear;
     if (F[h.idx].flags & 6) amb |= kAmbGradKink;
     if (std::fabs(ln_oG - ln_amax) <= cfg.margin_alpha + h.err) amb |= kAmbAlphaMax;
     const double Tn = T * (1.0 - h.alpha);
-    const double errTn = errT + h.err * h.alpha / (1.0 - h.alpha);
+    // Error bound of ln T': the alpha error through ln(1 - alpha), plus the float32 arithmetic
+    // of T' = T - alpha T (two roundings, the first magnified by alpha / (1 - alpha)).
+    const double errTn = errT + (h.err + 2.0 * kUnitRoundoff32) * h.alpha / (1.0 - h.alpha) +
+                         2.0 * kUnitRoundoff32;
     if (std::fabs(std::log(Tn / cfg.t_min)) <= cfg.margin_t + errTn) amb |= kAmbTMin;
     if (Tn < cfg.t_min) break;
     const double w = h.alpha * T;
@@ -722,6 +765,34 @@ void oracle_project(int n, int degree, const double* means, const double* log_sc
       o[11] = f.rgb[0]; o[12] = f.rgb[1]; o[13] = f.rgb[2];
       o[14] = f.kappa; o[15] = f.flags;
     }
+  }
+}
+
+// ln(o G) in double precision and its float32 error bound for m (view, Gaussian, pixel) triples:
+// items[m, 4] = (view, Gaussian, x, y); out[m, 2] = (ln(o G), bound); a Gaussian culled in the
+// view gets (-inf, 0). Used to pin the bound against a float32 evaluation.
+void oracle_log_og_bound(int n, int degree, const double* means, const double* log_scales,
+                         const double* quats, const double* logits, const double* sh,
+                         int n_views, const double* cams, const double* cfgv, int m,
+                         const double* items, double* out) {
+  const Config cfg = read_config(cfgv);
+  const int K = (degree + 1) * (degree + 1);
+  for (int k = 0; k < m; ++k) {
+    const int v = static_cast<int>(items[4 * k]), i = static_cast<int>(items[4 * k + 1]);
+    out[2 * k] = -std::numeric_limits<double>::infinity();
+    out[2 * k + 1] = 0.0;
+    if (v < 0 || v >= n_views || i < 0 || i >= n) continue;
+    const Camera cam = read_camera(cams + 18 * v);
+    GaussFwd f;
+    gaussian_forward(means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i],
+                     sh + static_cast<size_t>(3 * K) * i, degree, cam, cfg, f);
+    const Splat sp = to_splat(f);
+    if (!sp.valid) continue;
+    double power, err;
+    exponent_and_bound(sp, items[4 * k + 2] - sp.mean2d[0], items[4 * k + 3] - sp.mean2d[1], power,
+                       err);
+    out[2 * k] = std::log(sp.opacity) + power;
+    out[2 * k + 1] = err;
   }
 }
 

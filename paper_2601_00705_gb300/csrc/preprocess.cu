@@ -169,7 +169,7 @@ struct ViewProj {
   float T[6];              // J R, row-major 2x3
   float TS[6];             // T Sigma^W
   float cov[3];            // Sigma^I + eps: xx, xy, yy
-  float conic[3];          // a, b, c
+  float chol[3];           // l11, l21, l22: (log2(e) / 2) (Sigma^I + eps)^-1 = L L^T
   float mean2d[2];         // projected mean, hi parts
   float mean2d_lo[2];      // and lo parts (mean2d + mean2d_lo = fx u + cx, fy w + cy)
 };
@@ -254,10 +254,15 @@ __device__ __forceinline__ bool project_view(const GaussianLocal& g, const ViewP
   const float m12 = diff_of_products(A[1], A[5], A[2], A[4]);
   const float det = m01 * m01 + m02 * m02 + m12 * m12 + c.eps2d * (sxx + syy) + c.eps2d * c.eps2d;
   if (!(det > 0.0f)) return false;
+  // Lower-triangular factor of the base-2-scaled conic k Q (k = log2(e) / 2, Q = the inverse of
+  // Sigma^I + eps I) from the covariance entries and the accurate determinant, with no
+  // subtraction: l11 = sqrt(k Syy / det), l21 = -k Sxy / (det l11), l22 = sqrt(k / Syy); then
+  // l11^2 = k Q_xx, l11 l21 = k Q_xy and l21^2 + l22^2 = k Q_yy.
+  constexpr float k = 0.5f * kLog2e;
   const float idet = 1.0f / det;
-  p.conic[0] = p.cov[2] * idet;
-  p.conic[1] = -p.cov[1] * idet;
-  p.conic[2] = p.cov[0] * idet;
+  p.chol[0] = sqrtf(k * p.cov[2] * idet);
+  p.chol[1] = -k * p.cov[1] * idet / p.chol[0];
+  p.chol[2] = sqrtf(k / p.cov[2]);
   return true;
 }
 
@@ -455,9 +460,7 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
     ViewProj p;
     if (!project_view(g, vp, ps, c, p)) continue;
     const float4 r0 = make_float4(p.mean2d[0], p.mean2d[1], p.mean2d_lo[0], p.mean2d_lo[1]);
-    const float4 r1 =
-        make_float4(__fmul_rn(p.conic[0], -0.5f * kLog2e), __fmul_rn(p.conic[1], -kLog2e),
-                    __fmul_rn(p.conic[2], -0.5f * kLog2e), log2f(g.opacity));
+    const float4 r1 = make_float4(p.chol[0], p.chol[1], p.chol[2], log2f(g.opacity));
     float rgb[3] = {0.0f, 0.0f, 0.0f};
     if constexpr (DEG >= 0) sh_colour<DEG>(shc, g.m, ps, rgb);
     const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], p.mc[2]);
@@ -619,27 +622,28 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
     const float4 ga = *reinterpret_cast<const float4*>(gp);
     const float4 gb = *reinterpret_cast<const float4*>(gp + 4);
     const float2 gc2 = *reinterpret_cast<const float2*>(gp + 8);
-    const float m0 = ga.x, mx = ga.y, mxx = ga.z, my = ga.w;
-    const float mxy = gb.x, myy = gb.y, g_r = gb.z, g_g = gb.w;
+    const float m0 = ga.x, wt = ga.y, ws = ga.z, wtt = ga.w;
+    const float wts = gb.x, wss = gb.y, g_r = gb.z, g_g = gb.w;
     const float g_b = gc2.x, g_zo = gc2.y;
     ViewProj p;
     project_view(g, vp, ps, c, p);
     const float* R = ps.R;
-    const float a = p.conic[0], b = p.conic[1], cc = p.conic[2];
-    // Screen-space gradients from the blend's moments: power = -1/2 (a dx^2 + 2 b dx dy +
-    // c dy^2) with (dx, dy) = p - mu^I, alpha = o exp(power) (Section 3.1, Eq. alpha), so
-    // dpower/dmu^I = (a dx + b dy, b dx + c dy), dpower/d(a, b, c) = -(dx^2 / 2, dx dy, dy^2 / 2)
-    // and d alpha / d o = alpha / o.
-    const float g_mx = fmaf(a, mx, b * my), g_my = fmaf(b, mx, cc * my);
-    const float g_ca = -0.5f * mxx, g_cb = -mxy, g_cc = -0.5f * myy;
+    // Screen-space gradients from the blend's whitened moments (Section 3.1, Eq. alpha):
+    // power = ln o - ln 2 |w|^2 with w = L^T d, d = p - mu^I and L L^T = (log2(e) / 2) Q, so
+    //   dpower/dmu^I = Q d = 2 ln 2 L w,
+    //   dpower/dSigma^I = 1/2 Q d d^T Q = 2 (ln 2)^2 L w w^T L^T,
+    //   dpower/do = 1 / o,
+    // and the sums over the covered pixels of dp = dL/dpower times these are linear in
+    // sum dp w = (wt, ws) and sum dp w w^T = [[wtt, wts], [wts, wss]].
+    const float l11 = p.chol[0], l21 = p.chol[1], l22 = p.chol[2];
+    constexpr float c1 = 2.0f * kLn2, c2 = 2.0f * kLn2 * kLn2;
+    const float g_mx = c1 * (l11 * wt), g_my = c1 * fmaf(l21, wt, l22 * ws);
     const float g_op = m0 / g.opacity;
-    // Conic -> Sigma^I: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]].
-    const float hb = 0.5f * g_cb;
-    const float P00 = a * g_ca + b * hb, P01 = a * hb + b * g_cc;
-    const float P10 = b * g_ca + cc * hb, P11 = b * hb + cc * g_cc;
-    const float GS00 = -(P00 * a + P01 * b);
-    const float GS01 = -(P00 * b + P01 * cc);
-    const float GS11 = -(P10 * b + P11 * cc);
+    // G_S = c2 L W2 L^T with the lower-triangular L.
+    const float r1t = fmaf(l21, wtt, l22 * wts), r1s = fmaf(l21, wts, l22 * wss);
+    const float GS00 = c2 * (l11 * (l11 * wtt));
+    const float GS01 = c2 * (l11 * r1t);
+    const float GS11 = c2 * fmaf(l21, r1t, l22 * r1s);
     // Sigma^I = T Sigma^W T^T: G_T = 2 G_S (T Sigma^W); G_SigmaW = T^T G_S T.
     float GT[6], U[6];
 #pragma unroll

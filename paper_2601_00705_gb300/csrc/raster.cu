@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
         Ellipse eb;
         eb.mx = __shfl_sync(0xffffffffu, e.mx, src);
         eb.my = __shfl_sync(0xffffffffu, e.my, src);
-        eb.sxx = __shfl_sync(0xffffffffu, e.sxx, src);
-        eb.sxy = __shfl_sync(0xffffffffu, e.sxy, src);
-        eb.syy = __shfl_sync(0xffffffffu, e.syy, src);
+        eb.l11 = __shfl_sync(0xffffffffu, e.l11, src);
+        eb.l21 = __shfl_sync(0xffffffffu, e.l21, src);
+        eb.l22 = __shfl_sync(0xffffffffu, e.l22, src);
         eb.kappa = __shfl_sync(0xffffffffu, e.kappa, src);
         const ViewParams& vp = views.v[__shfl_sync(0xffffffffu, v, src)];
         TileCover tc;
@@ -192,27 +192,31 @@ __global__ void store_pair_count_kernel(Counters* counters, uint32_t capacity) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Staging of a batch of Gaussians in shared memory. For an even number of pixels per thread every
-// per-Gaussian operand is stored twice, as (x, x) pairs, so the packed f32x2 arithmetic of two
-// pixels reads its broadcast operands straight from shared memory:
-//   [0] (mx hi, mx hi), (mx lo, mx lo)   [1] (my hi, my hi), (my lo, my lo)
-//   [2] (qa, qa), (qb, qb)               [3] (qc, qc), (log2 o, log2 o)
+// Staging of a batch of Gaussians in shared memory, with the row terms of the tile's anchor row
+// y_a (anchor_terms). For an even number of pixels per thread every per-Gaussian operand is
+// stored twice, as (x, x) pairs, so the packed f32x2 arithmetic of two pixels reads its broadcast
+// operands straight from shared memory:
+//   [0] (mx hi, mx hi), (mx lo, mx lo)   [1] (l11, l11), (c21, c21)
+//   [2] (l21, l21), (l22, l22)           [3] (s_a, s_a), (-log2 o, -log2 o)
 //   [4] (r, r), (g, g)                   [5] (b, b), (z, z)
-// With one pixel per thread rows 0..2 hold rec0, rec1, rec2 as float4.
+// With one pixel per thread rows 0..2 hold (mx hi, mx lo, l11, c21), (l21, l22, s_a, -log2 o)
+// and rec2 as float4.
 // ------------------------------------------------------------------------------------------
 template <int R, int N>
 __device__ __forceinline__ void stage_gaussian(ulonglong2 (&sp)[R][N], int t, float4 r0,
-                                               float4 r1, float4 r2) {
+                                               float4 r1, float4 r2, float y_a) {
+  const AnchorTerms at = anchor_terms(r0, r1, y_a);
+  const float nlo = -r1.w;
   if constexpr (R == 6) {
     sp[0][t] = make_ulonglong2(f2_make(r0.x, r0.x), f2_make(r0.z, r0.z));
-    sp[1][t] = make_ulonglong2(f2_make(r0.y, r0.y), f2_make(r0.w, r0.w));
-    sp[2][t] = make_ulonglong2(f2_make(r1.x, r1.x), f2_make(r1.y, r1.y));
-    sp[3][t] = make_ulonglong2(f2_make(r1.z, r1.z), f2_make(r1.w, r1.w));
+    sp[1][t] = make_ulonglong2(f2_make(r1.x, r1.x), f2_make(at.c21, at.c21));
+    sp[2][t] = make_ulonglong2(f2_make(r1.y, r1.y), f2_make(r1.z, r1.z));
+    sp[3][t] = make_ulonglong2(f2_make(at.s_a, at.s_a), f2_make(nlo, nlo));
     sp[4][t] = make_ulonglong2(f2_make(r2.x, r2.x), f2_make(r2.y, r2.y));
     sp[5][t] = make_ulonglong2(f2_make(r2.z, r2.z), f2_make(r2.w, r2.w));
   } else {
-    reinterpret_cast<float4*>(sp[0])[t] = r0;
-    reinterpret_cast<float4*>(sp[1])[t] = r1;
+    reinterpret_cast<float4*>(sp[0])[t] = make_float4(r0.x, r0.z, r1.x, at.c21);
+    reinterpret_cast<float4*>(sp[1])[t] = make_float4(r1.y, r1.z, at.s_a, nlo);
     reinterpret_cast<float4*>(sp[2])[t] = r2;
   }
 }
@@ -249,10 +253,13 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   const int px = tx * TW + (int)(threadIdx.x % TW);
   const int py0 = ty * TH + (int)(threadIdx.x / TW) * PPT;
   const float fx = (float)px;
+  // Anchor row of the tile's row terms, and the thread's first row relative to it.
+  const float y_a = (float)(ty * TH + TH / 2);
+  const int r0_ = (int)(threadIdx.x / TW) * PPT - TH / 2;
   const uint2 range = ranges[gtile];
 
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
-  f32x2 T2[P2], C02[P2], C12[P2], C22[P2], D2[P2], FY[P2];
+  f32x2 T2[P2], C02[P2], C12[P2], C22[P2], D2[P2], FR[P2];
   int32_t last[PPT];
   uint32_t visited_end[PPT];  // one past the last list position the pixel visited
   bool done[PPT];             // one-pixel path: the pixel has stopped (or is off the image)
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     const int k0 = kPacked ? 2 * q : 0, k1 = kPacked ? 2 * q + 1 : 0;
     T2[q] = f2_make(T[k0], T[k1]);
     C02[q] = C12[q] = C22[q] = D2[q] = f2_make(0.0f, 0.0f);
-    FY[q] = f2_make((float)(py0 + k0), (float)(py0 + k1));
+    FR[q] = f2_make((float)(r0_ + k0), (float)(r0_ + k1));
   }
   const f32x2 FX = f2_make(fx, fx);
   // 0 <= x < t_min for a float x, as one unsigned compare of its bit pattern (t_min > 0).
@@ -286,26 +293,26 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     const uint32_t j = start + threadIdx.x;
     if (j < range.y) {
       const uint32_t vi = pair_vals[j];
-      stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi]);
+      stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi], y_a);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kThreads, range.y - start);
     for (int g = 0; g < cnt && live > 0; ++g) {
       const uint32_t pos = start + g;
       if constexpr (kPacked) {
-        const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
+        const ulonglong2 X = sp[0][g], L1 = sp[1][g], L2 = sp[2][g], L3 = sp[3][g];
         const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
-        // Column terms of Eq. alpha's exponent, computed as (x, x) pairs.
+        // Whitened offset t at the anchor row of the thread's column (Eq. alpha's exponent).
         const f32x2 dx = f2_sub(f2_sub(FX, X.x), X.y);
-        const f32x2 AA = f2_fma(f2_mul(Q1.x, dx), dx, Q2.y);
-        const f32x2 BB = f2_mul(Q1.y, dx);
+        const f32x2 TA = f2_fma(L1.x, dx, L1.y);
 #pragma unroll
         for (int q = 0; q < P2; ++q) {
           const int k0 = 2 * q, k1 = 2 * q + 1;
-          const f32x2 dy = f2_sub(f2_sub(FY[q], Y.x), Y.y);
-          const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
-          const float a0 = fminf(c.alpha_max, ex2_approx(f2_lo(pw)));
-          const float a1 = fminf(c.alpha_max, ex2_approx(f2_hi(pw)));
+          const f32x2 tt = f2_fma(FR[q], L2.x, TA);
+          const f32x2 ss = f2_fma(FR[q], L2.y, L3.x);
+          const f32x2 nq = f2_fma(tt, tt, f2_fma(ss, ss, L3.y));  // -log2(o G)
+          const float a0 = fminf(c.alpha_max, ex2_neg_approx(f2_lo(nq)));
+          const float a1 = fminf(c.alpha_max, ex2_neg_approx(f2_hi(nq)));
           const bool cov0 = a0 >= c.alpha_min, cov1 = a1 >= c.alpha_min;
           // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha):
           // positive while the pixel is live (alpha <= alpha_max < 1), negative once stopped.
@@ -336,13 +343,12 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
         const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
         const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
         const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
-        const ColumnTerms ct =
-            column_terms(__fsub_rn(__fsub_rn(fx, g0.x), g0.z), g1.x, g1.y, g1.w);
+        const float ta = __fmaf_rn(g0.z, __fsub_rn(__fsub_rn(fx, g0.x), g0.y), g0.w);
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (!done[k]) {
-            const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
-            const float a = fminf(c.alpha_max, opacity_times_gauss(ct, g1.z, dy));
+            const float nq = neg_log2_og(ta, g1.z, g1.x, g1.y, g1.w, (float)(r0_ + k));
+            const float a = fminf(c.alpha_max, ex2_neg_approx(nq));
             if (a >= c.alpha_min) {
               const float w = __fmul_rn(a, T[k]);
               const float Tn = __fsub_rn(T[k], w);
@@ -498,6 +504,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   const int px = tx * TW + (int)(threadIdx.x % TW);
   const int py0 = ty * TH + (int)(threadIdx.x / TW) * PPT;
   const float fx = (float)px;
+  // Anchor row of the tile's row terms, and the thread's first row relative to it (as in the
+  // forward, so both blends compute every pixel's exponent to the same bits).
+  const float y_a = (float)(ty * TH + TH / 2);
+  const int r0_ = (int)(threadIdx.x / TW) * PPT - TH / 2;
   const uint2 range = ranges[gtile];
   const int lane = threadIdx.x & 31;
   const int slot = reduced_slot(lane);
@@ -532,7 +542,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     thread_last = max(thread_last, last[k]);
   }
   // The same state as (pixel 2q, pixel 2q + 1) pairs for the packed arithmetic.
-  f32x2 T2[P2], U2[P2], GC02[P2], GC12[P2], GC22[P2], GD2[P2], GAT2[P2], FY[P2];
+  f32x2 T2[P2], U2[P2], GC02[P2], GC12[P2], GC22[P2], GD2[P2], GAT2[P2], FR[P2];
 #pragma unroll
   for (int q = 0; q < P2; ++q) {
     const int k0 = kPacked ? 2 * q : 0, k1 = kPacked ? 2 * q + 1 : 0;
@@ -543,7 +553,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     GC22[q] = f2_make(gC2[k0], gC2[k1]);
     GD2[q] = f2_make(gD[k0], gD[k1]);
     GAT2[q] = f2_make(gAT[k0], gAT[k1]);
-    FY[q] = f2_make((float)(py0 + k0), (float)(py0 + k1));
+    FR[q] = f2_make((float)(r0_ + k0), (float)(r0_ + k1));
   }
   const f32x2 FX = f2_make(fx, fx), ONE2 = f2_make(1.0f, 1.0f), ZERO2 = f2_make(0.0f, 0.0f);
   // Only list positions up to the largest last-contributor index of the tile matter.
@@ -572,24 +582,26 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     for (int s2 = 0; s2 < 10; ++s2) acc[s2] = 0.0f;
     bool contrib = false;
     if (!kCheckLast || jj <= thread_last) {
-      // Per-thread moments of dL/dpower over the thread's pixels (all share dx):
-      // sdp = sum dp, sdy = sum dp dy, sdy2 = sum dp dy^2.
-      float sdp = 0.0f, sdy = 0.0f, sdy2 = 0.0f, dx;
+      // Per-thread sums of dp = dL/dpower over the thread's pixels, weighted by their row offset
+      // r from the anchor row: sdp = sum dp, sr = sum dp r, srr = sum dp r^2. Every pixel of the
+      // column has w = (t, s) = (t_a + r l21, s_a + r l22), so the whitened moments follow
+      // from these three once per Gaussian.
+      float sdp = 0.0f, sr = 0.0f, srr = 0.0f, ta, l21, l22, s_a;
       if constexpr (kPacked) {
-        const ulonglong2 X = sp[0][g], Y = sp[1][g], Q1 = sp[2][g], Q2 = sp[3][g];
+        const ulonglong2 X = sp[0][g], L1 = sp[1][g], L2 = sp[2][g], L3 = sp[3][g];
         const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
         const f32x2 dx2 = f2_sub(f2_sub(FX, X.x), X.y);
-        const f32x2 AA = f2_fma(f2_mul(Q1.x, dx2), dx2, Q2.y);
-        const f32x2 BB = f2_mul(Q1.y, dx2);
+        const f32x2 TA = f2_fma(L1.x, dx2, L1.y);
         f32x2 aR = ZERO2, aG = ZERO2, aB = ZERO2, aZ = ZERO2, mP = ZERO2, mY = ZERO2,
               mYY = ZERO2;
         (void)aZ;
 #pragma unroll
         for (int q = 0; q < P2; ++q) {
           const int k0 = 2 * q, k1 = 2 * q + 1;
-          const f32x2 dy = f2_sub(f2_sub(FY[q], Y.x), Y.y);
-          const f32x2 pw = f2_fma(dy, f2_fma(Q2.x, dy, BB), AA);
-          const float oG0 = ex2_approx(f2_lo(pw)), oG1 = ex2_approx(f2_hi(pw));
+          const f32x2 tt = f2_fma(FR[q], L2.x, TA);
+          const f32x2 ss = f2_fma(FR[q], L2.y, L3.x);
+          const f32x2 nq = f2_fma(tt, tt, f2_fma(ss, ss, L3.y));  // -log2(o G)
+          const float oG0 = ex2_neg_approx(f2_lo(nq)), oG1 = ex2_neg_approx(f2_hi(nq));
           const float a0 = fminf(c.alpha_max, oG0), a1 = fminf(c.alpha_max, oG1);
           const bool cov0 = (!kCheckLast || jj <= last[k0]) && a0 >= c.alpha_min;
           const bool cov1 = (!kCheckLast || jj <= last[k1]) && a1 >= c.alpha_min;
@@ -621,30 +633,34 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           const bool m0 = cov0 && oG0 < c.alpha_max, m1 = cov1 && oG1 < c.alpha_max;
           const f32x2 dp = f2_make(m0 ? f2_lo(dpv) : 0.0f, m1 ? f2_hi(dpv) : 0.0f);
           mP = f2_add(mP, dp);
-          const f32x2 t = f2_mul(dp, dy);
+          const f32x2 t = f2_mul(dp, FR[q]);
           mY = f2_add(mY, t);
-          mYY = f2_fma(t, dy, mYY);
+          mYY = f2_fma(t, FR[q], mYY);
         }
         acc[kGR] = f2_lo(aR) + f2_hi(aR);
         acc[kGG] = f2_lo(aG) + f2_hi(aG);
         acc[kGB] = f2_lo(aB) + f2_hi(aB);
         if constexpr (kAux) acc[kGZ] = f2_lo(aZ) + f2_hi(aZ);
         sdp = f2_lo(mP) + f2_hi(mP);
-        sdy = f2_lo(mY) + f2_hi(mY);
-        sdy2 = f2_lo(mYY) + f2_hi(mYY);
-        dx = f2_lo(dx2);
+        sr = f2_lo(mY) + f2_hi(mY);
+        srr = f2_lo(mYY) + f2_hi(mYY);
+        ta = f2_lo(TA);
+        l21 = f2_lo(L2.x);
+        l22 = f2_lo(L2.y);
+        s_a = f2_lo(L3.x);
       } else {
         const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
         const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
         const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
-        dx = __fsub_rn(__fsub_rn(fx, g0.x), g0.z);
-        const float qc = g1.z;
-        const ColumnTerms ct = column_terms(dx, g1.x, g1.y, g1.w);
+        ta = __fmaf_rn(g0.z, __fsub_rn(__fsub_rn(fx, g0.x), g0.y), g0.w);
+        l21 = g1.x;
+        l22 = g1.y;
+        s_a = g1.z;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (kCheckLast && jj > last[k]) continue;
-          const float dy = __fsub_rn(__fsub_rn((float)(py0 + k), g0.y), g0.w);
-          const float oG = opacity_times_gauss(ct, qc, dy);
+          const float fr = (float)(r0_ + k);
+          const float oG = ex2_neg_approx(neg_log2_og(ta, s_a, l21, l22, g1.w, fr));
           const float a = fminf(c.alpha_max, oG);
           if (a < c.alpha_min) continue;
           contrib = true;
@@ -667,20 +683,24 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           if (oG < c.alpha_max) {
             const float dp = dLda * a;  // dL/dpower: d alpha / d power = o G = alpha
             sdp += dp;
-            const float t = dp * dy;
-            sdy += t;
-            sdy2 = fmaf(t, dy, sdy2);
+            const float t = dp * fr;
+            sr += t;
+            srr = fmaf(t, fr, srr);
           }
         }
       }
-      // The thread's share of the moments (all its pixels have the same dx); zero when it
+      // The thread's share of the whitened moments: with w_a = (t_a, s_a) at the anchor row and
+      // e = (l21, l22), sum dp w = sdp w_a + sr e and
+      // sum dp w w^T = sdp w_a w_a^T + sr (w_a e^T + e w_a^T) + srr e e^T; zero when the thread
       // covers nothing.
+      const float m1t = fmaf(l21, sr, ta * sdp), m1s = fmaf(l22, sr, s_a * sdp);
+      const float xt = fmaf(l21, srr, ta * sr), xs = fmaf(l22, srr, s_a * sr);
       acc[kM0] = sdp;
-      acc[kMx] = dx * sdp;
-      acc[kMxx] = dx * acc[kMx];
-      acc[kMy] = sdy;
-      acc[kMxy] = dx * sdy;
-      acc[kMyy] = sdy2;
+      acc[kWt] = m1t;
+      acc[kWs] = m1s;
+      acc[kWtt] = fmaf(l21, xt, ta * m1t);
+      acc[kWts] = fmaf(l22, xt, s_a * m1t);
+      acc[kWss] = fmaf(l22, xs, s_a * m1s);
     }
     if (__any_sync(0xffffffffu, contrib)) {
       const float total = transpose_reduce10(acc, lane);
@@ -697,7 +717,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     if (j < bend) {
       const uint32_t vi = pair_vals[j];
       s_vi[threadIdx.x] = vi;
-      stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi]);
+      stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi], y_a);
     }
     __syncthreads();
     // Positions above the warp's smallest last index test each pixel; the rest do not.

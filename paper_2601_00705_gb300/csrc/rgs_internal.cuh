@@ -4,7 +4,8 @@
 //   rec0[vi] = (mean2d.x hi, mean2d.y hi, mean2d.x lo, mean2d.y lo)   float4, the projected
 //              mean as an unevaluated double-float sum, so that p - mu^I is accurate to ~1e-7 px
 //              even at 1080p coordinates
-//   rec1[vi] = (qa, qb, qc, log2 o)                        float4, base-2 conic (see below)
+//   rec1[vi] = (l11, l21, l22, log2 o)                    float4, lower-triangular factor of the
+//              base-2-scaled conic (see below)
 //   rec2[vi] = (r, g, b, depth z)                          float4
 //   ntiles[vi]: tiles touched (0 = culled / invisible)
 //   g2d[vi * 16 + s]: the backward blend's sums over the covered pixels of dL/dpower moments
@@ -25,12 +26,16 @@ constexpr int kMaxViews = RGS_MAX_VIEWS;
 constexpr int kG2Stride = 16;  // floats per (view, Gaussian) gradient record (64 bytes)
 
 // Slots the backward blend accumulates per (view, Gaussian), with dp = dL/dpower of a covered,
-// unclamped pixel and (dx, dy) = p - mu^I:
-//   kM0 = sum dp, kMx = sum dp dx, kMxx = sum dp dx^2, kMy = sum dp dy, kMxy = sum dp dx dy,
-//   kMyy = sum dp dy^2; kGR/kGG/kGB/kGZ = dL/d(colour, depth) = sum dL/dC alpha T.
-// The screen-space gradients are linear in the moments (the conic and opacity are constant per
-// (view, Gaussian)), so the backward preprocess forms them once per record.
-enum G2Slot { kM0 = 0, kMx, kMxx, kMy, kMxy, kMyy, kGR, kGG, kGB, kGZ };
+// unclamped pixel and (t, s) = L^T (p - mu^I) the pixel's whitened offset (see the coverage
+// helpers below):
+//   kM0 = sum dp, kWt = sum dp t, kWs = sum dp s, kWtt = sum dp t^2, kWts = sum dp t s,
+//   kWss = sum dp s^2; kGR/kGG/kGB/kGZ = dL/d(colour, depth) = sum dL/dC alpha T.
+// The screen-space gradients are linear in these sums (L and the opacity are constant per
+// (view, Gaussian)), so the backward preprocess forms them once per record. Whitened moments
+// stay well conditioned where moments of p - mu^I do not: for a thin footprint whose centre lies
+// thousands of pixels off the image, sum dp (p - mu)(p - mu)^T is dominated by the long axis and
+// the thin-axis part that the covariance gradient needs is lost to FP32 accumulation.
+enum G2Slot { kM0 = 0, kWt, kWs, kWtt, kWts, kWss, kGR, kGG, kGB, kGZ };
 
 struct ViewParams {
   int width, height;
@@ -218,20 +223,41 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // Coverage of a pixel by a projected Gaussian, alpha = min(alpha_max, o G), with
-// G = exp(-1/2 d^T Q d) and d = p - mu^I. The record stores the conic scaled to base 2,
-// (qa, qb, qc) = -log2(e) (a/2, b, c/2), and lo = log2(o), so that
-//   log2(o G) = (qa dx^2 + lo) + dy (qb dx + qc dy).
-// A thread evaluates one Gaussian for several pixels of one column (same dx): the first bracket
-// and qb dx are computed once, each pixel then costs two FMAs and one ex2. Every operation is
-// explicitly rounded, so the forward and backward blends take identical coverage decisions.
-struct ColumnTerms {
-  float A, B;
+// G = exp(-1/2 d^T Q d) and d = p - mu^I (Section 3.1, Eq. alpha). The record stores the lower
+// triangular factor L of the base-2-scaled conic, (log2(e) / 2) Q = L L^T, and lo = log2(o), so
+//   log2(o G) = lo - (t^2 + s^2),  (t, s) = L^T d = (l11 dx + l21 dy, l22 dy).
+// The whitened offsets t and s are O(1) wherever the Gaussian is visible, so the exponent keeps
+// its accuracy for thin footprints far from their centre, where the expanded quadratic form
+// a dx^2 + 2 b dx dy + c dy^2 cancels terms of 10^4 and more.
+// A blend CTA evaluates its tile's pixels against one staged Gaussian: the row terms at the
+// tile's anchor row y_a (its middle row), c21 = l21 (y_a - mu_y) and s_a = l22 (y_a - mu_y), are
+// computed once per (Gaussian, tile); a thread then forms t_a = l11 dx + c21 once for its column,
+// and each pixel at row offset r = y - y_a costs t = t_a + r l21, s = s_a + r l22 and two FMAs
+// for t^2 + s^2 - lo. Every operation is explicitly rounded and a pixel's value depends only on
+// its tile row, so both blends take identical coverage decisions whatever their pixels per
+// thread.
+struct AnchorTerms {
+  float c21, s_a;
 };
-__device__ __forceinline__ ColumnTerms column_terms(float dx, float qa, float qb, float lo) {
-  return ColumnTerms{__fmaf_rn(__fmul_rn(qa, dx), dx, lo), __fmul_rn(qb, dx)};
+__device__ __forceinline__ AnchorTerms anchor_terms(float4 r0, float4 r1, float y_a) {
+  const float dya = __fsub_rn(__fsub_rn(y_a, r0.y), r0.w);
+  return AnchorTerms{__fmul_rn(r1.y, dya), __fmul_rn(r1.z, dya)};
 }
-__device__ __forceinline__ float opacity_times_gauss(const ColumnTerms& t, float qc, float dy) {
-  return ex2_approx(__fmaf_rn(dy, __fmaf_rn(qc, dy, t.B), t.A));
+// t at the anchor row of column px.
+__device__ __forceinline__ float column_t(float px, float4 r0, float l11, float c21) {
+  return __fmaf_rn(l11, __fsub_rn(__fsub_rn(px, r0.x), r0.z), c21);
+}
+// t^2 + s^2 - log2(o) = -log2(o G) at row offset r.
+__device__ __forceinline__ float neg_log2_og(float t_a, float s_a, float l21, float l22,
+                                             float neg_lo, float r) {
+  const float t = __fmaf_rn(r, l21, t_a), s = __fmaf_rn(r, l22, s_a);
+  return __fmaf_rn(t, t, __fmaf_rn(s, s, neg_lo));
+}
+// 2^(-x): o G from neg_log2_og.
+__device__ __forceinline__ float ex2_neg_approx(float x) {
+  float y;
+  asm("{\n\t.reg .f32 n;\n\tneg.f32 n, %1;\n\tex2.approx.ftz.f32 %0, n;\n\t}" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Packed FP32 pairs (PTX .f32x2 on the sm_100 family): one instruction performs the same IEEE
@@ -275,17 +301,16 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
   return r;
 }
 
-// Natural-log conic (a, b, c) from the stored base-2 form.
 constexpr float kLn2 = 0.69314718055994531f;
 constexpr float kLog2e = 1.4426950408889634f;
 
 // ------------------------------------------------------------------------------------------
 // Tile coverage of a projected Gaussian: the tiles whose pixel centres may lie inside the
-// alpha >= alpha_min ellipse {d : d^T Q d <= kappa} (Q = conic), padded by kTilePad pixels so
-// that the per-pixel FP32 test in the blend can never find a covered pixel outside the listed
-// tiles. The two tests differ only by rounding: a few ulps relative to the footprint's extent
-// (the blend adds the low part of the mean, below 1e-4 px; the extent here comes from
-// approximate reciprocals and square roots), and kappa is already widened by 1e-4 relative
+// alpha >= alpha_min ellipse {d : |L^T d|^2 <= kappa}, kappa = log2 o - log2 alpha_min, padded by
+// kTilePad pixels so that the per-pixel FP32 test in the blend can never find a covered pixel
+// outside the listed tiles. The two tests differ only by rounding: a few ulps relative to the
+// footprint's extent (the blend adds the low part of the mean, below 1e-4 px; the extent here
+// comes from approximate reciprocals and square roots), and kappa is widened by 1e-4 relative
 // below, so a sixteenth of a pixel is a wide margin. Each listed tile without a covered pixel
 // costs a full pass over the tile in both blends. Visits tile rows ty0..ty1 and, per row, the
 // column span [tx0, tx1] of the ellipse restricted to the row's pixel band.
@@ -294,25 +319,20 @@ constexpr float kTilePad = 0.0625f;
 
 struct Ellipse {
   float mx, my;           // centre
-  float sxx, sxy, syy;    // covariance Q^-1
+  float l11, l21, l22;    // factor of the scaled conic (the record's rec1.xyz)
   float kappa;
 };
 
-// From the stored records (rec0.xy = mean hi parts, rec1 = base-2 conic and log2 o), with
-// kappa = 2 ln(o / alpha_min) = 2 ln 2 (log2 o - log2 alpha_min).
+// From the stored records (rec0.xy = mean hi parts, rec1 = factor and log2 o).
 __device__ __forceinline__ bool make_ellipse(float4 r0, float4 r1, float log2_alpha_min,
                                              Ellipse& e) {
-  const float a = __fmul_rn(r1.x, -2.0f * kLn2), b = __fmul_rn(r1.y, -kLn2),
-              c = __fmul_rn(r1.z, -2.0f * kLn2);
-  const float detq = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
-  const float kappa = __fmul_rn(2.0f * kLn2, __fsub_rn(r1.w, log2_alpha_min));
-  if (!(detq > 0.0f) || !(kappa >= 0.0f)) return false;
+  const float kappa = __fsub_rn(r1.w, log2_alpha_min);
+  if (!(r1.x > 0.0f) || !(r1.z > 0.0f) || !(kappa >= 0.0f)) return false;
   e.mx = r0.x;
   e.my = r0.y;
-  const float inv = __fdividef(1.0f, detq);
-  e.sxx = __fmul_rn(c, inv);
-  e.sxy = __fmul_rn(-b, inv);
-  e.syy = __fmul_rn(a, inv);
+  e.l11 = r1.x;
+  e.l21 = r1.y;
+  e.l22 = r1.z;
   e.kappa = kappa;
   return true;
 }
@@ -345,8 +365,15 @@ struct TileCover {
     mx = e.mx;
     my = e.my;
     kap = __fadd_rn(__fmul_rn(e.kappa, 1.0001f), 1e-6f);
-    rx = sqrt_fixed(__fmul_rn(kap, e.sxx));
-    ry = sqrt_fixed(__fmul_rn(kap, e.syy));
+    // With (t, s) = L^T d: |s| <= sqrt(kap) bounds dy by sqrt(kap) / l22; for a given dy,
+    // |t| <= sqrt(kap - s^2) gives dx in -l21 / l11 dy +- sqrt(kap - (l22 dy)^2) / l11, whose
+    // extremes lie at dy* = -+ rx l11 l21 / (l21^2 + l22^2) with half-width
+    // rx = sqrt(kap (1 + (l21 / l22)^2)) / l11.
+    const float sk = sqrt_fixed(kap);
+    const float il11 = __fdiv_rn(1.0f, e.l11), il22 = __fdiv_rn(1.0f, e.l22);
+    const float r = __fmul_rn(e.l21, il22);
+    rx = __fmul_rn(__fmul_rn(sk, sqrt_fixed(__fmaf_rn(r, r, 1.0f))), il11);
+    ry = __fmul_rn(sk, il22);
     inv_tw = 1.0f / (float)tw;  // powers of two
     const float inv_th = 1.0f / (float)th;
     const float y_lo = __fsub_rn(__fsub_rn(e.my, ry), kTilePad);
@@ -364,11 +391,13 @@ struct TileCover {
     bx1 = min(tiles_x - 1, (int)ftx1);
     if (ty0 > ty1 || bx0 > bx1) return false;
     box_only = ty0 == ty1 || bx0 == bx1;
-    // x | y of the ellipse: centre mx + s dy, half-width h sqrt(kap - dy^2 / syy).
-    inv_syy = __fdividef(1.0f, e.syy);
-    s = __fmul_rn(e.sxy, inv_syy);
-    h = sqrt_fixed(__fsub_rn(e.sxx, __fmul_rn(e.sxy, s)));
-    dy_star = __fmul_rn(__fmul_rn(e.sxy, rx), __fdividef(1.0f, e.sxx));  // rightmost point
+    // x | y of the ellipse: centre mx + s dy, half-width h sqrt(kap - dy^2 / syy), with
+    // s = -l21 / l11, h = 1 / l11, 1 / syy = l22^2.
+    inv_syy = __fmul_rn(e.l22, e.l22);
+    s = __fmul_rn(-e.l21, il11);
+    h = il11;
+    dy_star = __fmul_rn(rx, __fdiv_rn(-__fmul_rn(e.l11, e.l21),
+                                      __fmaf_rn(e.l21, e.l21, __fmul_rn(e.l22, e.l22))));
     return true;
   }
 

@@ -7,8 +7,6 @@
 // serves them: it runs the same three scan kernels, and the only scratch it needs (one partial
 // sum per 4096-element block) lives in `g_scan_block_sums` below, which every GPU that loads the
 // library holds (64 KiB) until the process exits.
-#include <mutex>
-
 #include "rgs_internal.cuh"
 
 namespace {
@@ -21,25 +19,15 @@ constexpr int64_t kStaticScanBlocks = (kStaticScanMax + rgs::kScanTile - 1) / rg
 // cleared between calls.
 static __device__ __align__(256) uint32_t g_scan_block_sums[kStaticScanBlocks + 1];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-uint32_t* g_device_ptr[kMaxDevices] = {};  // device address of g_scan_block_sums, per device
-
-// Device address of the scratch array on the current device, looked up once per device. In host
-// code `g_scan_block_sums` names a host-side stand-in, never the device memory itself.
+// Device address of the scratch array in the current context. In host code `g_scan_block_sums`
+// names a host-side stand-in, never the device memory itself. The lookup is repeated on every
+// call (it is a cheap table lookup once the module is loaded), so a reset device or another
+// current context never sees a stale address.
 cudaError_t scratch_on_current_device(uint32_t** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scan_block_sums);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_device_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scan_block_sums);
-    if (e != cudaSuccess) return e;
-    g_device_ptr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_device_ptr[dev];
+  *out = static_cast<uint32_t*>(p);
   return cudaSuccess;
 }
 

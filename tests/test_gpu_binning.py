@@ -112,9 +112,9 @@ def _uncovered_pixels(name, sample=None, eps=1e-4, seed=0):
         W, H = int(wl.cameras[v]["width"]), int(wl.cameras[v]["height"])
         r0 = rec[e].astype(np.float64)
         mx, my = r0[0] + r0[2], r0[1] + r0[3]
-        qa, qb, qc, l2o = r0[4], r0[5], r0[6], r0[7]
-        # Pixels with A dx^2 + B dx dy + C dy^2 <= k (A = -qa, B = -qb, C = -qc).
-        A, B, C, k = -qa, -qb, -qc, l2o - (log2_amin - eps)
+        l11, l21, l22, l2o = r0[4], r0[5], r0[6], r0[7]
+        # Pixels with (l11 dx + l21 dy)^2 + (l22 dy)^2 <= k, i.e. A dx^2 + B dx dy + C dy^2 <= k.
+        A, B, C, k = l11 * l11, 2.0 * l11 * l21, l21 * l21 + l22 * l22, l2o - (log2_amin - eps)
         det = 4.0 * A * C - B * B
         if k < 0 or not (A > 0 and det > 0):
             continue

@@ -95,6 +95,21 @@ def test_tiny_forward_and_all_gradients():
     print("tiny", info, errs, gpu["stats"])
 
 
+def _assert_same_forward(out, ref, orc, same_tile_shape):
+    """Per-pixel compositing does not depend on the binning. Within one tile shape every pixel's
+    exponent is formed from the same tile anchor row whatever the pixels per thread, so the
+    forward is bit-identical; another tile shape rounds the whitened offsets from another anchor
+    row, which moves values by float32 rounding only (decisions the oracle flags as within that
+    rounding of their threshold may go either way there)."""
+    if same_tile_shape:
+        for k in ("color", "depth", "alpha"):
+            np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
+        return
+    ok = (orc["ambiguous"] & oracle.FORWARD_AMBIGUOUS) == 0
+    for k in ("color", "depth", "alpha"):
+        np.testing.assert_allclose(out[k][ok], ref[k][ok], rtol=0, atol=1e-5, err_msg=k)
+
+
 @pytest.mark.parametrize("tile", [(16, 16, 1), (16, 16, 2), (16, 16, 8), (8, 8, 1), (8, 8, 2),
                                   (32, 8, 1), (32, 8, 2), (32, 8, 4), (32, 8, 8),
                                   (16, 16, 8, 2), (16, 16, 1, 8), (32, 8, 2, 8), (8, 8, 2, 1)])
@@ -106,9 +121,7 @@ def test_tile_shape_and_pixels_per_thread_do_not_change_results(tile):
     out = gpu_render(g, wl.cameras, d_color=d_color, tile_w=tile[0], tile_h=tile[1],
                      pixels_per_thread=tile[2],
                      backward_pixels_per_thread=tile[3] if len(tile) > 3 else 0)
-    # Per-pixel compositing does not depend on the binning: the forward is bit-identical.
-    for k in ("color", "depth", "alpha"):
-        np.testing.assert_array_equal(out[k], ref[k], err_msg=k)
+    _assert_same_forward(out, ref, orc0, same_tile_shape=tile[:2] == (16, 16))
     for k in ("g_means", "g_log_scales", "g_quats", "g_opacity_logits", "g_sh", "g_pose"):
         np.testing.assert_allclose(out[k], ref[k], rtol=1e-4, atol=1e-6 * np.abs(ref[k]).max(),
                                    err_msg=k)
@@ -206,5 +219,5 @@ def test_autotuner_choice_is_valid_cached_and_leaves_results_unchanged():
                        pixels_per_thread=first["pixels_per_thread"],
                        backward_pixels_per_thread=first["backward_pixels_per_thread"])
     ref = gpu_render(g, wl.cameras)
-    for k in ("color", "depth", "alpha"):
-        np.testing.assert_array_equal(tuned[k], ref[k], err_msg=k)
+    _assert_same_forward(tuned, ref, oracle.render(g, wl.cameras),
+                         same_tile_shape=(first["tile_w"], first["tile_h"]) == (16, 16))
