@@ -828,7 +828,7 @@ def run_ours(args, world, rank, local):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     fp32_peak = 2.0 * 128 * props.multi_processor_count * sm_max * 1e6 / 1e12  # TFLOP/s
-    n_eval, n_contrib = stats["n_eval"], stats["n_contrib"]
+    n_eval = stats["n_eval"]
     work = {
         "blend_forward": FWD_FLOP_PER_EVAL * n_eval,
         "blend_backward": BWD_FLOP_PER_EVAL * n_eval,
@@ -887,7 +887,7 @@ def run_ours(args, world, rank, local):
                                 "speedup": loop_ms_per_step / ms_per_step},
         "phases_ms": phases,
         "counts": {"visible": stats["n_visible"], "pairs": stats["n_pairs"],
-                   "evaluated": n_eval, "composited": n_contrib},
+                   "evaluated": n_eval},
     }
     line["tracking"] = measure_tracking(r, params, wl.cameras, images,
                                         float(peaks.get("hbm_gbs", 6800.0)), args.steps, flush)

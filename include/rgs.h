@@ -144,7 +144,7 @@ typedef struct {
   int64_t n_pairs;         /* duplicated (view, tile, Gaussian) entries (of the visible entries
                               kept, when status bit 2 is set) */
   int64_t n_eval;          /* (pixel, Gaussian) list positions visited by the forward blend */
-  int64_t n_contrib;       /* of those, the ones composited (covering, before the stop) */
+  int64_t n_contrib;       /* reserved: 0 (the forward blend counts visited positions only) */
   int64_t n_nonfinite;     /* (view, Gaussian) culled for non-finite inputs (with an SH event,
                               non-finite SH coefficients are found, and counted, for the entries
                               that reach the tile lists) */

@@ -230,6 +230,9 @@ __device__ __forceinline__ void stage_gaussian(ulonglong2 (&sp)[R][N], int t, fl
 // result equals the one-pixel-per-thread kernel's. A pixel that has stopped (its transmittance
 // would fall below t_min) keeps its transmittance negated: -T, so that every later Gaussian
 // fails the composite test without a per-pixel flag, and only the rare stop itself branches.
+// For the backward each pixel saves the last list position it may composite: the one before its
+// stop, or the tile's last position if it never stops (between its last contributor and that
+// position no Gaussian covers it, so the backward takes the same decisions there).
 // ------------------------------------------------------------------------------------------
 template <int TW, int TH, int PPT>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   constexpr int P2 = kPacked ? PPT / 2 : 1;
   static_assert(kThreads % 32 == 0, "whole warps only");
   __shared__ ulonglong2 sp[kPacked ? 6 : 3][kThreads];
-  __shared__ unsigned long long s_eval[kThreads / 32], s_contrib[kThreads / 32];
+  __shared__ unsigned long long s_eval[kThreads / 32];
   const int gtile = blockIdx.x;
   const int v = view_of_tile(views, gtile);
   const ViewParams& vp = views.v[v];
@@ -260,7 +263,6 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
 
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
   f32x2 T2[P2], C02[P2], C12[P2], C22[P2], D2[P2], FR[P2];
-  int32_t last[PPT];
   uint32_t visited_end[PPT];  // one past the last list position the pixel visited
   bool done[PPT];             // one-pixel path: the pixel has stopped (or is off the image)
   int live = 0;               // pixels of the thread that have not stopped
@@ -269,7 +271,6 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     done[k] = !(px < vp.width && py0 + k < vp.height);
     T[k] = done[k] ? -1.0f : 1.0f;
     C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
-    last[k] = -1;
     visited_end[k] = done[k] ? range.x : range.y;
     live += done[k] ? 0 : 1;
   }
@@ -283,11 +284,52 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   const f32x2 FX = f2_make(fx, fx);
   // 0 <= x < t_min for a float x, as one unsigned compare of its bit pattern (t_min > 0).
   const uint32_t t_min_bits = __float_as_uint(c.t_min);
-  uint32_t contribs = 0;
-  // Packed path: Gaussians composited by the thread's even / odd pixels, counted in floats. The
-  // sums are exact: a pixel composites at most ln(t_min) / ln(1 - alpha_min) ~ 2.3e3 Gaussians
-  // before it stops, so they stay far below 2^24.
-  f32x2 cnt2 = f2_make(0.0f, 0.0f);
+
+  // One staged Gaussian (list position pos, slot g) against the thread's pixel pairs; kClamp:
+  // the Gaussian may reach alpha_max somewhere, so alpha is clamped.
+  auto composite_pairs = [&](uint32_t pos, int g, auto clamp_tag) {
+    constexpr bool kClamp = decltype(clamp_tag)::value;
+    const ulonglong2 X = sp[0][g], L1 = sp[1][g], L2 = sp[2][g], L3 = sp[3][g];
+    const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
+    // Whitened offset t at the anchor row of the thread's column (Eq. alpha's exponent).
+    const f32x2 dx = f2_sub(f2_sub(FX, X.x), X.y);
+    const f32x2 TA = f2_fma(L1.x, dx, L1.y);
+#pragma unroll
+    for (int q = 0; q < P2; ++q) {
+      const int k0 = 2 * q, k1 = 2 * q + 1;
+      const f32x2 tt = f2_fma(FR[q], L2.x, TA);
+      const f32x2 ss = f2_fma(FR[q], L2.y, L3.x);
+      const f32x2 nq = f2_fma(tt, tt, f2_fma(ss, ss, L3.y));  // -log2(o G)
+      float a0 = ex2_neg_approx(f2_lo(nq)), a1 = ex2_neg_approx(f2_hi(nq));
+      if constexpr (kClamp) {
+        a0 = fminf(c.alpha_max, a0);
+        a1 = fminf(c.alpha_max, a1);
+      }
+      const bool cov0 = a0 >= c.alpha_min, cov1 = a1 >= c.alpha_min;
+      // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha):
+      // positive while the pixel is live (alpha <= alpha_max < 1), negative once stopped.
+      const f32x2 w = f2_mul(f2_make(a0, a1), T2[q]);
+      const f32x2 Tn = f2_sub(T2[q], w);
+      const float tn0 = f2_lo(Tn), tn1 = f2_hi(Tn);
+      const bool take0 = cov0 && !(tn0 < c.t_min), take1 = cov1 && !(tn1 < c.t_min);
+      const bool stop0 = cov0 && __float_as_uint(tn0) < t_min_bits;
+      const bool stop1 = cov1 && __float_as_uint(tn1) < t_min_bits;
+      const f32x2 wm = f2_make(take0 ? f2_lo(w) : 0.0f, take1 ? f2_hi(w) : 0.0f);
+      C02[q] = f2_fma(wm, CA.x, C02[q]);
+      C12[q] = f2_fma(wm, CA.y, C12[q]);
+      C22[q] = f2_fma(wm, CB.x, C22[q]);
+      D2[q] = f2_fma(wm, CB.y, D2[q]);
+      T2[q] = f2_sub(T2[q], wm);
+      if (stop0 || stop1) {  // once per pixel: keep -T from here on
+        const float t0 = f2_lo(T2[q]), t1 = f2_hi(T2[q]);
+        T2[q] = f2_make(stop0 ? -t0 : t0, stop1 ? -t1 : t1);
+        if (stop0) visited_end[k0] = pos + 1;
+        if (stop1) visited_end[k1] = pos + 1;
+        live -= (int)stop0 + (int)stop1;
+      }
+    }
+  };
+
   for (uint32_t start = range.x; start < range.y; start += kThreads) {
     if (__syncthreads_count(live == 0) == kThreads) break;
     const uint32_t j = start + threadIdx.x;
@@ -300,45 +342,11 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     for (int g = 0; g < cnt && live > 0; ++g) {
       const uint32_t pos = start + g;
       if constexpr (kPacked) {
-        const ulonglong2 X = sp[0][g], L1 = sp[1][g], L2 = sp[2][g], L3 = sp[3][g];
-        const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
-        // Whitened offset t at the anchor row of the thread's column (Eq. alpha's exponent).
-        const f32x2 dx = f2_sub(f2_sub(FX, X.x), X.y);
-        const f32x2 TA = f2_fma(L1.x, dx, L1.y);
-#pragma unroll
-        for (int q = 0; q < P2; ++q) {
-          const int k0 = 2 * q, k1 = 2 * q + 1;
-          const f32x2 tt = f2_fma(FR[q], L2.x, TA);
-          const f32x2 ss = f2_fma(FR[q], L2.y, L3.x);
-          const f32x2 nq = f2_fma(tt, tt, f2_fma(ss, ss, L3.y));  // -log2(o G)
-          const float a0 = fminf(c.alpha_max, ex2_neg_approx(f2_lo(nq)));
-          const float a1 = fminf(c.alpha_max, ex2_neg_approx(f2_hi(nq)));
-          const bool cov0 = a0 >= c.alpha_min, cov1 = a1 >= c.alpha_min;
-          // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha):
-          // positive while the pixel is live (alpha <= alpha_max < 1), negative once stopped.
-          const f32x2 w = f2_mul(f2_make(a0, a1), T2[q]);
-          const f32x2 Tn = f2_sub(T2[q], w);
-          const float tn0 = f2_lo(Tn), tn1 = f2_hi(Tn);
-          const bool take0 = cov0 && !(tn0 < c.t_min), take1 = cov1 && !(tn1 < c.t_min);
-          const bool stop0 = cov0 && __float_as_uint(tn0) < t_min_bits;
-          const bool stop1 = cov1 && __float_as_uint(tn1) < t_min_bits;
-          const f32x2 wm = f2_make(take0 ? f2_lo(w) : 0.0f, take1 ? f2_hi(w) : 0.0f);
-          C02[q] = f2_fma(wm, CA.x, C02[q]);
-          C12[q] = f2_fma(wm, CA.y, C12[q]);
-          C22[q] = f2_fma(wm, CB.x, C22[q]);
-          D2[q] = f2_fma(wm, CB.y, D2[q]);
-          T2[q] = f2_sub(T2[q], wm);
-          if (take0) last[k0] = (int32_t)pos;
-          if (take1) last[k1] = (int32_t)pos;
-          cnt2 = f2_add(cnt2, f2_make(take0 ? 1.0f : 0.0f, take1 ? 1.0f : 0.0f));
-          if (stop0 || stop1) {  // once per pixel: keep -T from here on
-            const float t0 = f2_lo(T2[q]), t1 = f2_hi(T2[q]);
-            T2[q] = f2_make(stop0 ? -t0 : t0, stop1 ? -t1 : t1);
-            if (stop0) visited_end[k0] = pos + 1;
-            if (stop1) visited_end[k1] = pos + 1;
-            live -= (int)stop0 + (int)stop1;
-          }
-        }
+        // Warp-uniform: every thread reads the same staged opacity.
+        if (f2_lo(sp[3][g].y) > c.unclamped_neg_lo)
+          composite_pairs(pos, g, std::false_type{});
+        else
+          composite_pairs(pos, g, std::true_type{});
       } else {
         const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
         const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
@@ -362,8 +370,6 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
                 C2[k] = fmaf(w, g2.z, C2[k]);
                 D[k] = fmaf(w, g2.w, D[k]);
                 T[k] = Tn;
-                ++contribs;
-                last[k] = (int32_t)pos;
               }
             }
           }
@@ -371,10 +377,12 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       }
     }
   }
+  bool stopped[PPT];
   if constexpr (kPacked) {
-    contribs = (uint32_t)f2_lo(cnt2) + (uint32_t)f2_hi(cnt2);
 #pragma unroll
     for (int q = 0; q < P2; ++q) {
+      stopped[2 * q] = f2_lo(T2[q]) < 0.0f;
+      stopped[2 * q + 1] = f2_hi(T2[q]) < 0.0f;
       T[2 * q] = fabsf(f2_lo(T2[q]));
       T[2 * q + 1] = fabsf(f2_hi(T2[q]));
       C0[2 * q] = f2_lo(C02[q]);
@@ -386,6 +394,9 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       D[2 * q] = f2_lo(D2[q]);
       D[2 * q + 1] = f2_hi(D2[q]);
     }
+  } else {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) stopped[k] = done[k];
   }
   uint32_t evals = 0;
 #pragma unroll
@@ -400,30 +411,21 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       depth[pix] = D[k];
       alpha_out[pix] = 1.0f - T[k];
       t_final[pix] = T[k];
-      last_index[pix] = last[k];
+      // The last position the pixel may composite (stop position - 1, or the tile's last).
+      last_index[pix] = stopped[k] ? (int32_t)visited_end[k] - 2 : (int32_t)range.y - 1;
     }
   }
-  // Visited and composited (pixel, Gaussian) positions, for the roofline accounting.
-  unsigned long long e = evals, n_c = contribs;
+  // Visited (pixel, Gaussian) positions, for the roofline accounting.
+  unsigned long long e = evals;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    n_c += __shfl_xor_sync(0xffffffffu, n_c, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_eval[threadIdx.x >> 5] = e;
-    s_contrib[threadIdx.x >> 5] = n_c;
-  }
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) s_eval[threadIdx.x >> 5] = e;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long s = 0, sc = 0;
+    unsigned long long s = 0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-      s += s_eval[w];
-      sc += s_contrib[w];
-    }
+    for (int w = 0; w < kThreads / 32; ++w) s += s_eval[w];
     atomicAdd(&counters->n_eval, s);
-    atomicAdd(&counters->n_contrib, sc);
   }
 }
 
@@ -575,8 +577,11 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
 
   // One Gaussian (list position jj, staged at g) against the thread's pixels; kCheckLast tests
   // each pixel's last-contributor index.
-  auto visit = [&](int jj, int g, auto check_last) {
+  // kClamp: the Gaussian may reach alpha_max somewhere (clamp, and no gradient through a
+  // clamped alpha); without it neither can happen and both tests drop out.
+  auto visit = [&](int jj, int g, auto check_last, auto clamp_tag) {
     constexpr bool kCheckLast = decltype(check_last)::value;
+    constexpr bool kClamp = decltype(clamp_tag)::value;
     float acc[10];
 #pragma unroll
     for (int s2 = 0; s2 < 10; ++s2) acc[s2] = 0.0f;
@@ -602,7 +607,8 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           const f32x2 ss = f2_fma(FR[q], L2.y, L3.x);
           const f32x2 nq = f2_fma(tt, tt, f2_fma(ss, ss, L3.y));  // -log2(o G)
           const float oG0 = ex2_neg_approx(f2_lo(nq)), oG1 = ex2_neg_approx(f2_hi(nq));
-          const float a0 = fminf(c.alpha_max, oG0), a1 = fminf(c.alpha_max, oG1);
+          const float a0 = kClamp ? fminf(c.alpha_max, oG0) : oG0;
+          const float a1 = kClamp ? fminf(c.alpha_max, oG1) : oG1;
           const bool cov0 = (!kCheckLast || jj <= last[k0]) && a0 >= c.alpha_min;
           const bool cov1 = (!kCheckLast || jj <= last[k1]) && a1 >= c.alpha_min;
           contrib = contrib || cov0 || cov1;
@@ -628,10 +634,13 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
             dLda = f2_fma(T2[q], qv, f2_mul(rom, f2_sub(ZERO2, U2[q])));
           }
           U2[q] = f2_fma(w, qv, U2[q]);
-          // dL/dpower = dL/dalpha * alpha (d alpha / d power = o G = alpha), unclamped only.
-          const f32x2 dpv = f2_mul(dLda, am);
-          const bool m0 = cov0 && oG0 < c.alpha_max, m1 = cov1 && oG1 < c.alpha_max;
-          const f32x2 dp = f2_make(m0 ? f2_lo(dpv) : 0.0f, m1 ? f2_hi(dpv) : 0.0f);
+          // dL/dpower = dL/dalpha * alpha (d alpha / d power = o G = alpha), unclamped only
+          // (an uncovered pixel has alpha 0 here, so its share is 0 already).
+          f32x2 dp = f2_mul(dLda, am);
+          if constexpr (kClamp) {
+            const bool m0 = oG0 < c.alpha_max, m1 = oG1 < c.alpha_max;
+            dp = f2_make(m0 ? f2_lo(dp) : 0.0f, m1 ? f2_hi(dp) : 0.0f);
+          }
           mP = f2_add(mP, dp);
           const f32x2 t = f2_mul(dp, FR[q]);
           mY = f2_add(mY, t);
@@ -720,10 +729,25 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
       stage_gaussian(sp, threadIdx.x, rec0[vi], rec1[vi], rec2[vi], y_a);
     }
     __syncthreads();
-    // Positions above the warp's smallest last index test each pixel; the rest do not.
+    // Positions above the warp's smallest last index test each pixel; the rest do not. Whether
+    // the staged Gaussian can reach alpha_max is warp-uniform (every thread reads its opacity).
+    auto clamps = [&](int gg) {
+      if constexpr (kPacked) return !(f2_lo(sp[3][gg].y) > c.unclamped_neg_lo);
+      return true;
+    };
     const int split = max(bstart - 1, min(bend - 1, warp_min_last));
-    for (int jj = bend - 1; jj > split; --jj) visit(jj, jj - bstart, std::true_type{});
-    for (int jj = split; jj >= bstart; --jj) visit(jj, jj - bstart, std::false_type{});
+    for (int jj = bend - 1; jj > split; --jj) {
+      if (clamps(jj - bstart))
+        visit(jj, jj - bstart, std::true_type{}, std::true_type{});
+      else
+        visit(jj, jj - bstart, std::true_type{}, std::false_type{});
+    }
+    for (int jj = split; jj >= bstart; --jj) {
+      if (clamps(jj - bstart))
+        visit(jj, jj - bstart, std::false_type{}, std::true_type{});
+      else
+        visit(jj, jj - bstart, std::false_type{}, std::false_type{});
+    }
   }
 }
 

@@ -438,6 +438,7 @@ rgs_status build_views(rgs_ctx* ctx, const rgs_camera* cams, int n_views, const 
   consts.eps2d = cfg.eps2d;
   for (int k = 0; k < 3; ++k) consts.bg[k] = cfg.bg[k];
   consts.log2_alpha_min = (float)std::log2((double)cfg.alpha_min);
+  consts.unclamped_neg_lo = (float)(1e-5 - std::log2((double)cfg.alpha_max));
   if (!(cfg.alpha_min > 0.0f) || !(cfg.alpha_max > cfg.alpha_min) || !(cfg.alpha_max < 1.0f) ||
       !(cfg.t_min > 0.0f) || !(cfg.eps2d >= 0.0f) || !(cfg.znear > 0.0f) ||
       !std::isfinite(cfg.znear))

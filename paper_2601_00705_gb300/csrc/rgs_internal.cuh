@@ -97,6 +97,10 @@ struct Consts {
   float alpha_min, alpha_max, t_min, znear, eps2d;
   float bg[3];
   float log2_alpha_min;  // log2(alpha_min), rounded once on the host
+  // A staged Gaussian with -log2(o) above this value cannot reach alpha_max at any pixel
+  // (o G <= o < alpha_max by a margin far beyond the error of the hardware exponential), so the
+  // blends skip the clamp and its gradient kink test for it: 1e-5 - log2(alpha_max).
+  float unclamped_neg_lo;
 };
 
 // Device status bits.
@@ -117,7 +121,7 @@ struct Counters {
   uint32_t n_visible_kept;  // min(n_visible, visible-list capacity): the entries sorted and used
   uint32_t pad;
   unsigned long long n_eval;     // (pixel, Gaussian) positions the forward blend visited
-  unsigned long long n_contrib;  // of which composited (covering, before the stop)
+  unsigned long long n_contrib;  // reserved (0): composites are not counted
 };
 
 // Programmatic dependent launch. Every kernel of the library is launched with programmatic

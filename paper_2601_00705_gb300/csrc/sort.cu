@@ -654,6 +654,191 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
 }
 
 // ------------------------------------------------------------------------------------------
+// Wide radix passes for large sorts (the pair list: 10^7 - 10^8 keys): digits of up to 9 bits,
+// so that the 17-bit tile ids of a 16-view 1080p window sort in two passes instead of three, and
+// blocks of kWideTile = 8192 keys (512 threads x 16), so that each digit's run inside a block is
+// long enough for coalesced stores. The same three kernels per pass as above:
+//   upsweep   per-block digit counts, digit-major; equal digits of a warp's 32 keys are added
+//             once (the keys of one Gaussian's footprint are consecutive tile ids, so the high
+//             digits of a warp's keys are mostly equal, and per-key shared-memory atomics would
+//             serialise on one address);
+//   row scan  one block per digit over the blocks;
+//   downsweep stable ranks within each warp's contiguous sub-range, a local sort of keys and
+//             values through shared memory (values are read only when they are placed, so the
+//             ranking holds keys and ranks only), coalesced stores of each digit's run.
+// ------------------------------------------------------------------------------------------
+constexpr int kWideThreads = 512;
+constexpr int kWideWarps = kWideThreads / 32;
+constexpr int kWideItems = 16;
+constexpr int kWideTile = kWideThreads * kWideItems;
+constexpr int kWideBins = 512;
+constexpr int kWideBits = 9;
+// Dynamic shared memory of the wide downsweep: per-warp digit counts, the tile's keys and
+// values, the per-digit block-local starts and global shifts.
+constexpr size_t kWideSmemBytes =
+    sizeof(uint32_t) * ((size_t)kWideWarps * kWideBins + 2 * (size_t)kWideTile + 2 * kWideBins);
+
+__global__ void __launch_bounds__(kWideThreads) wide_upsweep_kernel(const uint32_t* keys,
+                                                                    int64_t n_cap,
+                                                                    const uint32_t* n_dev,
+                                                                    int shift, uint32_t mask,
+                                                                    uint32_t* hist,
+                                                                    int64_t n_blocks) {
+  chain_wait();
+  __shared__ uint32_t counts[kWideBins];
+  const uint32_t n = read_count(n_dev, n_cap);
+  for (int d = threadIdx.x; d < kWideBins; d += kWideThreads) counts[d] = 0;
+  __syncthreads();
+  // Thread t counts the kWideItems consecutive keys base + t * kWideItems + k (four 16-byte
+  // loads; the key arrays are 256-byte aligned and blocks hold whole multiples of 16 keys), one
+  // shared-memory add per run of equal digits.
+  const int64_t first = (int64_t)blockIdx.x * kWideTile + (int64_t)threadIdx.x * kWideItems;
+  if (first < n) {
+    uint32_t k[kWideItems];
+    if (first + kWideItems <= n) {
+      const uint4* p4 = reinterpret_cast<const uint4*>(keys + first);
+#pragma unroll
+      for (int q = 0; q < kWideItems / 4; ++q) {
+        const uint4 v = p4[q];
+        k[4 * q] = v.x;
+        k[4 * q + 1] = v.y;
+        k[4 * q + 2] = v.z;
+        k[4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kWideItems; ++j) k[j] = first + j < n ? keys[first + j] : 0u;
+    }
+    const int cnt = (int)min((int64_t)kWideItems, (int64_t)n - first);
+    uint32_t run_digit = (k[0] >> shift) & mask, run = 1;
+#pragma unroll
+    for (int j = 1; j < kWideItems; ++j) {
+      if (j >= cnt) break;
+      const uint32_t d = (k[j] >> shift) & mask;
+      if (d == run_digit) {
+        ++run;
+      } else {
+        atomicAdd(&counts[run_digit], run);
+        run_digit = d;
+        run = 1;
+      }
+    }
+    atomicAdd(&counts[run_digit], run);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d <= (int)mask; d += kWideThreads)
+    hist[(int64_t)d * n_blocks + blockIdx.x] = counts[d];
+}
+
+__global__ void __launch_bounds__(kWideThreads) wide_row_scan_kernel(uint32_t* hist,
+                                                                     int64_t n_blocks) {
+  chain_wait();
+  const int d = blockIdx.x;
+  uint32_t* row = hist + (int64_t)d * n_blocks;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n_blocks; base += kWideThreads * 4) {
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * 4 + k;
+      v[k] = idx < n_blocks ? row[idx] : 0u;
+      s += v[k];
+    }
+    uint32_t chunk_total;
+    uint32_t pre = block_exclusive_scan<kWideThreads>(s, &chunk_total);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * 4 + k;
+      if (idx < n_blocks) row[idx] = carry + pre;
+      pre += v[k];
+    }
+    carry += chunk_total;
+  }
+  if (threadIdx.x == 0) hist[(int64_t)kWideBins * n_blocks + d] = carry;
+}
+
+__global__ void __launch_bounds__(kWideThreads, 2) wide_downsweep_kernel(
+    const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+    int64_t n_cap, const uint32_t* n_dev, int shift, uint32_t mask, const uint32_t* hist,
+    int64_t n_blocks) {
+  chain_wait();
+  static_assert(kWideThreads == kWideBins, "one thread per digit in the digit scans");
+  extern __shared__ uint32_t wide_smem[];
+  uint32_t* warp_counts = wide_smem;                                  // [kWideWarps][kWideBins]
+  uint32_t* s_keys = warp_counts + kWideWarps * kWideBins;            // [kWideTile]
+  uint32_t* s_vals = s_keys + kWideTile;                              // [kWideTile]
+  uint32_t* s_digit_start = s_vals + kWideTile;                       // [kWideBins]
+  uint32_t* s_digit_shift = s_digit_start + kWideBins;                // [kWideBins]
+  const uint32_t n = read_count(n_dev, n_cap);
+  const int64_t base = (int64_t)blockIdx.x * kWideTile;
+  if (base >= n) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* wc = warp_counts + warp * kWideBins;
+  for (int d = lane; d < kWideBins; d += 32) wc[d] = 0;
+  __syncwarp();
+  const int64_t wbase = base + (int64_t)warp * 32 * kWideItems;
+  uint32_t key[kWideItems], rank[kWideItems];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int nbits = 32 - __clz(mask);
+#pragma unroll
+  for (int r = 0; r < kWideItems; ++r) {
+    const int64_t idx = wbase + r * 32 + lane;
+    key[r] = idx < n ? keys_in[idx] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kWideItems; ++r) {
+    const int64_t idx = wbase + r * 32 + lane;
+    const bool valid = idx < n;
+    const uint32_t digit = valid ? ((key[r] >> shift) & mask) : 0u;
+    const uint32_t peers = warp_digit_peers(digit, valid, nbits);
+    const uint32_t before = __popc(peers & lt_mask);
+    uint32_t prior = 0;
+    if (valid) prior = wc[digit];
+    __syncwarp();
+    if (valid && before == 0) wc[digit] = prior + __popc(peers);
+    __syncwarp();
+    rank[r] = valid ? prior + before : 0xffffffffu;
+  }
+  __syncthreads();
+  {
+    // Thread d: exclusive prefix of digit d over the warps, then the block-local start of the
+    // digit's run and its global shift (global position minus local position, mod 2^32).
+    const int d = threadIdx.x;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < kWideWarps; ++w) {
+      const uint32_t c = warp_counts[w * kWideBins + d];
+      warp_counts[w * kWideBins + d] = acc;
+      acc += c;
+    }
+    const uint32_t local_start = block_exclusive_scan<kWideThreads>(acc, nullptr);
+    const uint32_t row_total = d <= (int)mask ? hist[(int64_t)kWideBins * n_blocks + d] : 0u;
+    const uint32_t digit_base = block_exclusive_scan<kWideThreads>(row_total, nullptr);
+    s_digit_start[d] = local_start;
+    s_digit_shift[d] = d <= (int)mask
+                           ? digit_base + hist[(int64_t)d * n_blocks + blockIdx.x] - local_start
+                           : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kWideItems; ++r) {
+    if (rank[r] == 0xffffffffu) continue;
+    const uint32_t digit = (key[r] >> shift) & mask;
+    const uint32_t local = s_digit_start[digit] + wc[digit] + rank[r];
+    s_keys[local] = key[r];
+    if (vals_in) s_vals[local] = vals_in[wbase + r * 32 + lane];
+  }
+  __syncthreads();
+  const int count = (int)min((int64_t)kWideTile, (int64_t)n - base);
+  for (int t = threadIdx.x; t < count; t += kWideThreads) {
+    const uint32_t k = s_keys[t];
+    const uint32_t pos = s_digit_shift[(k >> shift) & mask] + (uint32_t)t;
+    keys_out[pos] = k;
+    if (vals_out) vals_out[pos] = s_vals[t];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Single-cluster radix sort: the whole sort in one launch of one cluster of C blocks (C = 16,
 // else 8), for n <= C * kCsSlice; used for n_cap <= kCsMaxN, where it beats three launches per
 // pass. Block c owns the slice [c S, (c + 1) S) of the sequence,
@@ -840,6 +1025,74 @@ cudaError_t launch_gather_scan(const uint32_t* ntiles, const uint32_t* order, in
                   stream, lb);
 }
 
+// Sorts of at least this many keys (capacity) take the wide passes.
+constexpr int64_t kWideMinN = 4 << 20;
+
+cudaError_t radix_sort_wide(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                            int64_t n_cap, const uint32_t* n_dev, int begin_bit, int end_bit,
+                            uint32_t* hist, bool* result_in_alt, cudaStream_t stream) {
+  *result_in_alt = false;
+  const int64_t nb = (n_cap + kWideTile - 1) / kWideTile;
+  if (nb == 0 || end_bit <= begin_bit) return cudaSuccess;
+  {
+    // The kernel's dynamic shared memory limit is raised once per device, before its first use.
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t ea = cudaGetDevice(&dev);
+    if (ea != cudaSuccess) return ea;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      ea = cudaFuncSetAttribute(wide_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kWideSmemBytes);
+      if (ea != cudaSuccess) return ea;
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+  }
+  const int bits = end_bit - begin_bit;
+  const int passes = (bits + kWideBits - 1) / kWideBits;
+  const int per_pass = (bits + passes - 1) / passes;
+  uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals ? vals_alt : nullptr;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = begin_bit + p * per_pass;
+    const int w = (shift + per_pass <= end_bit) ? per_pass : end_bit - shift;
+    const uint32_t mask = (1u << w) - 1u;
+    cudaError_t e = launch_chained(wide_upsweep_kernel, dim3((unsigned)nb), dim3(kWideThreads),
+                                   stream, (const uint32_t*)kin, n_cap, n_dev, shift, mask, hist,
+                                   nb);
+    RGS_LAUNCHED();
+    if (e == cudaSuccess)
+      e = launch_chained(wide_row_scan_kernel, dim3(mask + 1), dim3(kWideThreads), stream, hist,
+                         nb);
+    RGS_LAUNCHED();
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)nb);
+      cfg.blockDim = dim3(kWideThreads);
+      cfg.dynamicSmemBytes = kWideSmemBytes;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, wide_downsweep_kernel, (const uint32_t*)kin,
+                             (const uint32_t*)vin, kout, vout, n_cap, n_dev, shift, mask,
+                             (const uint32_t*)hist, nb);
+    }
+    RGS_LAUNCHED();
+    if (e != cudaSuccess) return e;
+    uint32_t* t = kin;
+    kin = kout;
+    kout = t;
+    t = vin;
+    vin = vout;
+    vout = t;
+    *result_in_alt = !*result_in_alt;
+  }
+  return cudaGetLastError();
+}
+
 template <int ITEMS>
 cudaError_t radix_sort_t(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                          int64_t n_cap, const uint32_t* n_dev, int begin_bit, int end_bit,
@@ -959,6 +1212,12 @@ cudaError_t launch_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
       return e;
     }
   }
+  // The wide upsweep reads keys with 16-byte loads: both key buffers must be 16-byte aligned.
+  const bool aligned16 = reinterpret_cast<uintptr_t>(keys) % 16 == 0 &&
+                         reinterpret_cast<uintptr_t>(keys_alt) % 16 == 0;
+  if (n_cap >= kWideMinN && items == kSortItems && aligned16)
+    return radix_sort_wide(keys, vals, keys_alt, vals_alt, n_cap, n_dev, begin_bit, end_bit, hist,
+                           result_in_alt, stream);
   if (items == kSortItemsSmall)
     return radix_sort_t<kSortItemsSmall>(keys, vals, keys_alt, vals_alt, n_cap, n_dev, begin_bit,
                                          end_bit, hist, result_in_alt, stream);

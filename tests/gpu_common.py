@@ -71,8 +71,16 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
 
 
-def compare_forward(gpu, orc, mask=None):
-    """Asserts forward parity on non-ambiguous pixels; returns a dict of the measured errors."""
+# Largest fraction of the compared pixels the oracle may flag as ambiguous (a discrete decision
+# within the modelled FP32 error of its threshold) per workload: about twice the fraction
+# measured on the tests' inputs (tiny 1.6e-4, replica and tum 5.5e-4, uneven 6.5e-4, large
+# 2.9e-3). A larger fraction means the flag model or its margins widened.
+AMBIGUOUS_BUDGET = dict(tiny=4e-4, replica=1.2e-3, tum=1.2e-3, uneven=1.3e-3, large=6e-3)
+
+
+def compare_forward(gpu, orc, mask=None, budget=None):
+    """Asserts forward parity on non-ambiguous pixels, and that at most `budget` of the compared
+    pixels are ambiguous; returns a dict of the measured errors."""
     ok = (orc["ambiguous"] & oracle.FORWARD_AMBIGUOUS) == 0
     if mask is not None:
         ok &= mask
@@ -93,6 +101,8 @@ def compare_forward(gpu, orc, mask=None):
     assert ec <= COLOR_ATOL, info
     assert ea <= COLOR_ATOL, info
     assert ed <= DEPTH_RTOL, info
+    if budget is not None:
+        assert info["ambiguous_fraction"] <= budget, info
     return info
 
 

@@ -163,7 +163,7 @@ def test_cuda_graph_replay_matches_eager(scene, tile):
     for k in grads:
         assert rel_l2(grads[k].cpu().numpy(), eager_grad[k].cpu().numpy()) <= 1e-5, k
     st = r.stats(state)
-    assert st["n_eval"] > 0 and st["n_contrib"] > 0, st
+    assert st["n_eval"] > 0, st
     r.release(state)
 
 

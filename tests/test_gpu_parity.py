@@ -11,8 +11,8 @@ import torch
 import oracle
 from paper_2601_00705_gb300 import binding, synthetic
 
-from gpu_common import (compare_backward, compare_forward, gpu_render, masked_l1_upstream,
-                        renderer, to_dev)
+from gpu_common import (AMBIGUOUS_BUDGET, compare_backward, compare_forward, gpu_render,
+                        masked_l1_upstream, renderer, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +57,31 @@ def test_radix_sort_is_stable_and_matches_numpy(n, begin, end, distinct):
     np.testing.assert_array_equal(v.cpu().numpy().view(np.uint32), vals[order])
 
 
+# From 4M keys (capacity) the sort takes passes of up to 9 bits in blocks of 8192 keys.
+@pytest.mark.parametrize("n,begin,end,runs", [
+    (4_194_304, 0, 17, False), (4_194_305, 0, 17, True), (5_000_003, 0, 32, False),
+    (9_000_001, 3, 20, True), (8_191 * 1024 + 7, 0, 31, True)])
+def test_wide_radix_sort_is_stable_and_matches_numpy(n, begin, end, runs):
+    rng = np.random.default_rng(n + begin)
+    if runs:
+        # Pair-list-like keys: runs of consecutive values (a footprint's tiles), runs in random
+        # order, so that a warp's keys share their high digits.
+        starts = rng.integers(0, 1 << min(end, 31), size=n // 6 + 1, dtype=np.uint64)
+        keys = (starts[:, None] + np.arange(6, dtype=np.uint64)[None, :]).ravel()[:n]
+        keys = (keys % np.uint64(1 << 32)).astype(np.uint32)
+    else:
+        keys = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    k = torch.from_numpy(keys.view(np.int32)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    _ctx().radix_sort_u32(k.data_ptr(), v.data_ptr(), n, begin, end)
+    mask = np.uint64((1 << (end - begin)) - 1)
+    digits = (keys.astype(np.uint64) >> np.uint64(begin)) & mask
+    order = np.argsort(digits, kind="stable")
+    np.testing.assert_array_equal(k.cpu().numpy().view(np.uint32), keys[order])
+    np.testing.assert_array_equal(v.cpu().numpy().view(np.uint32), vals[order])
+
+
 def test_radix_sort_keys_only():
     rng = np.random.default_rng(7)
     keys = rng.integers(0, 1 << 31, size=123_457, dtype=np.uint64).astype(np.uint32)
@@ -90,7 +115,7 @@ def test_tiny_forward_and_all_gradients():
     d_alpha[~keep] = 0.0
     orc = oracle.render(g, wl.cameras, d_color=d_color, d_alpha=d_alpha)
     gpu = gpu_render(g, wl.cameras, d_color=d_color, d_alpha=d_alpha)
-    info = compare_forward(gpu, orc)
+    info = compare_forward(gpu, orc, budget=AMBIGUOUS_BUDGET["tiny"])
     errs = compare_backward(gpu, orc)
     print("tiny", info, errs, gpu["stats"])
 
@@ -132,7 +157,7 @@ def test_replica_forward_and_pose_gradient():
     g, orc0, d_color, d_depth = _oracle_l1_case(wl, weight_depth=0.1)
     orc = oracle.render(g, wl.cameras, d_color=d_color, d_depth=d_depth)
     gpu = gpu_render(g, wl.cameras, d_color=d_color, d_depth=d_depth, grad_mask=binding.GRAD_POSE)
-    info = compare_forward(gpu, orc)
+    info = compare_forward(gpu, orc, budget=AMBIGUOUS_BUDGET["replica"])
     errs = compare_backward(gpu, orc, keys=("g_pose",))
     print("replica", info, errs, gpu["stats"])
 
@@ -143,7 +168,7 @@ def test_tum_window_all_gradients():
     g, orc0, d_color, _ = _oracle_l1_case(wl)
     orc = oracle.render(g, wl.cameras, d_color=d_color)
     gpu = gpu_render(g, wl.cameras, d_color=d_color)
-    info = compare_forward(gpu, orc)
+    info = compare_forward(gpu, orc, budget=AMBIGUOUS_BUDGET["tum"])
     errs = compare_backward(gpu, orc)
     print("tum", info, errs, gpu["stats"])
 
