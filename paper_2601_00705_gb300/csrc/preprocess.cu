@@ -770,7 +770,10 @@ __global__ void __launch_bounds__(kPreThreads) backward_view_kernel(
 // exactly once.
 // ------------------------------------------------------------------------------------------
 template <int DEG, bool kReg>
-__global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
+// At most 80 registers (6 blocks of 128 threads per SM): the kernel waits on its gathers, and
+// 24 resident warps per SM instead of 16 halve its time despite a few spilled registers (0.98
+// -> 0.50 ms over 3M Gaussians; with 64 registers the spills cost more than the warps gain).
+__global__ void __launch_bounds__(kPreThreads, 6) backward_gaussian_kernel(
     const __grid_constant__ Views views, int n, const float* __restrict__ means,
     const float* __restrict__ log_scales, const float* __restrict__ quats,
     const float* __restrict__ logits, unsigned long long* __restrict__ vis_mask,
@@ -780,6 +783,7 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
     int pose_blocks, int n_views, float* __restrict__ d_pose) {
   chain_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
+  __shared__ float s_gsh[3 * K * kPreThreads];
   // Blocks 0 .. 6 V - 1 first finish the twist gradient: d_pose[v, k] = the sum over phase 1's
   // blocks of their partials, in double precision (phase 1 is complete when this kernel runs).
   if (d_pose && (int)blockIdx.x < 6 * n_views) {
@@ -815,9 +819,12 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
   }
   const float logit = __ldg(logits + i);
   float gm[3] = {0, 0, 0}, gSw[6] = {0, 0, 0, 0, 0, 0}, gop = 0.0f;
-  float gsh[3 * K];
+  // The SH coefficient gradients accumulate in this thread's column of shared memory (bank =
+  // thread), which keeps 3K accumulators out of registers: at 114 registers the kernel held 16
+  // warps per SM and waited on its loads.
+  float* gsh = s_gsh + threadIdx.x;  // gsh[k * kPreThreads]
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0f;
+  for (int k = 0; k < 3 * K; ++k) gsh[k * kPreThreads] = 0.0f;
   // Views that see the Gaussian, as marked by phase 1 (consumed: left zero for the next call).
   uint64_t vis = vis_mask[i];
   if (vis) vis_mask[i] = 0ull;
@@ -878,9 +885,9 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
       sh_basis<DEG>(d0 * rn, d1 * rn, d2 * rn, Y);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        gsh[3 * k + 0] += cur.r2.y * Y[k];
-        gsh[3 * k + 1] += cur.r2.z * Y[k];
-        gsh[3 * k + 2] += cur.r2.w * Y[k];
+        gsh[(3 * k + 0) * kPreThreads] += cur.r2.y * Y[k];
+        gsh[(3 * k + 1) * kPreThreads] += cur.r2.z * Y[k];
+        gsh[(3 * k + 2) * kPreThreads] += cur.r2.w * Y[k];
       }
     }
     v = v_next;
@@ -993,10 +1000,11 @@ __global__ void __launch_bounds__(kPreThreads) backward_gaussian_kernel(
 #pragma unroll
       for (int k = 0; k < 3 * K / 4; ++k)
         reinterpret_cast<float4*>(p)[k] =
-            make_float4(gsh[4 * k], gsh[4 * k + 1], gsh[4 * k + 2], gsh[4 * k + 3]);
+            make_float4(gsh[(4 * k) * kPreThreads], gsh[(4 * k + 1) * kPreThreads],
+                        gsh[(4 * k + 2) * kPreThreads], gsh[(4 * k + 3) * kPreThreads]);
     } else {
 #pragma unroll
-      for (int k = 0; k < 3 * K; ++k) p[k] = gsh[k];
+      for (int k = 0; k < 3 * K; ++k) p[k] = gsh[k * kPreThreads];
     }
   }
 }

@@ -405,6 +405,33 @@ struct TileCover {
     return true;
   }
 
+  // The cover set up by lane src of the warp, in every lane (all lanes must call it).
+  __device__ __forceinline__ TileCover broadcast(int src) const {
+    TileCover o;
+    const unsigned m = 0xffffffffu;
+    o.ty0 = __shfl_sync(m, ty0, src);
+    o.ty1 = __shfl_sync(m, ty1, src);
+    o.bx0 = __shfl_sync(m, bx0, src);
+    o.bx1 = __shfl_sync(m, bx1, src);
+    o.box_only = __shfl_sync(m, (int)box_only, src) != 0;
+    o.tile_w = __shfl_sync(m, tile_w, src);
+    o.tile_h = __shfl_sync(m, tile_h, src);
+    o.tiles_x = __shfl_sync(m, tiles_x, src);
+    o.mx = __shfl_sync(m, mx, src);
+    o.my = __shfl_sync(m, my, src);
+    o.kap = __shfl_sync(m, kap, src);
+    o.rx = __shfl_sync(m, rx, src);
+    o.ry = __shfl_sync(m, ry, src);
+    o.inv_tw = __shfl_sync(m, inv_tw, src);
+    o.x_lo = __shfl_sync(m, x_lo, src);
+    o.x_hi = __shfl_sync(m, x_hi, src);
+    o.inv_syy = __shfl_sync(m, inv_syy, src);
+    o.s = __shfl_sync(m, s, src);
+    o.h = __shfl_sync(m, h, src);
+    o.dy_star = __shfl_sync(m, dy_star, src);
+    return o;
+  }
+
   // Column span [tx0, tx1] of tile row ty (ty0 <= ty <= ty1); false if the row is not touched.
   __device__ __forceinline__ bool span(int ty, int& tx0, int& tx1) const {
     if (box_only) {

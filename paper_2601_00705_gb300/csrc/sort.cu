@@ -663,9 +663,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
 //             digits of a warp's keys are mostly equal, and per-key shared-memory atomics would
 //             serialise on one address);
 //   row scan  one block per digit over the blocks;
-//   downsweep stable ranks within each warp's contiguous sub-range, a local sort of keys and
-//             values through shared memory (values are read only when they are placed, so the
-//             ranking holds keys and ranks only), coalesced stores of each digit's run.
+//   downsweep stable ranks within each warp's contiguous sub-range (the lanes holding equal
+//             digits found by one ballot per digit bit; a match instruction per 32 keys was
+//             slower, 2.37 against 1.96 ms for the two passes over 155M pairs), a local sort of
+//             keys and values through shared memory (values are read only when they are placed,
+//             so the ranking holds keys and ranks only), coalesced stores of each digit's run.
 // ------------------------------------------------------------------------------------------
 constexpr int kWideThreads = 512;
 constexpr int kWideWarps = kWideThreads / 32;
