@@ -287,8 +287,8 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, int i, flo
 }
 
 // Forward, pass 1 (cull): one thread per (Gaussian, chunk of views). Only the camera-space mean,
-// the projected centre and the footprint-radius bound of project_view are computed; every entry
-// gets ntiles = 0, and the entries that may touch the image are appended to `cand` (gathered in
+// the projected centre and the footprint-radius bound of project_view are computed, and the
+// entries that may touch the image are appended to `cand` (gathered in
 // shared memory, then one global atomic per block; their order does not matter). Pass 2 then
 // projects only those, so its warps are not held up by the large majority of entries that fall
 // outside the image.
@@ -342,11 +342,17 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
     bool keep = false;
     if (finite && kappa >= 0.0f) {
       const float* R = ps.R;
-      float lo;
-      const float z = dot3_plus_dd(R[6], R[7], R[8], m[0], m[1], m[2], ps.t[2], lo);
-      if (z > c.znear) {
-        const float x = dot3_plus_dd(R[0], R[1], R[2], m[0], m[1], m[2], ps.t[0], lo);
-        const float y = dot3_plus_dd(R[3], R[4], R[5], m[0], m[1], m[2], ps.t[1], lo);
+      // Plain FMA dot products: the cull only has to keep every Gaussian the projection keeps.
+      // Their error is below 8 units of roundoff of the summed magnitudes, so a Gaussian is
+      // dropped for the near plane only when even z + that bound is at or below it (the
+      // projection then decides with its compensated depth); the projected centre's error is
+      // far inside the radius bound's 4 px slack.
+      const float z = fmaf(R[6], m[0], fmaf(R[7], m[1], fmaf(R[8], m[2], ps.t[2])));
+      const float z_err =
+          4.8e-7f * (fabsf(R[6] * m[0]) + fabsf(R[7] * m[1]) + fabsf(R[8] * m[2]) + fabsf(ps.t[2]));
+      if (z + z_err > c.znear && z > 0.0f) {
+        const float x = fmaf(R[0], m[0], fmaf(R[1], m[1], fmaf(R[2], m[2], ps.t[0])));
+        const float y = fmaf(R[3], m[0], fmaf(R[4], m[1], fmaf(R[5], m[2], ps.t[1])));
         const float rz = 1.0f / z;
         const float u = x * rz, w = y * rz;
         float uc = u, wc = w;
@@ -366,8 +372,9 @@ __global__ void __launch_bounds__(kPreThreads) cull_kernel(
                  my - rad > (float)(vp.height - 1));
       }
     }
-    if (in_range) ntiles[vi] = 0u;
-    // The block's Gaussians own whole words of row v of the visibility bitmask.
+    // The block's Gaussians own whole words of row v of the visibility bitmask. Tile counts are
+    // written by the projection for its candidates only: the later passes read them only for
+    // entries whose visibility bit is set.
     if (threadIdx.x < kPreThreads / 32) {
       const int w = blockIdx.x * (kPreThreads / 32) + threadIdx.x;
       if (w < bit_words) vis_bits[(size_t)v * bit_words + w] = 0u;

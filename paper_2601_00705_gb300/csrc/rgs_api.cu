@@ -19,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "rgs_internal.cuh"
 
@@ -1073,7 +1074,22 @@ rgs_status rgs_copy_records(rgs_ctx* ctx, uint64_t handle, float* host_rec,
                                cudaMemcpyDeviceToHost, stream),
                "copy tile counts");
   }
+  std::vector<uint32_t> bits;
+  const int64_t n = s->g.n, words = vis_bit_words_per_view(n);
+  if (host_ntiles && vn > 0 && n > 0) {
+    bits.resize((size_t)(vn / n) * words);
+    RGS_CUDA(cudaMemcpyAsync(bits.data(), s->vis_bits, sizeof(uint32_t) * bits.size(),
+                             cudaMemcpyDeviceToHost, stream),
+             "copy visibility bits");
+  }
   RGS_CUDA(cudaStreamSynchronize(stream), "sync");
+  // The forward writes tile counts for its projection candidates only; an entry whose
+  // visibility bit is clear touches no tile.
+  if (!bits.empty())
+    for (int64_t vi = 0; vi < vn; ++vi) {
+      const int64_t v = vi / n, i = vi - v * n;
+      if (!((bits[(size_t)(v * words + i / 32)] >> (i % 32)) & 1u)) host_ntiles[vi] = 0u;
+    }
   return RGS_OK;
 }
 
