@@ -430,50 +430,42 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
 }
 
 // ------------------------------------------------------------------------------------------
-// Warp reduction of the ten screen-space gradient values of one Gaussian. Each butterfly level
-// halves the number of values a lane carries (10 -> 5 -> 3 -> 2 -> 1 -> 1), so it takes 12
-// shuffles instead of 10 x 5. On return the lane whose bits (b4 b3 b2 b1) select slot
-// reduced_slot() holds that slot's warp total (lanes with b0 = 1 hold a copy; slot -1 = none).
+// Per-warp reduction of the visited Gaussians' gradient sums through shared memory. Each visit
+// writes the lane's kRedVals partial sums as one column of kRedVals rows (row b * kRedVals + k
+// for the b-th Gaussian of the group); after kRedBatch visits (or at the end of a staged batch)
+// every lane adds up whole rows (eight 16-byte reads of a row padded to 36 floats, so that both
+// the column writes and the row reads are free of bank conflicts) and parks the row total in
+// the padding. Lane b then turns Gaussian b's totals into its whitened moments and issues the
+// atomics. Per visit this costs kRedVals shared stores and a share of the row sums, in place of
+// a shuffle butterfly with its selects after every Gaussian.
+//
+// The lane's values: k = 0..2: sdp, sr, srr (the sums of dp, dp r and dp r^2 over its pixels,
+// r the row offset from the tile's anchor row), k = 3..5: t_a sdp, t_a sr, t_a^2 sdp (t_a the
+// whitened offset of its column at the anchor row), k = 6..8 (9): the colour (depth) weights.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float transpose_reduce10(const float (&a)[10], int lane) {
-  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
-  float b[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float keep = h4 ? a[k + 5] : a[k];
-    const float send = h4 ? a[k] : a[k + 5];
-    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-  float cc[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float hi = k + 3 < 5 ? b[(k + 3) % 5] : 0.0f;  // slots 3, 4 and an empty third
-    const float keep = h3 ? hi : b[k];
-    const float send = h3 ? b[k] : hi;
-    cc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  float d[2];
-  {
-    const float keep0 = h2 ? cc[2] : cc[0];
-    const float send0 = h2 ? cc[0] : cc[2];
-    d[0] = keep0 + __shfl_xor_sync(0xffffffffu, send0, 4);
-    const float keep1 = h2 ? 0.0f : cc[1];
-    const float send1 = h2 ? cc[1] : 0.0f;
-    d[1] = keep1 + __shfl_xor_sync(0xffffffffu, send1, 4);
-  }
-  const float keep = h1 ? d[1] : d[0];
-  const float send = h1 ? d[0] : d[1];
-  float e = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  e += __shfl_xor_sync(0xffffffffu, e, 1);
-  return e;
-}
+constexpr int kRedPad = 36;
 
-__device__ __forceinline__ int reduced_slot(int lane) {
-  const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1,
-            b1 = (lane >> 1) & 1;
-  if (b2 == 0) return (b1 ? (b3 ? 4 : 1) : (b3 ? 3 : 0)) + 5 * b4;
-  if (b1 == 0 && b3 == 0) return 2 + 5 * b4;
-  return -1;
+template <bool kAux>
+struct RedLayout {
+  static constexpr int kVals = kAux ? 10 : 9;
+  static constexpr int kBatch = kAux ? 6 : 7;  // kVals * kBatch <= 64: two row passes
+  static constexpr int kRows = kVals * kBatch;
+};
+
+// Adds up row r (32 lane values) and parks the total in its first padding float.
+__device__ __forceinline__ void reduce_row(float* red, int r) {
+  const ulonglong2* row = reinterpret_cast<const ulonglong2*>(red + r * kRedPad);
+  f32x2 s[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const ulonglong2 v = row[c];
+    s[c] = f2_add(v.x, v.y);
+  }
+#pragma unroll
+  for (int h = 4; h > 0; h >>= 1)
+#pragma unroll
+    for (int c = 0; c < h; ++c) s[c] = f2_add(s[c], s[c + h]);
+  red[r * kRedPad + 32] = f2_lo(s[0]) + f2_hi(s[0]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -495,9 +487,11 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   constexpr bool kPacked = PPT % 2 == 0;
   constexpr int P2 = kPacked ? PPT / 2 : 1;
   static_assert(kThreads % 32 == 0, "whole warps only");
+  using RL = RedLayout<kAux>;
   __shared__ ulonglong2 sp[kPacked ? 6 : 3][kThreads];
   __shared__ uint32_t s_vi[kThreads];
   __shared__ int s_max_last[kThreads / 32];
+  __shared__ __align__(16) float s_red[kThreads / 32][RL::kRows * kRedPad];
   const int gtile = blockIdx.x;
   const int v = view_of_tile(views, gtile);
   const ViewParams& vp = views.v[v];
@@ -512,7 +506,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   const int r0_ = (int)(threadIdx.x / TW) * PPT - TH / 2;
   const uint2 range = ranges[gtile];
   const int lane = threadIdx.x & 31;
-  const int slot = reduced_slot(lane);
+  float* const red = s_red[threadIdx.x >> 5];
 
   // Per pixel: transmittance behind the current position, the upstream gradients, and
   // U = sum_ch dL/dC_ch S_ch + dL/dD S_D, where S is the colour / depth composited behind the
@@ -578,20 +572,19 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   // One Gaussian (list position jj, staged at g) against the thread's pixels; kCheckLast tests
   // each pixel's last-contributor index.
   // kClamp: the Gaussian may reach alpha_max somewhere (clamp, and no gradient through a
-  // clamped alpha); without it neither can happen and both tests drop out.
-  auto visit = [&](int jj, int g, auto check_last, auto clamp_tag) {
+  // clamped alpha); without it neither can happen and both tests drop out. The lane's partial
+  // sums go to column `lane` of the rows from `rows` on (zeros where it covers nothing).
+  auto visit = [&](int jj, int g, float* rows, auto check_last, auto clamp_tag) {
     constexpr bool kCheckLast = decltype(check_last)::value;
     constexpr bool kClamp = decltype(clamp_tag)::value;
-    float acc[10];
-#pragma unroll
-    for (int s2 = 0; s2 < 10; ++s2) acc[s2] = 0.0f;
-    bool contrib = false;
+    (void)kClamp;  // the one-pixel path always clamps
+    // Per-thread sums of dp = dL/dpower over the thread's pixels, weighted by their row offset
+    // r from the anchor row: sdp = sum dp, sr = sum dp r, srr = sum dp r^2. Every pixel of the
+    // column has w = (t, s) = (t_a + r l21, s_a + r l22), so the whitened moments follow from
+    // these three and t_a once per Gaussian.
+    float sdp = 0.0f, sr = 0.0f, srr = 0.0f, ta = 0.0f, gr = 0.0f, gg = 0.0f, gb = 0.0f,
+          gz = 0.0f;
     if (!kCheckLast || jj <= thread_last) {
-      // Per-thread sums of dp = dL/dpower over the thread's pixels, weighted by their row offset
-      // r from the anchor row: sdp = sum dp, sr = sum dp r, srr = sum dp r^2. Every pixel of the
-      // column has w = (t, s) = (t_a + r l21, s_a + r l22), so the whitened moments follow
-      // from these three once per Gaussian.
-      float sdp = 0.0f, sr = 0.0f, srr = 0.0f, ta, l21, l22, s_a;
       if constexpr (kPacked) {
         const ulonglong2 X = sp[0][g], L1 = sp[1][g], L2 = sp[2][g], L3 = sp[3][g];
         const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
@@ -611,7 +604,6 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           const float a1 = kClamp ? fminf(c.alpha_max, oG1) : oG1;
           const bool cov0 = (!kCheckLast || jj <= last[k0]) && a0 >= c.alpha_min;
           const bool cov1 = (!kCheckLast || jj <= last[k1]) && a1 >= c.alpha_min;
-          contrib = contrib || cov0 || cov1;
           // A pixel this Gaussian does not cover gets alpha 0 and 1 / (1 - alpha) = 1 (the
           // hardware reciprocal of 1 is exactly 1 on sm_103a, measured), so its transmittance,
           // suffix sum and every accumulator stay bit-identical.
@@ -646,42 +638,35 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           mY = f2_add(mY, t);
           mYY = f2_fma(t, FR[q], mYY);
         }
-        acc[kGR] = f2_lo(aR) + f2_hi(aR);
-        acc[kGG] = f2_lo(aG) + f2_hi(aG);
-        acc[kGB] = f2_lo(aB) + f2_hi(aB);
-        if constexpr (kAux) acc[kGZ] = f2_lo(aZ) + f2_hi(aZ);
+        gr = f2_lo(aR) + f2_hi(aR);
+        gg = f2_lo(aG) + f2_hi(aG);
+        gb = f2_lo(aB) + f2_hi(aB);
+        if constexpr (kAux) gz = f2_lo(aZ) + f2_hi(aZ);
         sdp = f2_lo(mP) + f2_hi(mP);
         sr = f2_lo(mY) + f2_hi(mY);
         srr = f2_lo(mYY) + f2_hi(mYY);
         ta = f2_lo(TA);
-        l21 = f2_lo(L2.x);
-        l22 = f2_lo(L2.y);
-        s_a = f2_lo(L3.x);
       } else {
         const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
         const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
         const float4 g2 = reinterpret_cast<const float4*>(sp[2])[g];
         ta = __fmaf_rn(g0.z, __fsub_rn(__fsub_rn(fx, g0.x), g0.y), g0.w);
-        l21 = g1.x;
-        l22 = g1.y;
-        s_a = g1.z;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           if (kCheckLast && jj > last[k]) continue;
           const float fr = (float)(r0_ + k);
-          const float oG = ex2_neg_approx(neg_log2_og(ta, s_a, l21, l22, g1.w, fr));
+          const float oG = ex2_neg_approx(neg_log2_og(ta, g1.z, g1.x, g1.y, g1.w, fr));
           const float a = fminf(c.alpha_max, oG);
           if (a < c.alpha_min) continue;
-          contrib = true;
           const float rom = rcp_approx(__fsub_rn(1.0f, a));
           T[k] = T[k] * rom;  // transmittance in front of this Gaussian
           const float w = a * T[k];
-          acc[kGR] = fmaf(gC0[k], w, acc[kGR]);
-          acc[kGG] = fmaf(gC1[k], w, acc[kGG]);
-          acc[kGB] = fmaf(gC2[k], w, acc[kGB]);
+          gr = fmaf(gC0[k], w, gr);
+          gg = fmaf(gC1[k], w, gg);
+          gb = fmaf(gC2[k], w, gb);
           float q, dLda;
           if constexpr (kAux) {
-            acc[kGZ] = fmaf(gD[k], w, acc[kGZ]);
+            gz = fmaf(gD[k], w, gz);
             q = fmaf(gC0[k], g2.x, fmaf(gC1[k], g2.y, fmaf(gC2[k], g2.z, gD[k] * g2.w)));
             dLda = fmaf(T[k], q, rom * (gAT[k] - U[k]));
           } else {
@@ -698,24 +683,70 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
           }
         }
       }
-      // The thread's share of the whitened moments: with w_a = (t_a, s_a) at the anchor row and
-      // e = (l21, l22), sum dp w = sdp w_a + sr e and
-      // sum dp w w^T = sdp w_a w_a^T + sr (w_a e^T + e w_a^T) + srr e e^T; zero when the thread
-      // covers nothing.
-      const float m1t = fmaf(l21, sr, ta * sdp), m1s = fmaf(l22, sr, s_a * sdp);
-      const float xt = fmaf(l21, srr, ta * sr), xs = fmaf(l22, srr, s_a * sr);
-      acc[kM0] = sdp;
-      acc[kWt] = m1t;
-      acc[kWs] = m1s;
-      acc[kWtt] = fmaf(l21, xt, ta * m1t);
-      acc[kWts] = fmaf(l22, xt, s_a * m1t);
-      acc[kWss] = fmaf(l22, xs, s_a * m1s);
     }
-    if (__any_sync(0xffffffffu, contrib)) {
-      const float total = transpose_reduce10(acc, lane);
-      if (slot >= 0 && (lane & 1) == 0)
-        atomicAdd(g2d + (size_t)s_vi[g] * kG2Stride + slot, total);
+    const float tsdp = ta * sdp;
+    float* col = rows + lane;
+    col[0 * kRedPad] = sdp;
+    col[1 * kRedPad] = sr;
+    col[2 * kRedPad] = srr;
+    col[3 * kRedPad] = tsdp;
+    col[4 * kRedPad] = ta * sr;
+    col[5 * kRedPad] = ta * tsdp;
+    col[6 * kRedPad] = gr;
+    col[7 * kRedPad] = gg;
+    col[8 * kRedPad] = gb;
+    if constexpr (kAux) col[9 * kRedPad] = gz;
+    else (void)gz;
+  };
+
+  // Row sums of the last nb visits (staged at g_first, g_first - 1, ...), then one lane per
+  // Gaussian forms its whitened moments (with w = (t_a + r l21, s_a + r l22):
+  // sum dp w = (S3 + l21 S1, s_a S0 + l22 S1) and
+  // sum dp w w^T = (S5 + l21 (2 S4 + l21 S2), s_a W_t + l22 (S4 + l21 S2),
+  // s_a W_s + l22 (s_a S1 + l22 S2)) for the lane values S0..S5) and adds them to its record.
+  auto flush = [&](int nb, int g_first) {
+    __syncwarp();
+    const int nrows = nb * RL::kVals;
+    for (int r = lane; r < nrows; r += 32) reduce_row(red, r);
+    __syncwarp();
+    if (lane < nb) {
+      const int g = g_first - lane;
+      const float* tot = red + lane * RL::kVals * kRedPad + 32;
+      float S[RL::kVals];
+#pragma unroll
+      for (int k = 0; k < RL::kVals; ++k) S[k] = tot[k * kRedPad];
+      float l21, l22, s_a;
+      if constexpr (kPacked) {
+        l21 = f2_lo(sp[2][g].x);
+        l22 = f2_lo(sp[2][g].y);
+        s_a = f2_lo(sp[3][g].x);
+      } else {
+        const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
+        l21 = g1.x;
+        l22 = g1.y;
+        s_a = g1.z;
+      }
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < RL::kVals; ++k) any = any || S[k] != 0.0f;
+      if (any) {
+        const float wt = fmaf(l21, S[1], S[3]);
+        const float ws = fmaf(s_a, S[0], l22 * S[1]);
+        const float u = fmaf(l21, S[2], S[4]);
+        float* dst = g2d + (size_t)s_vi[g] * kG2Stride;
+        atomicAdd(dst + kM0, S[0]);
+        atomicAdd(dst + kWt, wt);
+        atomicAdd(dst + kWs, ws);
+        atomicAdd(dst + kWtt, fmaf(l21, S[4] + u, S[5]));
+        atomicAdd(dst + kWts, fmaf(s_a, wt, l22 * u));
+        atomicAdd(dst + kWss, fmaf(s_a, ws, l22 * fmaf(s_a, S[1], l22 * S[2])));
+        atomicAdd(dst + kGR, S[6]);
+        atomicAdd(dst + kGG, S[7]);
+        atomicAdd(dst + kGB, S[8]);
+        if constexpr (kAux) atomicAdd(dst + kGZ, S[9]);
+      }
     }
+    __syncwarp();
   };
 
   const int first = (int)range.x;
@@ -731,23 +762,38 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     __syncthreads();
     // Positions above the warp's smallest last index test each pixel; the rest do not. Whether
     // the staged Gaussian can reach alpha_max is warp-uniform (every thread reads its opacity).
-    auto clamps = [&](int gg) {
-      if constexpr (kPacked) return !(f2_lo(sp[3][gg].y) > c.unclamped_neg_lo);
+    auto clamps = [&](int g) {
+      if constexpr (kPacked) return !(f2_lo(sp[3][g].y) > c.unclamped_neg_lo);
       return true;
+    };
+    int nb = 0, g_first = bend - 1 - bstart;
+    auto next = [&](int g) {
+      if (++nb == RL::kBatch) {
+        flush(nb, g_first);
+        nb = 0;
+        g_first = g - 1;
+      }
     };
     const int split = max(bstart - 1, min(bend - 1, warp_min_last));
     for (int jj = bend - 1; jj > split; --jj) {
-      if (clamps(jj - bstart))
-        visit(jj, jj - bstart, std::true_type{}, std::true_type{});
+      const int g = jj - bstart;
+      float* rows = red + nb * RL::kVals * kRedPad;
+      if (clamps(g))
+        visit(jj, g, rows, std::true_type{}, std::true_type{});
       else
-        visit(jj, jj - bstart, std::true_type{}, std::false_type{});
+        visit(jj, g, rows, std::true_type{}, std::false_type{});
+      next(g);
     }
     for (int jj = split; jj >= bstart; --jj) {
-      if (clamps(jj - bstart))
-        visit(jj, jj - bstart, std::false_type{}, std::true_type{});
+      const int g = jj - bstart;
+      float* rows = red + nb * RL::kVals * kRedPad;
+      if (clamps(g))
+        visit(jj, g, rows, std::false_type{}, std::true_type{});
       else
-        visit(jj, jj - bstart, std::false_type{}, std::false_type{});
+        visit(jj, g, rows, std::false_type{}, std::false_type{});
+      next(g);
     }
+    if (nb > 0) flush(nb, g_first);
   }
 }
 
