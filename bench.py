@@ -820,8 +820,29 @@ def run_ours(args, world, rank, local):
         e1.record()
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = reduce_max(float(np.sum(e2e_ms)), world, dev)
-    e2e_value = throughput(world, pixels, args.steps, e2e_total)
+    # Copies over the host link see other tenants of the machine: a step now and then takes
+    # 1.5-3x the others. The value is taken at the median step (the mean and the slowest step
+    # are reported beside it).
+    e2e_median = reduce_max(float(np.median(e2e_ms)), world, dev)
+    e2e_mean = reduce_max(float(np.mean(e2e_ms)), world, dev)
+    e2e_worst = reduce_max(float(np.max(e2e_ms)), world, dev)
+    e2e_value = throughput(world, pixels, 1, e2e_median)
+    # The host link's copy rates on this machine (pinned buffers, one direction at a time), the
+    # bound of the end-to-end step's copies.
+    link = {}
+    probe_host = pin["sh"]
+    probe_dev = torch.empty_like(probe_host, device=dev)
+    for label, copy in (("h2d_gbs", lambda: probe_dev.copy_(probe_host, non_blocking=True)),
+                        ("d2h_gbs", lambda: probe_host.copy_(probe_dev, non_blocking=True))):
+        copy()
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record()
+        copy()
+        l1.record()
+        l1.synchronize()
+        link[label] = probe_host.numel() * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9
+    del probe_dev
 
     # Roofline of the dominant kernel (the blend phases are single launches per step).
     peaks, peak_src = measured_peaks()
@@ -877,8 +898,9 @@ def run_ours(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / args.steps,
-                "cuda_graph": True},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_median,
+                "statistic": f"median of {args.steps} steps", "ms_per_step_mean": e2e_mean,
+                "ms_per_step_max": e2e_worst, "cuda_graph": True, "link": link},
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
         "roofline": roofline,
         "memory": memory,

@@ -228,9 +228,12 @@ __device__ __forceinline__ void stage_gaussian(ulonglong2 (&sp)[R][N], int t, fl
 // staged in shared memory is read once per thread and evaluated for PPT pixels. With an even PPT
 // the pixels go in pairs through packed f32x2 arithmetic: a pixel that does not composite a
 // Gaussian gets weight +0, which leaves its colour, depth and transmittance bit-identical, so the
-// result equals the one-pixel-per-thread kernel's. A pixel that has stopped (its transmittance
-// would fall below t_min) keeps its transmittance negated: -T, so that every later Gaussian
-// fails the composite test without a per-pixel flag, and only the rare stop itself branches.
+// result equals the one-pixel-per-thread kernel's. Alpha is zeroed where it is below alpha_min
+// before the weight is formed, so a live pixel composites its weight unconditionally and only
+// the rare stop (its transmittance would fall below t_min) branches. A pixel that has stopped, or
+// lies off the image, gets a row offset of 1e18 from the anchor row: its exponent is then
+// astronomically large, its alpha 0, and it keeps its colour and transmittance with no per-pixel
+// test in the loop.
 // For the backward each pixel saves the last list position it may composite: the one before its
 // stop, or the tile's last position if it never stops (between its last contributor and that
 // position no Gaussian covers it, so the backward takes the same decisions there).
@@ -241,7 +244,8 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
     const uint32_t* __restrict__ pair_vals, const float4* __restrict__ rec0,
     const float4* __restrict__ rec1, const float4* __restrict__ rec2, float* __restrict__ color,
     float* __restrict__ depth, float* __restrict__ alpha_out, float* __restrict__ t_final,
-    int32_t* __restrict__ last_index, Counters* __restrict__ counters) {
+    int32_t* __restrict__ last_index, const uint32_t* __restrict__ tile_order,
+    Counters* __restrict__ counters) {
   chain_wait();
   constexpr int kThreads = TW * TH / PPT;
   constexpr bool kPacked = PPT % 2 == 0;
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   static_assert(kThreads % 32 == 0, "whole warps only");
   __shared__ ulonglong2 sp[kPacked ? 6 : 3][kThreads];
   __shared__ unsigned long long s_eval[kThreads / 32];
-  const int gtile = blockIdx.x;
+  const int gtile = (int)tile_order[blockIdx.x];
   const int v = view_of_tile(views, gtile);
   const ViewParams& vp = views.v[v];
   const int local = gtile - vp.tile_base;
@@ -265,12 +269,14 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
   f32x2 T2[P2], C02[P2], C12[P2], C22[P2], D2[P2], FR[P2];
   uint32_t visited_end[PPT];  // one past the last list position the pixel visited
-  bool done[PPT];             // one-pixel path: the pixel has stopped (or is off the image)
+  bool done[PPT];             // the pixel has stopped (or is off the image)
   int live = 0;               // pixels of the thread that have not stopped
+  // Row offset of a pixel that takes no further part: every Gaussian's alpha there is 0.
+  constexpr float kFarRow = 1e18f;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     done[k] = !(px < vp.width && py0 + k < vp.height);
-    T[k] = done[k] ? -1.0f : 1.0f;
+    T[k] = 1.0f;
     C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
     visited_end[k] = done[k] ? range.x : range.y;
     live += done[k] ? 0 : 1;
@@ -278,18 +284,14 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
 #pragma unroll
   for (int q = 0; q < P2; ++q) {
     const int k0 = kPacked ? 2 * q : 0, k1 = kPacked ? 2 * q + 1 : 0;
-    T2[q] = f2_make(T[k0], T[k1]);
+    T2[q] = f2_make(1.0f, 1.0f);
     C02[q] = C12[q] = C22[q] = D2[q] = f2_make(0.0f, 0.0f);
-    FR[q] = f2_make((float)(r0_ + k0), (float)(r0_ + k1));
+    FR[q] = f2_make(done[k0] ? kFarRow : (float)(r0_ + k0), done[k1] ? kFarRow : (float)(r0_ + k1));
   }
   const f32x2 FX = f2_make(fx, fx);
-  // 0 <= x < t_min for a float x, as one unsigned compare of its bit pattern (t_min > 0).
-  const uint32_t t_min_bits = __float_as_uint(c.t_min);
 
-  // One staged Gaussian (list position pos, slot g) against the thread's pixel pairs; kClamp:
-  // the Gaussian may reach alpha_max somewhere, so alpha is clamped.
-  auto composite_pairs = [&](uint32_t pos, int g, auto clamp_tag) {
-    constexpr bool kClamp = decltype(clamp_tag)::value;
+  // One staged Gaussian (list position pos, slot g) against the thread's pixel pairs.
+  auto composite_pairs = [&](uint32_t pos, int g) {
     const ulonglong2 X = sp[0][g], L1 = sp[1][g], L2 = sp[2][g], L3 = sp[3][g];
     const ulonglong2 CA = sp[4 % (kPacked ? 6 : 3)][g], CB = sp[5 % (kPacked ? 6 : 3)][g];
     // Whitened offset t at the anchor row of the thread's column (Eq. alpha's exponent).
@@ -301,33 +303,30 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       const f32x2 tt = f2_fma(FR[q], L2.x, TA);
       const f32x2 ss = f2_fma(FR[q], L2.y, L3.x);
       const f32x2 nq = f2_fma(tt, tt, f2_fma(ss, ss, L3.y));  // -log2(o G)
-      float a0 = ex2_neg_approx(f2_lo(nq)), a1 = ex2_neg_approx(f2_hi(nq));
-      if constexpr (kClamp) {
-        a0 = fminf(c.alpha_max, a0);
-        a1 = fminf(c.alpha_max, a1);
-      }
-      const bool cov0 = a0 >= c.alpha_min, cov1 = a1 >= c.alpha_min;
-      // w = alpha T, and the transmittance after this Gaussian T' = T - w = T (1 - alpha):
-      // positive while the pixel is live (alpha <= alpha_max < 1), negative once stopped.
-      const f32x2 w = f2_mul(f2_make(a0, a1), T2[q]);
-      const f32x2 Tn = f2_sub(T2[q], w);
-      const float tn0 = f2_lo(Tn), tn1 = f2_hi(Tn);
-      const bool take0 = cov0 && !(tn0 < c.t_min), take1 = cov1 && !(tn1 < c.t_min);
-      const bool stop0 = cov0 && __float_as_uint(tn0) < t_min_bits;
-      const bool stop1 = cov1 && __float_as_uint(tn1) < t_min_bits;
-      const f32x2 wm = f2_make(take0 ? f2_lo(w) : 0.0f, take1 ? f2_hi(w) : 0.0f);
-      C02[q] = f2_fma(wm, CA.x, C02[q]);
-      C12[q] = f2_fma(wm, CA.y, C12[q]);
-      C22[q] = f2_fma(wm, CB.x, C22[q]);
-      D2[q] = f2_fma(wm, CB.y, D2[q]);
-      T2[q] = f2_sub(T2[q], wm);
-      if (stop0 || stop1) {  // once per pixel: keep -T from here on
+      const float a0 = fminf(c.alpha_max, ex2_neg_approx(f2_lo(nq)));
+      const float a1 = fminf(c.alpha_max, ex2_neg_approx(f2_hi(nq)));
+      // w = alpha T and the transmittance after this Gaussian T' = T - w; an uncovered pixel
+      // (alpha < alpha_min) has w = +0 and T' = T.
+      f32x2 w = f2_mul(f2_make(a0 >= c.alpha_min ? a0 : 0.0f, a1 >= c.alpha_min ? a1 : 0.0f),
+                       T2[q]);
+      f32x2 Tn = f2_sub(T2[q], w);
+      const bool stop0 = f2_lo(Tn) < c.t_min, stop1 = f2_hi(Tn) < c.t_min;
+      if (stop0 || stop1) {  // once per pixel: it composites nothing from here on
         const float t0 = f2_lo(T2[q]), t1 = f2_hi(T2[q]);
-        T2[q] = f2_make(stop0 ? -t0 : t0, stop1 ? -t1 : t1);
+        w = f2_make(stop0 ? 0.0f : f2_lo(w), stop1 ? 0.0f : f2_hi(w));
+        Tn = f2_make(stop0 ? t0 : f2_lo(Tn), stop1 ? t1 : f2_hi(Tn));
+        FR[q] = f2_make(stop0 ? kFarRow : f2_lo(FR[q]), stop1 ? kFarRow : f2_hi(FR[q]));
         if (stop0) visited_end[k0] = pos + 1;
         if (stop1) visited_end[k1] = pos + 1;
+        done[k0] = done[k0] || stop0;
+        done[k1] = done[k1] || stop1;
         live -= (int)stop0 + (int)stop1;
       }
+      C02[q] = f2_fma(w, CA.x, C02[q]);
+      C12[q] = f2_fma(w, CA.y, C12[q]);
+      C22[q] = f2_fma(w, CB.x, C22[q]);
+      D2[q] = f2_fma(w, CB.y, D2[q]);
+      T2[q] = Tn;
     }
   };
 
@@ -346,7 +345,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
         // Always with the clamp: a warp-uniform clamp-free variant (as in the backward) made
         // this loop slower (two copies of its body), measured 3.64 against 3.21 ms on the
         // 16-view 1080p window.
-        composite_pairs(pos, g, std::true_type{});
+        composite_pairs(pos, g);
       } else {
         const float4 g0 = reinterpret_cast<const float4*>(sp[0])[g];
         const float4 g1 = reinterpret_cast<const float4*>(sp[1])[g];
@@ -377,14 +376,11 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       }
     }
   }
-  bool stopped[PPT];
   if constexpr (kPacked) {
 #pragma unroll
     for (int q = 0; q < P2; ++q) {
-      stopped[2 * q] = f2_lo(T2[q]) < 0.0f;
-      stopped[2 * q + 1] = f2_hi(T2[q]) < 0.0f;
-      T[2 * q] = fabsf(f2_lo(T2[q]));
-      T[2 * q + 1] = fabsf(f2_hi(T2[q]));
+      T[2 * q] = f2_lo(T2[q]);
+      T[2 * q + 1] = f2_hi(T2[q]);
       C0[2 * q] = f2_lo(C02[q]);
       C0[2 * q + 1] = f2_hi(C02[q]);
       C1[2 * q] = f2_lo(C12[q]);
@@ -394,9 +390,6 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       D[2 * q] = f2_lo(D2[q]);
       D[2 * q + 1] = f2_hi(D2[q]);
     }
-  } else {
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) stopped[k] = done[k];
   }
   uint32_t evals = 0;
 #pragma unroll
@@ -412,7 +405,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
       alpha_out[pix] = 1.0f - T[k];
       t_final[pix] = T[k];
       // The last position the pixel may composite (stop position - 1, or the tile's last).
-      last_index[pix] = stopped[k] ? (int32_t)visited_end[k] - 2 : (int32_t)range.y - 1;
+      last_index[pix] = done[k] ? (int32_t)visited_end[k] - 2 : (int32_t)range.y - 1;
     }
   }
   // Visited (pixel, Gaussian) positions, for the roofline accounting.
@@ -481,7 +474,8 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
     const float4* __restrict__ rec1, const float4* __restrict__ rec2,
     const float* __restrict__ t_final, const int32_t* __restrict__ last_index,
     const float* __restrict__ d_color, const float* __restrict__ d_depth,
-    const float* __restrict__ d_alpha, float* __restrict__ g2d) {
+    const float* __restrict__ d_alpha, const uint32_t* __restrict__ tile_order,
+    float* __restrict__ g2d) {
   chain_wait();
   constexpr int kThreads = TW * TH / PPT;
   constexpr bool kPacked = PPT % 2 == 0;
@@ -492,7 +486,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   __shared__ uint32_t s_vi[kThreads];
   __shared__ int s_max_last[kThreads / 32];
   __shared__ __align__(16) float s_red[kThreads / 32][RL::kRows * kRedPad];
-  const int gtile = blockIdx.x;
+  const int gtile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   const int v = view_of_tile(views, gtile);
   const ViewParams& vp = views.v[v];
   const int local = gtile - vp.tile_base;
@@ -797,27 +791,53 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Launch order of the blends' tiles: longest run first. A CTA's time grows with its tile's run,
+// and runs differ by two orders of magnitude (a few tiles near dense structure hold thousands of
+// Gaussians); launched in tile order, a long run that starts late holds its SM after the others
+// have drained. Sorted by decreasing length, the long runs start first and the short ones fill
+// the end. The key is a length class (16 per octave, 8 bits), so the stable sort keeps equal
+// classes in tile order.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t length_class(uint32_t len) {
+  const uint32_t n = len + 1u;
+  const int e = 31 - __clz(n);
+  const uint32_t m = e >= 4 ? (n >> (e - 4)) & 15u : (n << (4 - e)) & 15u;
+  return min(255u, 16u * (uint32_t)e + m);
+}
+
+__global__ void tile_order_keys_kernel(const uint2* __restrict__ ranges, uint32_t total_tiles,
+                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  chain_wait();
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total_tiles) return;
+  const uint2 r = ranges[t];
+  keys[t] = 255u - length_class(r.y - r.x);
+  vals[t] = t;
+}
+
 template <int TW, int TH, int PPT>
 cudaError_t launch_blends_t(bool forward, const Views& views, const Consts& c,
                             const uint2* ranges, const uint32_t* pair_vals, const float4* rec0,
                             const float4* rec1, const float4* rec2, float* color, float* depth,
                             float* alpha, float* t_final, int32_t* last_index,
                             const float* d_color, const float* d_depth, const float* d_alpha,
-                            float* g2d, Counters* counters, cudaStream_t stream) {
+                            float* g2d, const uint32_t* tile_order, Counters* counters,
+                            cudaStream_t stream) {
   if (views.total_tiles == 0) return cudaSuccess;
   constexpr int kThreads = TW * TH / PPT;
   cudaError_t e;
   if (forward) {
     e = launch_chained(blend_forward_kernel<TW, TH, PPT>, dim3(views.total_tiles), dim3(kThreads),
                        stream, views, c, ranges, pair_vals, rec0, rec1, rec2, color, depth, alpha,
-                       t_final, last_index, counters);
+                       t_final, last_index, tile_order, counters);
   } else {
     const bool aux = d_depth != nullptr || d_alpha != nullptr;
     e = launch_chained(aux ? blend_backward_kernel<TW, TH, PPT, true>
                            : blend_backward_kernel<TW, TH, PPT, false>,
                        dim3(views.total_tiles), dim3(kThreads), stream, views, c, ranges,
                        pair_vals, rec0, rec1, rec2, (const float*)t_final,
-                       (const int32_t*)last_index, d_color, d_depth, d_alpha, g2d);
+                       (const int32_t*)last_index, d_color, d_depth, d_alpha, tile_order, g2d);
   }
   RGS_LAUNCHED();
   return e;
@@ -850,19 +870,37 @@ cudaError_t launch_duplicate(const Views& views, int n, const uint32_t* order,
   return e;
 }
 
+cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* keys,
+                              uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                              uint32_t* hist, uint32_t* block_sums, const uint32_t** order,
+                              cudaStream_t stream) {
+  *order = vals;
+  if (total_tiles <= 0) return cudaSuccess;
+  constexpr int kThreads = 256;
+  cudaError_t e = launch_chained(tile_order_keys_kernel, dim3((total_tiles + kThreads - 1) / kThreads),
+                                 dim3(kThreads), stream, ranges, (uint32_t)total_tiles, keys, vals);
+  RGS_LAUNCHED();
+  if (e != cudaSuccess) return e;
+  bool alt = false;
+  e = launch_radix_sort(keys, vals, keys_alt, vals_alt, total_tiles, nullptr, 0, 8, hist,
+                        block_sums, &alt, stream, kSortItemsSmall);
+  *order = alt ? vals_alt : vals;
+  return e;
+}
+
 cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, const uint2* ranges,
                          const uint32_t* pair_vals, const float4* rec0, const float4* rec1,
                          const float4* rec2, float* color, float* depth, float* alpha,
                          float* t_final, int32_t* last_index, const float* d_color,
                          const float* d_depth, const float* d_alpha, float* g2d,
-                         Counters* counters, cudaStream_t stream) {
+                         const uint32_t* tile_order, Counters* counters, cudaStream_t stream) {
   const int tw = views.tile_w, th = views.tile_h;
   const int ppt = forward ? views.pixels_per_thread : views.bwd_pixels_per_thread;
 #define RGS_BLEND(W, H, P)                                                                        \
   if (tw == W && th == H && ppt == P)                                                             \
   return launch_blends_t<W, H, P>(forward, views, c, ranges, pair_vals, rec0, rec1, rec2, color, \
                                   depth, alpha, t_final, last_index, d_color, d_depth, d_alpha,   \
-                                  g2d, counters, stream)
+                                  g2d, tile_order, counters, stream)
   RGS_BLEND(16, 16, 1);
   RGS_BLEND(16, 16, 2);
   RGS_BLEND(16, 16, 4);

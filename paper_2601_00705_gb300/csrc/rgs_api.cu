@@ -53,7 +53,11 @@ cudaError_t launch_blend(bool forward, const Views& views, const Consts& c, cons
                          const float4* rec2, float* color, float* depth, float* alpha,
                          float* t_final, int32_t* last_index, const float* d_color,
                          const float* d_depth, const float* d_alpha, float* g2d,
-                         Counters* counters, cudaStream_t stream);
+                         const uint32_t* tile_order, Counters* counters, cudaStream_t stream);
+cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* keys,
+                              uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                              uint32_t* hist, uint32_t* block_sums, const uint32_t** order,
+                              cudaStream_t stream);
 }  // namespace rgs
 
 using namespace rgs;
@@ -108,6 +112,9 @@ struct State {
   float* t_final = nullptr;
   int32_t* last_index = nullptr;
   uint2* ranges = nullptr;
+  // Launch order of the blends' tiles (longest run first) and the buffers of its sort.
+  uint32_t *tile_keys[2] = {nullptr, nullptr}, *tile_vals[2] = {nullptr, nullptr};
+  const uint32_t* tile_order = nullptr;
   uint32_t *pair_keys[2] = {nullptr, nullptr}, *pair_vals[2] = {nullptr, nullptr};
   const uint32_t* sorted_vals = nullptr;
   // Scratch.
@@ -218,9 +225,11 @@ bool is_capturing(cudaStream_t s) {
 
 // Scratch for the scans and sorts of up to `items` elements.
 rgs_status ensure_scratch(rgs_ctx* ctx, State& s, int64_t items, bool capturing) {
-  // The depth sort runs with small blocks over the per-Gaussian capacity, the tile sort with
-  // large blocks over the pair capacity; the table must fit either.
-  const int64_t hist = std::max(sort_hist_entries(std::max<int64_t>(s.vn_cap, 1), kSortItemsSmall),
+  // The depth sort and the sort of the tiles' launch order run with small blocks over the
+  // per-Gaussian and tile capacities, the tile sort with large blocks over the pair capacity;
+  // the table must fit each.
+  const int64_t small = std::max<int64_t>(std::max(s.vn_cap, s.tile_cap), 1);
+  const int64_t hist = std::max(sort_hist_entries(small, kSortItemsSmall),
                                 sort_hist_entries(std::max<int64_t>(items, 1)));
   const int64_t sums = std::max(scan_blocks(hist), scan_blocks(std::max<int64_t>(items, 1))) + 1;
   if (hist <= s.hist_cap && sums <= s.sums_cap) return RGS_OK;
@@ -298,8 +307,15 @@ rgs_status ensure_pix_tiles(rgs_ctx* ctx, State& s, int64_t pixels, int64_t tile
   if (tiles > s.tile_cap) {
     if (capturing) return fail(ctx, RGS_ERR_CAPACITY, "tile buffers grow during capture");
     RGS_CUDA(cudaDeviceSynchronize(), "sync before growth");
-    RGS_CUDA(alloc_region(s.r_tile, sizeof(uint2) * tiles), "allocate tile ranges");
-    s.ranges = static_cast<uint2*>(s.r_tile.base);
+    RGS_CUDA(alloc_region(s.r_tile, align_up(sizeof(uint2) * tiles) +
+                                         4 * align_up(sizeof(uint32_t) * tiles)),
+             "allocate tile ranges");
+    char* p = static_cast<char*>(s.r_tile.base);
+    s.ranges = carve<uint2>(p, tiles);
+    s.tile_keys[0] = carve<uint32_t>(p, tiles);
+    s.tile_keys[1] = carve<uint32_t>(p, tiles);
+    s.tile_vals[0] = carve<uint32_t>(p, tiles);
+    s.tile_vals[1] = carve<uint32_t>(p, tiles);
     s.tile_cap = tiles;
   }
   return RGS_OK;
@@ -862,11 +878,15 @@ rgs_status render_forward(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera
                                 s->vis_list, vis_cap, defer_colour, s->rec1, s->rec2, cnt,
                                 stream),
            "tile ranges and colours");
+  RGS_CUDA(launch_tile_order(s->ranges, views.total_tiles, s->tile_keys[0], s->tile_vals[0],
+                             s->tile_keys[1], s->tile_vals[1], s->hist, s->block_sums,
+                             &s->tile_order, stream),
+           "tile order");
   RGS_CUDA(mark(ctx, *s, 7, stream, capturing), "event");
   // 8. Blend.
   RGS_CUDA(launch_blend(true, views, consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
                         s->rec2, out->color, out->depth, out->alpha, s->t_final, s->last_index,
-                        nullptr, nullptr, nullptr, nullptr, cnt, stream),
+                        nullptr, nullptr, nullptr, nullptr, s->tile_order, cnt, stream),
            "blend forward");
   RGS_CUDA(mark(ctx, *s, 8, stream, capturing), "event");
   s->fwd_launches = (uint32_t)(launch_counter() - launches0);
@@ -961,7 +981,7 @@ rgs_status render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads*
   RGS_CUDA(mark(ctx, *s, kEvBwd0, stream, capturing), "event");
   RGS_CUDA(launch_blend(false, s->views, s->consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
                         s->rec2, nullptr, nullptr, nullptr, s->t_final, s->last_index, dc, dd, da,
-                        s->g2d, s->counters, stream),
+                        s->g2d, nullptr, s->counters, stream),
            "blend backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 1, stream, capturing), "event");
   RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->vis_mask, s->vis_list,

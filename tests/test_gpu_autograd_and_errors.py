@@ -337,9 +337,11 @@ def test_sh_event_defers_the_wait_for_the_coefficients():
     torch.cuda.synchronize()
     for a, b in zip(got[:3], ref[:3]):
         assert torch.equal(a, b)
+    # Gradients are sums of float atomics whose order varies from run to run: equal to about
+    # 1e-6 of the largest entry, not bit for bit.
     for k in ("means", "sh", "pose"):
         np.testing.assert_allclose(got_g[k].cpu().numpy(), ref_g[k].cpu().numpy(), rtol=1e-5,
-                                   atol=1e-7 * float(ref_g[k].abs().max()))
+                                   atol=1e-6 * float(ref_g[k].abs().max()))
     assert r2.stats(got[3])["status"] == 0
     r.release(ref[3])
     r2.release(got[3])
@@ -377,7 +379,8 @@ def test_deferred_colours_treat_nonfinite_sh_like_the_projection():
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose"):
         a0, a1 = g0[k].cpu().numpy(), g1[k].cpu().numpy()
         assert np.isfinite(a1).all(), k
-        np.testing.assert_allclose(a1, a0, rtol=1e-5, atol=1e-7 * float(np.abs(a0).max()))
+        # Sums of float atomics in a run-dependent order (see above).
+        np.testing.assert_allclose(a1, a0, rtol=1e-5, atol=1e-6 * float(np.abs(a0).max()))
     assert not g1["means"][bad].any() and not g1["sh"][bad].any()
     assert s0["n_nonfinite"] == 1 and s1["n_nonfinite"] == 1
     assert s0["status"] == 0 and s1["status"] == 0
