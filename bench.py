@@ -666,6 +666,17 @@ def run_ours(args, world, rank, local):
     ms_per_step = total_ms / args.steps
     value = throughput(world, pixels, args.steps, total_ms)
     stats = r.stats(state)
+    # Spread of the per-tile work: the run length of each non-empty tile (its Gaussians), the
+    # quantity a blend CTA's time follows.
+    runs = np.diff(r.ctx.tile_ranges(state, int(sum(
+        -(-c["width"] // tuned["tile_w"]) * -(-c["height"] // tuned["tile_h"])
+        for c in wl.cameras))).astype(np.int64), axis=1)[:, 0]
+    runs = runs[runs > 0]
+    tile_work = {"tiles": int(runs.size), "mean": float(runs.mean()) if runs.size else 0.0,
+                 "p50": float(np.median(runs)) if runs.size else 0.0,
+                 "p99": float(np.quantile(runs, 0.99)) if runs.size else 0.0,
+                 "max": int(runs.max()) if runs.size else 0, "unit": "Gaussians per tile",
+                 "blend_order": "forward: longest run first; backward: tile order"}
     # Device footprint of the timed step: everything the library holds for it (saved state,
     # pair lists, scratch) plus the caller's tensors the step reads and writes; and the device's
     # used memory as the driver reports it right after the timed region (the CUDA context, the
@@ -904,6 +915,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
         "roofline": roofline,
         "memory": memory,
+        "tile_work": tile_work,
         "batched_vs_per_view": {"per_view_loop_ms": loop_ms_per_step,
                                 "batched_ms": ms_per_step,
                                 "speedup": loop_ms_per_step / ms_per_step},

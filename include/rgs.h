@@ -338,8 +338,9 @@ rgs_status rgs_phase_times(rgs_ctx* ctx, uint64_t state, float* ms, int32_t n, v
  * and the [first, last + 1) range of every global tile into host_ranges (2 u32 per tile; global
  * tile ids count view by view, row-major inside a view).
  * rgs_copy_records: the projected records of every (view, Gaussian) into host_rec
- * ([n_views * n][12] floats: mean2d hi x, y, lo x, y; base-2 conic qa, qb, qc and log2 o;
- * r, g, b and camera-space depth), and the touched-tile counts into host_ntiles (may be NULL).
+ * ([n_views * n][12] floats: mean2d hi x, y, lo x, y; the whitening factor l11, l21, l22, lower
+ * triangular with L L^T = (log2 e / 2) (Sigma^I)^-1, and log2 o; r, g, b and camera-space depth),
+ * and the touched-tile counts into host_ntiles (may be NULL).
  * A record is meaningful only where its tile count is non-zero. */
 rgs_status rgs_copy_tile_lists(rgs_ctx* ctx, uint64_t state, uint32_t* host_vals, int64_t vals_cap,
                                uint32_t* host_ranges, int64_t* n_pairs, void* stream);

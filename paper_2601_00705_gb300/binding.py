@@ -425,6 +425,15 @@ class Context:
             ranges.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n), ctypes.c_void_p(stream)))
         return vals[:n.value], ranges[:total_tiles]
 
+    def tile_ranges(self, state: int, total_tiles: int, stream: int = 0):
+        """[first, last + 1) of every global tile's run in a state's sorted pair list."""
+        n = ctypes.c_int64()
+        ranges = np.zeros((max(total_tiles, 1), 2), dtype=np.uint32)
+        self._check(self.lib.rgs_copy_tile_lists(
+            self.handle, ctypes.c_uint64(state), None, 0, ranges.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(n), ctypes.c_void_p(stream)))
+        return ranges[:total_tiles]
+
     def records(self, state: int, vn: int, stream: int = 0):
         """(records [vn, 12] f32, tile counts [vn] u32) of a state."""
         rec = np.zeros((max(vn, 1), 12), dtype=np.float32)
