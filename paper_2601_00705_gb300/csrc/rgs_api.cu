@@ -559,7 +559,7 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, RGS_ERR_CUDA, "cudaSetDevice");
   const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
   const int64_t n = g->n;
-  // Scratch: images [P,5], upstream colour gradient [P,3] (zero), parameter and pose gradients.
+  // Scratch: images [P,5], upstream colour gradient [P,3], parameter and pose gradients.
   const int64_t n1 = std::max<int64_t>(n, 1);
   const size_t bytes = align_up(sizeof(float) * 5 * pixels) + align_up(sizeof(float) * 3 * pixels) +
                        3 * align_up(sizeof(float) * 4 * n1) + align_up(sizeof(float) * n1) +
@@ -579,7 +579,10 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   uint64_t state = 0;
   do {
-    if (cudaMemsetAsync(upc, 0, sizeof(float) * 3 * pixels, stream) != cudaSuccess ||
+    // Every byte 0x3a makes each upstream value 7.1e-4: a non-zero colour gradient, so that the
+    // trials' backward blends issue their gradient atomics as under a real loss (with zeros the
+    // all-zero sums skip them, which favoured the settings with more atomics).
+    if (cudaMemsetAsync(upc, 0x3a, sizeof(float) * 3 * pixels, stream) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaEventCreate(&e2) != cudaSuccess) {
       result = fail(ctx, RGS_ERR_CUDA, "autotune setup");
