@@ -697,7 +697,7 @@ def run_ours(args, world, rank, local):
                  "p50": float(np.median(runs)) if runs.size else 0.0,
                  "p99": float(np.quantile(runs, 0.99)) if runs.size else 0.0,
                  "max": int(runs.max()) if runs.size else 0, "unit": "Gaussians per tile",
-                 "blend_order": "forward: longest run first; backward: tile order"}
+                 "blend_order": "both blends: longest run first (by octave of the run length)"}
     # Device footprint of the timed step: everything the library holds for it (saved state,
     # pair lists, scratch) plus the caller's tensors the step reads and writes; and the device's
     # used memory as the driver reports it right after the timed region (the CUDA context, the

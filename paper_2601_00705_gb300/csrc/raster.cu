@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
   __shared__ uint32_t s_vi[kThreads];
   __shared__ int s_max_last[kThreads / 32];
   __shared__ __align__(16) float s_red[kThreads / 32][RL::kRows * kRedPad];
-  const int gtile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+  const int gtile = (int)tile_order[blockIdx.x];
   const int v = view_of_tile(views, gtile);
   const ViewParams& vp = views.v[v];
   const int local = gtile - vp.tile_base;
@@ -800,14 +800,13 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_backward_kernel(
 // and runs differ by two orders of magnitude (a few tiles near dense structure hold thousands of
 // Gaussians); launched in tile order, a long run that starts late holds its SM after the others
 // have drained. Sorted by decreasing length, the long runs start first and the short ones fill
-// the end. The key is a length class (16 per octave, 8 bits), so the stable sort keeps equal
-// classes in tile order.
+// the end. The key is the run length's octave, so the stable sort keeps each octave's tiles in
+// tile order: neighbouring tiles, which share Gaussians (their records, and in the backward their
+// gradient atomics), still run together. Finer classes (16 per octave) made the backward 3 %
+// slower; octaves made it 1 % faster than plain tile order.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t length_class(uint32_t len) {
-  const uint32_t n = len + 1u;
-  const int e = 31 - __clz(n);
-  const uint32_t m = e >= 4 ? (n >> (e - 4)) & 15u : (n << (4 - e)) & 15u;
-  return min(255u, 16u * (uint32_t)e + m);
+__device__ __forceinline__ uint32_t length_octave(uint32_t len) {
+  return (uint32_t)(31 - __clz(len + 1u));  // 0 .. 32
 }
 
 __global__ void tile_order_keys_kernel(const uint2* __restrict__ ranges, uint32_t total_tiles,
@@ -816,7 +815,7 @@ __global__ void tile_order_keys_kernel(const uint2* __restrict__ ranges, uint32_
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total_tiles) return;
   const uint2 r = ranges[t];
-  keys[t] = 255u - length_class(r.y - r.x);
+  keys[t] = 32u - length_octave(r.y - r.x);
   vals[t] = t;
 }
 
@@ -886,7 +885,7 @@ cudaError_t launch_tile_order(const uint2* ranges, int total_tiles, uint32_t* ke
   RGS_LAUNCHED();
   if (e != cudaSuccess) return e;
   bool alt = false;
-  e = launch_radix_sort(keys, vals, keys_alt, vals_alt, total_tiles, nullptr, 0, 8, hist,
+  e = launch_radix_sort(keys, vals, keys_alt, vals_alt, total_tiles, nullptr, 0, 6, hist,
                         block_sums, &alt, stream, kSortItemsSmall);
   *order = alt ? vals_alt : vals;
   return e;

@@ -984,7 +984,7 @@ rgs_status render_backward(rgs_ctx* ctx, uint64_t handle, const rgs_image_grads*
   RGS_CUDA(mark(ctx, *s, kEvBwd0, stream, capturing), "event");
   RGS_CUDA(launch_blend(false, s->views, s->consts, s->ranges, s->sorted_vals, s->rec0, s->rec1,
                         s->rec2, nullptr, nullptr, nullptr, s->t_final, s->last_index, dc, dd, da,
-                        s->g2d, nullptr, s->counters, stream),
+                        s->g2d, s->tile_order, s->counters, stream),
            "blend backward");
   RGS_CUDA(mark(ctx, *s, kEvBwd0 + 1, stream, capturing), "event");
   RGS_CUDA(launch_preprocess_backward(s->views, s->consts, s->g, s->vis_mask, s->vis_list,
