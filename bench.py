@@ -489,6 +489,60 @@ def measured_fp64_tflops(dev) -> float:
     return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
 
 
+def views_tiles(wl, tuned) -> int:
+    """Global tiles of the workload's views at the tuned tile shape."""
+    return int(sum(-(-c["width"] // tuned["tile_w"]) * -(-c["height"] // tuned["tile_h"])
+                   for c in wl.cameras))
+
+
+def phase_rooflines(phases, stats, n, V, K, tiles, hbm_peak, fp32_peak):
+    """Every phase of the step against its roofline: the blends by their FP32 work (15 and 40
+    FLOP per visited position), the others by their algorithmic bytes, the minimum each must
+    move (inputs read once, outputs written once, sort passes as the radix digits require):
+    - preprocess: the cull reads mean, log-scales, quaternion and opacity logit (44 B) per
+      Gaussian and clears one visibility bit per (view, Gaussian); the projection reads those and
+      the SH coefficients (12K B) and writes a 48 B record and a 4 B tile count per visible entry;
+    - compact: the visibility bits, and a key, a value and a list entry (12 B) written plus a
+      16 B record read per visible entry;
+    - depth sort: 4 passes of 8-bit digits over the 31-bit depth keys, each reading the key
+      twice and the value once and writing both (20 B per entry);
+    - offsets: a tile count gathered and an offset written per visible entry (8 B);
+    - duplicate: a (tile, entry) pair written (8 B) per pair, order, offset, count and two
+      records read (44 B) per visible entry;
+    - tile sort: ceil(bits / 9) passes of the wide radix sort, 20 B per pair each;
+    - ranges: every pair's key read, two words written per tile, and the tile order's keys and
+      values sorted (one pass, 24 B per tile);
+    - preprocess backward: a 64 B record read and written per visible entry, the parameters read
+      and their gradients written once per Gaussian (11 + 3K floats each)."""
+    nv, pairs, n_eval = stats["n_visible"], stats["n_pairs"], stats["n_eval"]
+    tile_bits = max(1, int(np.ceil(np.log2(tiles + 2))))
+    bytes_model = {
+        "preprocess": 44 * n + n * V / 8 + nv * (44 + 12 * K + 52),
+        "compact": n * V / 8 + 28 * nv,
+        "depth_sort": 4 * 20 * nv,
+        "offsets": 8 * nv,
+        "duplicate": 8 * pairs + 44 * nv,
+        "tile_sort": int(np.ceil(tile_bits / 9)) * 20 * pairs,
+        "ranges": 4 * pairs + 8 * tiles + 24 * tiles,
+        "preprocess_backward": 2 * 64 * nv + 2 * 4 * (11 + 3 * K) * n,
+    }
+    flop_model = {"blend_forward": FWD_FLOP_PER_EVAL * n_eval,
+                  "blend_backward": BWD_FLOP_PER_EVAL * n_eval}
+    out = {}
+    for name, ms in phases.items():
+        if ms <= 0:
+            continue
+        if name in flop_model:
+            a = flop_model[name] / (ms * 1e-3) / 1e12
+            out[name] = {"ms": ms, "bound": "alu", "flop": flop_model[name], "achieved": a,
+                         "unit": "TFLOP/s", "frac": a / fp32_peak}
+        elif name in bytes_model:
+            a = bytes_model[name] / (ms * 1e-3) / 1e9
+            out[name] = {"ms": ms, "bound": "hbm", "bytes": float(bytes_model[name]),
+                         "achieved": a, "unit": "GB/s", "frac": a / hbm_peak}
+    return out
+
+
 def measure_seeding(r, steps):
     """Dense initialisation on a TUM-shaped keyframe window (10 views, 640x480): 131072 matched
     reference pixels with up to 4 neighbours each (0.3 px noise, 5 % outliers)."""
@@ -914,6 +968,9 @@ def run_ours(args, world, rank, local):
                     "unit": "GB/s", "frac": achieved / hbm if achieved is not None else None,
                     "traffic": None}
 
+    phase_roofline = phase_rooflines(phases, stats, n, V, K, views_tiles(wl, tuned),
+                                     float(peaks.get("hbm_gbs", 6800.0)), fp32_peak)
+
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -935,6 +992,7 @@ def run_ours(args, world, rank, local):
                 "ms_per_step_max": e2e_worst, "cuda_graph": True, "link": link},
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
         "roofline": roofline,
+        "phase_roofline": phase_roofline,
         "memory": memory,
         "tile_work": tile_work,
         "batched_vs_per_view": {"per_view_loop_ms": loop_ms_per_step,
