@@ -1,12 +1,13 @@
 // raster.cu -- pair duplication, tile ranges, and the forward / backward alpha blends.
 //
-// Forward blend (Section 3.1, Eq. alpha; Section 3.2.2): one CTA per (view, tile); the tile's
-// Gaussians, already in near-to-far order, are staged through shared memory in batches of one
-// Gaussian per thread and every thread composites its pixels front to back with early exit.
+// Forward blend (Section 3.1, Eq. alpha; Section 3.2.2): one CTA per (view, tile), the tiles
+// taken longest run first; the tile's Gaussians, already in near-to-far order, are staged
+// through shared memory in batches of one Gaussian per thread and every thread composites its
+// pixels front to back with early exit.
 // Backward blend: the same tiles are walked back to front from each pixel's last contributor,
 // recovering the transmittance by division from the saved final value, so no per-pixel list is
-// stored; per-Gaussian screen-space gradients are reduced across the warp before one atomic per
-// value and warp.
+// stored; per-Gaussian screen-space gradient sums are reduced per warp through shared memory, in
+// groups of Gaussians, before one atomic per value and Gaussian.
 #include <algorithm>
 #include <type_traits>
 
