@@ -50,6 +50,8 @@ L2_FLUSH_BYTES = 256 << 20
 # compositing, 15 FP32 operations (plus one exp); the backward's recomputation, transmittance
 # recovery and screen-space gradients, 40 FP32 operations (plus two MUFU operations and the
 # atomics after the warp reduction).
+# Sorts of at least this many pairs take the library's wide radix passes (9-bit digits).
+WIDE_SORT_MIN_PAIRS = 4 << 20
 FWD_FLOP_PER_EVAL = 15
 BWD_FLOP_PER_EVAL = 40
 
@@ -509,7 +511,8 @@ def phase_rooflines(phases, stats, n, V, K, tiles, hbm_peak, fp32_peak):
     - offsets: a tile count gathered and an offset written per visible entry (8 B);
     - duplicate: a (tile, entry) pair written (8 B) per pair, order, offset, count and two
       records read (44 B) per visible entry;
-    - tile sort: ceil(bits / 9) passes of the wide radix sort, 20 B per pair each;
+    - tile sort: ceil(bits / 9) passes of the wide radix sort from 4M pairs on, else ceil(bits /
+      8) passes of the small one, 20 B per pair each;
     - ranges: every pair's key read, two words written per tile, and the tile order's keys and
       values sorted (one pass, 24 B per tile);
     - preprocess backward: a 64 B record read and written per visible entry, the parameters read
@@ -522,7 +525,8 @@ def phase_rooflines(phases, stats, n, V, K, tiles, hbm_peak, fp32_peak):
         "depth_sort": 4 * 20 * nv,
         "offsets": 8 * nv,
         "duplicate": 8 * pairs + 44 * nv,
-        "tile_sort": int(np.ceil(tile_bits / 9)) * 20 * pairs,
+        "tile_sort": int(np.ceil(tile_bits / (9 if pairs >= WIDE_SORT_MIN_PAIRS else 8)))
+                     * 20 * pairs,
         "ranges": 4 * pairs + 8 * tiles + 24 * tiles,
         "preprocess_backward": 2 * 64 * nv + 2 * 4 * (11 + 3 * K) * n,
     }
