@@ -206,9 +206,10 @@ rgs_status rgs_render_backward(rgs_ctx* ctx, uint64_t state, const rgs_image_gra
 /* Autotuner: picks the blend tile shape and the pixels per thread of each blend (the per-thread
  * batch depth) that make one forward + backward of this exact workload fastest on this GPU. For
  * every tile shape (16x16, 8x8, 32x8) and every pixels-per-thread value it admits (1, 2, 4, 8)
- * the forward and the backward are timed separately with CUDA events (one warm-up and three
- * timed runs, zero upstream colour gradient, all gradients requested) in scratch buffers of its
- * own; per tile shape the fastest forward and the fastest backward setting are combined, and the
+ * the forward and the backward are timed separately with CUDA events (one warm-up and the
+ * fastest of four timed runs, a uniform non-zero upstream colour gradient, all gradients
+ * requested) in scratch buffers of its own; per tile shape the fastest forward and the fastest
+ * backward setting are combined, and the
  * tile shape with the smallest sum wins. The choice is written into cfg->tile_w, cfg->tile_h,
  * cfg->pixels_per_thread and cfg->backward_pixels_per_thread (other fields are kept) and cached
  * in the context under (n, sh_degree, the views' sizes); a later call with the same key returns

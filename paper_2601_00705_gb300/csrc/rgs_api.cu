@@ -611,8 +611,10 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
         trial.pixels_per_thread = ppt;
         trial.backward_pixels_per_thread = ppt;
         trial.sh_ready_event = nullptr;  // the trials run on coefficients already on the device
-        float t_f = 0.0f, t_b = 0.0f;
-        for (int it = 0; it < 4 && result == RGS_OK; ++it) {
+        // The fastest of four timed runs (after one warm-up) of each blend: the minimum is the
+        // least disturbed by the eager forward's host synchronisations and other tenants.
+        float t_f = 1e30f, t_b = 1e30f;
+        for (int it = 0; it < 5 && result == RGS_OK; ++it) {
           cudaEventRecord(e0, stream);
           rgs_status st = rgs_render_forward(ctx, g, cams, n_views, &trial, &out, &state, stream);
           cudaEventRecord(e1, stream);
@@ -628,8 +630,8 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
                      cudaEventElapsedTime(&ms_b, e1, e2) != cudaSuccess) {
             result = fail(ctx, RGS_ERR_CUDA, "autotune timing");
           } else if (it > 0) {  // the first run is the warm-up
-            t_f += ms_f;
-            t_b += ms_b;
+            t_f = fminf(t_f, ms_f);
+            t_b = fminf(t_b, ms_b);
           }
         }
         if (result != RGS_OK) break;
@@ -654,7 +656,7 @@ rgs_status rgs_autotune(rgs_ctx* ctx, const rgs_gaussians* g, const rgs_camera* 
     cfg->tile_h = choice.tile_h;
     cfg->pixels_per_thread = choice.ppt;
     cfg->backward_pixels_per_thread = choice.bwd_ppt;
-    if (ms_out) *ms_out = best / 3.0f;
+    if (ms_out) *ms_out = best;
   } while (false);
   cudaStreamSynchronize(stream);
   if (state) {
