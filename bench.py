@@ -596,8 +596,9 @@ def measure_seeding(r, steps):
                                      "nominal_peak": FP64_NOMINAL_TFLOPS,
                                      "flop_per_hypothesis": TRI_FP64_FLOP_PER_HYP},
             "init_seeds_ms": float(np.median(sms)),
-            "init_seeds_note": "host wall clock of the synchronous call (scratch allocation, "
-                               "two count read-backs, ~15 kernels)"}
+            "init_seeds_note": "host wall clock of the synchronous call (two count read-backs, "
+                               "~15 kernels; the scratch, kept by the context, was allocated "
+                               "by the first call outside the timing)"}
 
 
 def measure_mapping(r, params, cameras, images, mask, steps, hbm_peak):

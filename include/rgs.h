@@ -478,7 +478,9 @@ rgs_status rgs_triangulate(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views
  *   outputs (DEVICE, capacity m seeds, in increasing reference-pixel order): index [m] int32
  *     (the reference pixel of each seed), means [m][3], log_scales [m][3], quats [m][4],
  *     opacity_logits [m], sh [m][K][3], normals [m][3]; n_seeds: HOST, the number written.
- * Allocates and frees device scratch and synchronises `stream`; not for stream capture. */
+ * Uses a device scratch region held by the context (allocated on the first call and again when m
+ * outgrows it, freed by rgs_destroy), so two calls on one context must not run at the same time;
+ * synchronises `stream`; not for stream capture. */
 rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views, int64_t m,
                           int32_t k, const int32_t* ref_view, const int32_t* nb_view,
                           const uint32_t* valid, const double* X, const double* err,

@@ -172,6 +172,7 @@ struct rgs_ctx {
   uint64_t next_id = 1;
   Counters* host_counters = nullptr;  // pinned
   double* track_sums = nullptr;       // device [kMaxViews][4]: exposure-fit sums
+  Region r_seed;                      // seed-initialisation scratch, grown on demand
 };
 
 namespace {
@@ -528,6 +529,7 @@ void rgs_destroy(rgs_ctx* ctx) {
   ctx->states.clear();
   if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
   if (ctx->track_sums) cudaFree(ctx->track_sums);
+  free_region(ctx->r_seed);
   delete ctx;
 }
 
@@ -1419,9 +1421,11 @@ rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
                        align_up(sizeof(uint32_t) * sums) + align_up(sizeof(uint64_t) * m) +
                        align_up(sizeof(double) * 3 * m) +
                        align_up(sizeof(float) * (size_t)m * (3 + 3 + 4 + 1 + 3 + 3 * sh_k));
-  char* base = nullptr;
-  RGS_CUDA(cudaMalloc(&base, bytes), "allocate seeding scratch");
-  char* p = base;
+  // The scratch region is kept in the context and only grows: repeated calls (one per new
+  // keyframe) neither allocate nor free.
+  if (ctx->r_seed.bytes < bytes)
+    RGS_CUDA(alloc_region(ctx->r_seed, bytes), "allocate seeding scratch");
+  char* p = static_cast<char*>(ctx->r_seed.base);
   uint32_t* flags = carve<uint32_t>(p, m);
   uint32_t* pos = carve<uint32_t>(p, m);
   uint32_t* vidx = carve<uint32_t>(p, m);
@@ -1473,7 +1477,6 @@ rgs_status rgs_init_seeds(rgs_ctx* ctx, const rgs_camera* cams, int32_t n_views,
     *n_seeds = s > 0 ? (int64_t)host_tot[1] : 0;
   } while (false);
   cudaStreamSynchronize(stream);
-  cudaFree(base);
   return result;
 }
 
