@@ -810,6 +810,34 @@ __global__ void __launch_bounds__(kPreThreads, 6) backward_gaussian_kernel(
   }
   const int i = blockIdx.x * kPreThreads + threadIdx.x;
   if (i >= n) return;
+  // Views that see the Gaussian, as marked by phase 1 (consumed: left zero for the next call).
+  uint64_t vis = vis_mask[i];
+  if constexpr (!kReg) {
+    // Seen by no view: every gradient is zero, and nothing else needs the parameters.
+    if (vis == 0) {
+      if ((grad_mask & RGS_GRAD_MEANS) && d_means)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d_means[3 * (size_t)i + k] = 0.0f;
+      if ((grad_mask & RGS_GRAD_SCALES) && d_log_scales)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d_log_scales[3 * (size_t)i + k] = 0.0f;
+      if ((grad_mask & RGS_GRAD_QUATS) && d_quats)
+        reinterpret_cast<float4*>(d_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((grad_mask & RGS_GRAD_OPACITY) && d_logits) d_logits[i] = 0.0f;
+      if ((grad_mask & RGS_GRAD_SH) && d_sh) {
+        float* p = d_sh + (size_t)i * 3 * K;
+        if ((3 * K) % 4 == 0) {
+#pragma unroll
+          for (int k = 0; k < 3 * K / 4; ++k)
+            reinterpret_cast<float4*>(p)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3 * K; ++k) p[k] = 0.0f;
+        }
+      }
+      return;
+    }
+  }
   // Every parameter read is issued here, together, ahead of the records' loads.
   float m[3], ls[3], q[4];
 #pragma unroll
@@ -832,8 +860,6 @@ __global__ void __launch_bounds__(kPreThreads, 6) backward_gaussian_kernel(
   float* gsh = s_gsh + threadIdx.x;  // gsh[k * kPreThreads]
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) gsh[k * kPreThreads] = 0.0f;
-  // Views that see the Gaussian, as marked by phase 1 (consumed: left zero for the next call).
-  uint64_t vis = vis_mask[i];
   if (vis) vis_mask[i] = 0ull;
   const bool any_visible = vis != 0;
   const int n_seen = __popcll(vis);
