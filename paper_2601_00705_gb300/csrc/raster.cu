@@ -429,13 +429,13 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_forward_kernel(
 
 // ------------------------------------------------------------------------------------------
 // Per-warp reduction of the visited Gaussians' gradient sums through shared memory. Each visit
-// writes the lane's kRedVals partial sums as one column of kRedVals rows (row b * kRedVals + k
-// for the b-th Gaussian of the group); after kRedBatch visits (or at the end of a staged batch)
+// writes the lane's kVals partial sums as one column of kVals rows (row b * kVals + k for the
+// b-th Gaussian of the group, RedLayout); after kBatch visits (or at the end of a staged batch)
 // every lane adds up whole rows (eight 16-byte reads of a row padded to 36 floats, so that both
 // the column writes and the row reads are free of bank conflicts) and parks the row total in
 // the padding. Lane b then turns Gaussian b's totals into its whitened moments and issues the
-// atomics. Per visit this costs kRedVals shared stores and a share of the row sums, in place of
-// a shuffle butterfly with its selects after every Gaussian.
+// atomics. Per visit this costs kVals shared stores and a share of the row sums, in place of a
+// shuffle butterfly with its selects after every Gaussian.
 //
 // The lane's values: k = 0..2: sdp, sr, srr (the sums of dp, dp r and dp r^2 over its pixels,
 // r the row offset from the tile's anchor row), k = 3..5: t_a sdp, t_a sr, t_a^2 sdp (t_a the
