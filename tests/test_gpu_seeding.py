@@ -10,7 +10,8 @@ a TUM-shaped keyframe window (noise 0.3 px, 5 % outliers):
     logits max-abs 1e-6; axial log-scale 2e-4 (it moves with the error and angle above);
     normals and the quaternion's rotation max-abs 1e-5; SH DC max-abs 1e-5;
     with voxel thinning, the same kept set;
-  * edge cases: m = 0, reference or neighbour views out of range.
+  * edge cases: m = 0, reference or neighbour views out of range;
+  * the seeding scratch the context keeps, across calls that grow it and calls that reuse it.
 """
 import numpy as np
 import pytest
@@ -128,3 +129,13 @@ def test_seeding_edge_cases():
         seeding.triangulate(r.ctx, c.cameras, c.ref_view, c.ref_xy,
                             np.zeros((64, 9), np.int32), np.zeros((64, 9, 2)),
                             np.zeros((64, 9), np.float32), r.device, r.stream_handle(), **cfg)
+
+
+def test_seed_scratch_grows_and_is_reused():
+    # The context keeps the seeding scratch between calls: a small call, a larger one (the
+    # scratch grows) and a small one again (reused) each match the oracle.
+    cfg = _cfg(plane_radius=0.25)
+    for m, seed in ((300, 1010), (4096, 1011), (300, 1012)):
+        gpu, ref = _seed_both(_case(m=m, seed=seed), cfg)
+        np.testing.assert_array_equal(gpu["index"], ref["index"], err_msg=str(m))
+        np.testing.assert_allclose(gpu["means"], ref["means"], rtol=0, atol=1e-6, err_msg=str(m))
