@@ -152,21 +152,21 @@ def test_tile_shape_and_pixels_per_thread_do_not_change_results(tile):
                                    err_msg=k)
 
 
-@pytest.mark.parametrize("bwd_ppt", [8, 4, 1])
-def test_long_tile_runs_backward_matches_oracle(bwd_ppt):
+@pytest.mark.parametrize("bwd_ppt,weight_depth", [(8, 0.0), (4, 0.0), (1, 0.0), (8, 0.1)])
+def test_long_tile_runs_backward_matches_oracle(bwd_ppt, weight_depth):
     """Runs of thousands of Gaussians per tile (the crowded scene: its longest run exceeds 8192,
     see the binning test, and most depths are shared by ~30 Gaussians): the backward walks many
     staged batches and reduction groups per tile; every gradient against the oracle, for one,
-    two and eight warps per tile."""
+    two and eight warps per tile; with a depth term in the loss, the blend's depth variant."""
     wl = synthetic.crowded()
-    g, orc0, d_color, _ = _oracle_l1_case(wl)
-    orc = oracle.render(g, wl.cameras, d_color=d_color)
-    gpu = gpu_render(g, wl.cameras, d_color=d_color, tile_w=16, tile_h=16, pixels_per_thread=4,
-                     backward_pixels_per_thread=bwd_ppt)
+    g, orc0, d_color, d_depth = _oracle_l1_case(wl, weight_depth=weight_depth)
+    orc = oracle.render(g, wl.cameras, d_color=d_color, d_depth=d_depth)
+    gpu = gpu_render(g, wl.cameras, d_color=d_color, d_depth=d_depth, tile_w=16, tile_h=16,
+                     pixels_per_thread=4, backward_pixels_per_thread=bwd_ppt)
     assert gpu["stats"]["n_pairs"] > 2 * 8192
     info = compare_forward(gpu, orc)
     errs = compare_backward(gpu, orc)
-    print("crowded", bwd_ppt, info, errs)
+    print("crowded", bwd_ppt, weight_depth, info, errs)
 
 
 def test_replica_forward_and_pose_gradient():
