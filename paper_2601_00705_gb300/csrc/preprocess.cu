@@ -486,8 +486,8 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
 
 // Forward, pass 3 (after the tile lists are built, before the blend), one launch of two
 // independent parts.
-//  * Blocks [0, range_blocks): tile ranges. Thread t looks at the four sorted keys 4t .. 4t + 3
-//    (one 16-byte load; the key arrays are 256-byte aligned) and the key before them, and writes
+//  * Blocks [0, range_blocks): tile ranges. Thread t looks at the eight sorted keys 8t .. 8t + 7
+//    (two 16-byte loads; the key arrays are 256-byte aligned) and the key before them, and writes
 //    the run boundaries among them into `ranges` (zero on entry: tiles without pairs keep
 //    [0, 0)).
 //  * The other blocks: one thread per visible entry, in (view, Gaussian) order (grid-stride
@@ -498,6 +498,7 @@ __global__ void __launch_bounds__(kPreThreads) project_kernel(
 //    rec2.xyz. An entry with a non-finite coefficient gets log2 opacity -inf, so that it covers
 //    no pixel in either blend, and is counted as culled.
 constexpr int kRangesColourThreads = 256;
+constexpr int kRangesKeys = 8;  // sorted keys per thread of the range part (two 16-byte loads)
 
 template <int DEG, bool kDevPose>
 __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
@@ -509,27 +510,30 @@ __global__ void __launch_bounds__(kRangesColourThreads) ranges_colour_kernel(
   chain_wait();
   if (blockIdx.x < range_blocks) {
     const uint32_t np = counters->n_pairs_stored;
-    const uint32_t p0 = 4u * (blockIdx.x * kRangesColourThreads + threadIdx.x);
+    const uint32_t p0 = (uint32_t)kRangesKeys * (blockIdx.x * kRangesColourThreads + threadIdx.x);
     if (p0 >= np) return;
-    uint32_t k[5];  // k[0] = key before p0 (or none), k[1..4] = keys p0 .. p0 + 3
+    uint32_t k[kRangesKeys + 1];  // k[0] = key before p0 (or none), k[1..] = keys p0 ..
     k[0] = p0 > 0 ? keys[p0 - 1] : 0xffffffffu;
-    if (p0 + 4 <= np) {
-      const uint4 q = *reinterpret_cast<const uint4*>(keys + p0);
-      k[1] = q.x;
-      k[2] = q.y;
-      k[3] = q.z;
-      k[4] = q.w;
+    if (p0 + kRangesKeys <= np) {
+#pragma unroll
+      for (int h = 0; h < kRangesKeys / 4; ++h) {
+        const uint4 q = *reinterpret_cast<const uint4*>(keys + p0 + 4 * h);
+        k[4 * h + 1] = q.x;
+        k[4 * h + 2] = q.y;
+        k[4 * h + 3] = q.z;
+        k[4 * h + 4] = q.w;
+      }
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) k[j + 1] = p0 + j < np ? keys[p0 + j] : 0xffffffffu;
+      for (int j = 0; j < kRangesKeys; ++j) k[j + 1] = p0 + j < np ? keys[p0 + j] : 0xffffffffu;
     }
-    const uint32_t next = p0 + 4 < np ? keys[p0 + 4] : 0xffffffffu;
+    const uint32_t next = p0 + kRangesKeys < np ? keys[p0 + kRangesKeys] : 0xffffffffu;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kRangesKeys; ++j) {
       const uint32_t p = p0 + j;
       const uint32_t key = k[j + 1];
       if (p >= np || key >= total_tiles) continue;
-      const uint32_t after = j < 3 ? k[j + 2] : next;
+      const uint32_t after = j < kRangesKeys - 1 ? k[j + 2] : next;
       if (p == 0 || k[j] != key) ranges[key].x = p;
       if (p == np - 1 || after != key) ranges[key].y = p + 1;
     }
@@ -1109,8 +1113,8 @@ cudaError_t launch_ranges_colour(const uint32_t* keys, int total_tiles, uint2* r
                                  bool colour, float4* rec1, float4* rec2, Counters* counters,
                                  cudaStream_t stream) {
   const uint32_t range_blocks =
-      (uint32_t)(((int64_t)pair_capacity + 4 * kRangesColourThreads - 1) /
-                 (4 * kRangesColourThreads));
+      (uint32_t)(((int64_t)pair_capacity + kRangesKeys * kRangesColourThreads - 1) /
+                 (kRangesKeys * kRangesColourThreads));
   const int64_t colour_items = colour && g.n > 0 ? vis_cap : 0;
   const uint32_t colour_blocks = (uint32_t)std::min<int64_t>(
       (colour_items + kRangesColourThreads - 1) / kRangesColourThreads, 4 * 152);
